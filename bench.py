@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Throughput of the TR-BRSGD step on one GB300 (and N replicas under torchrun).
+
+Workload (the headline configuration): N=4 tensor 100x100x100x100 FP32
+(400 MB), TR ranks all 10, planted cores G_{n(2)} = U_n S V^T with singular
+values geometric from 1 to 1e-3, noise of relative norm 1e-4, uniform fiber
+sampling, |F| = 1000, fixed step, plain TR-BRSGD.  Inputs are synthetic and
+seeded (synth module); X is formed on the device by the library's
+reconstruction.  One bench step = one TR-BRSGD iteration (Algorithm 3): mode
+draw, Algorithm 2 sampling and fiber gather, residual, gradient (Eq.
+S_gradient), update of G_n.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle on the same workload instead (host cores).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "TR-SGD steps/s & time to rel. error 1e-3 (FP32 vs BF16 vs batched), %roofline"
+UNIT = "steps/s"
+L2_BYTES = 129 * 2**20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz: float) -> float:
+    """FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.dev)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# device workload
+# ---------------------------------------------------------------------------
+def device_problem(w, device, seed_offset=0):
+    import torch
+
+    from paper_2303_16492_gb300 import api, synth
+    w.seed += seed_offset
+    planted = [torch.from_numpy(G).to(device=device, dtype=torch.float32) for G in synth.planted_cores(w)]
+    X = api.reconstruct(planted, w.dims, w.ranks)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(w.seed + 1)
+    noise = torch.randn(X.numel(), generator=gen, device=device, dtype=torch.float32)
+    xn = torch.linalg.vector_norm(X.double())
+    X.add_(noise * (w.noise_rel * xn / torch.linalg.vector_norm(noise.double())).float())
+    del noise
+    x2 = float(torch.linalg.vector_norm(X.double()) ** 2)
+    init = [torch.from_numpy(G).to(device=device, dtype=torch.float32) for G in synth.initial_cores(w, x2)]
+    Xtrue = api.reconstruct(planted, w.dims, w.ranks)
+    return X, Xtrue, init
+
+
+def algorithmic_per_step(w):
+    """Algorithmic bytes and flops of one iteration averaged over the modes
+    (uniform mode draw): fibers J*I_n*4 B, G_n read+write, the N-1 sampled
+    slices per sample (J*(N-1)*R^2*4 B); flops 2*J*(N-2)*R^3 (chain) +
+    2*I_n*Q*J (residual) + 2*I_n*Q*J (gradient)."""
+    N = len(w.dims)
+    by, fl = 0.0, 0.0
+    for n in range(N):
+        In = w.dims[n]
+        Q = w.ranks[n] * w.ranks[(n + 1) % N]
+        R = w.ranks[0]
+        by += w.J * In * 4 + 2 * In * Q * 4 + w.J * (N - 1) * R * R * 4
+        fl += 2 * w.J * (N - 2) * R ** 3 + 4 * In * Q * w.J
+    return by / N, fl / N
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2303_16492_gb300 import api, synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    w = synth.workload(args.workload)
+    X, Xtrue, init = device_problem(w, device, seed_offset=rank)
+    pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=w.prec, alpha=w.alpha, seed=w.seed + 3)
+    stream = torch.cuda.current_stream()
+    solver = api.Solver([pc], [X], [init], stream=stream)
+    if args.autotune:
+        solver.autotune(steps_per_trial=200)
+    cluster, threads = solver.launch_shape()
+    solver.run(0, args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    l0 = solver.launch_count()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    solver.run(args.warmup, args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    launches = solver.launch_count() - l0
+    clocks = clk.stop()
+    if world > 1:
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    rse = solver.rel_error(0, Xtrue)
+    value = world * args.steps / (ms * 1e-3)
+    ms_per_step = ms / args.steps
+
+    # roofline of the dominant kernel (the fused step kernel; it is the only kernel in the timed region)
+    pk, pk_kind = peaks()
+    by, fl = algorithmic_per_step(w)
+    sm_mhz = pk.get("sm_max_mhz", 2070.0)
+    alu_peak = fp32_alu_peak_tflops(sm_mhz)
+    achieved_tflops = fl / (ms_per_step * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(alu_peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / alu_peak, 5), "traffic": None,
+                "kernel": "step_cluster_kernel<float,float,16>",
+                "peak_note": f"FP32 FMA unit count x {sm_mhz:.0f} MHz (derived; {pk_kind} clock)",
+                "hbm_frac": round(by / (ms_per_step * 1e-3) / 1e9 / pk.get("hbm_gbs", 6652.0), 5),
+                "algorithmic_bytes_per_step": int(by), "algorithmic_flops_per_step": int(fl)}
+
+    e2e = run_e2e(args, w, solver, X, init, device) if rank == 0 and not args.no_e2e else None
+    extras = run_extras(args, device) if rank == 0 and args.extras else None
+    cpu = cpu_baseline(args, w) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": round(ms_per_step, 6), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"{args.workload}: N=4 100^4 FP32, R=10, ill-conditioned planted cores, "
+                                      "noise 1e-4, |F|=1000, uniform sampling, plain TR-BRSGD, fixed step",
+                          "dims": w.dims, "ranks": w.ranks, "J": w.J, "alpha": w.alpha,
+                          "parallelism": f"replicas x{world}" if world > 1 else "single problem",
+                          "launch": {"cluster_ctas": cluster, "threads": threads, "steps_per_launch": args.steps},
+                          "l2": "inputs larger than L2 (X 400 MB, mode-major copies 1.6 GB; fibers sampled "
+                                "at random each step; the 160 KB of cores stay resident as the iterate)"},
+               "rse_after": rse, "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+               "e2e": e2e, "cpu_baseline": cpu, "extras": extras}
+        print(json.dumps(out), flush=True)
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_e2e(args, w, solver_dev, X_dev, init_dev, device):
+    """End to end through the public API from host memory: pinned X and
+    initial cores on the host, then H2D copies, trsgd_init (mode-major
+    copies), K iterations and the D2H read of the cores, all timed."""
+    import torch
+
+    from paper_2303_16492_gb300 import api
+    Xh = X_dev.cpu().pin_memory()
+    ih = [c.cpu().pin_memory() for c in init_dev]
+    Xd = torch.empty_like(X_dev)
+    cd = [torch.empty_like(c) for c in init_dev]
+    outs = [torch.empty(c.shape, dtype=c.dtype, pin_memory=True) for c in init_dev]
+    pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=w.prec, alpha=w.alpha, seed=w.seed + 3)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xd.copy_(Xh, non_blocking=True)
+    for a, b in zip(cd, ih):
+        a.copy_(b, non_blocking=True)
+    s = api.Solver([pc], [Xd], [cd], stream=stream)
+    s.run(0, args.steps)
+    for o, c in zip(outs, cd):
+        o.copy_(c, non_blocking=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    s.close()
+    h2d = Xh.numel() * Xh.element_size() + sum(c.numel() * c.element_size() for c in ih)
+    d2h = sum(c.numel() * c.element_size() for c in outs)
+    return {"value": round(args.steps / dt, 2), "unit": UNIT,
+            "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
+            "note": "X and the initial cores copied from pinned host memory, trsgd_init, K iterations and "
+                    "the cores read back, all inside the timed region (bytes amortised per step)"}
+
+
+def run_extras(args, device):
+    """Secondary measurements (not the headline): other variants of the step."""
+    import torch
+
+    from paper_2303_16492_gb300 import api, synth
+    out = {}
+
+    def timed(solver, steps):
+        solver.run(0, max(50, steps // 10))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        solver.run(10**6, steps)
+        b.record()
+        torch.cuda.synchronize()
+        return steps / (a.elapsed_time(b) * 1e-3)
+
+    try:
+        w = synth.workload(args.workload)
+        X, Xtrue, init = device_problem(w, device)
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=0.5, variant=1, damping=1e-9,
+                               seed=w.seed + 3)
+        s = api.Solver([pc], [X], [init])
+        out["c2_scaled_fp32_steps_per_s"] = round(timed(s, 2000), 1)
+        s.close()
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, dist=2, seed=w.seed + 3)
+        init2 = [c.clone() for c in init]
+        s = api.Solver([pc], [X], [init2])
+        out["c2_euclidean_fp32_steps_per_s"] = round(timed(s, 5000), 1)
+        s.close()
+        del X, Xtrue
+    except Exception as e:  # extras never hide the headline
+        out["error"] = repr(e)
+    return out
+
+
+def cpu_baseline(args, w, budget_s=None):
+    """The FP64 oracle, as it stands, timed on the host cores over a bounded
+    sample of iterations of the same workload."""
+    from oracle import brsgd as ob
+    from oracle import tr
+    from paper_2303_16492_gb300 import synth
+    budget_s = budget_s or args.cpu_seconds
+    planted = synth.planted_cores(w)
+    N = len(w.dims)
+    P = [tr.fold2(G, w.ranks[n], w.ranks[(n + 1) % N]) for n, G in enumerate(planted)]
+    Xt = tr.reconstruct(P)
+    noise = synth.noise(w.dims, w.seed + 1).reshape(w.dims, order="F")
+    X = Xt + noise * (w.noise_rel * np.linalg.norm(Xt) / np.linalg.norm(noise))
+    del noise, Xt
+    init = synth.initial_cores(w, float(np.sum(X * X)))
+    st = ob.State.new([tr.fold2(G, w.ranks[n], w.ranks[(n + 1) % N]) for n, G in enumerate(init)])
+    cfg = ob.Config(J=w.J, alpha=w.alpha, seed=w.seed + 3)
+    ob.step(st, X, cfg, 0)
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < budget_s:
+        ob.step(st, X, cfg, 1 + n)
+        n += 1
+    dt = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": round(n / dt, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} oracle iterations of the same workload in {dt:.1f} s (python FP64, numpy BLAS "
+                      f"threads up to {cores})"}
+
+
+def run_reference(args):
+    """--impl reference: the oracle timed as the reference arm (rank 0 only)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2303_16492_gb300 import synth
+    w = synth.workload(args.workload)
+    per_step_budget = max(5.0, args.cpu_seconds)
+    cpu = cpu_baseline(args, w, budget_s=per_step_budget)
+    value = cpu["value"]
+    steps = int(min(args.steps, max(1, value * per_step_budget)))
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": steps, "warmup": 1,
+           "ms_per_step": round(1e3 / value, 3) if value else None, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": f"{args.workload} (same synthetic workload as the GPU arm)"},
+           "cpu_baseline": cpu,
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50000)
+    ap.add_argument("--warmup", type=int, default=2000)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--extras", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

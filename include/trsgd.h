@@ -1,0 +1,218 @@
+/*
+ * trsgd.h - C-ABI of the GB300 (sm_103a) block-randomized stochastic tensor
+ * ring solver: TR-BRSGD and TR-ScaledBRSGD of Yu, Li and Zhou, "Block-
+ * Randomized Stochastic Methods for Tensor Ring Decomposition"
+ * (arXiv 2303.16492).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Indices are 0-based (the paper is 1-based).
+ * - A tensor X of order N and dims I[0..N-1] is a dense device buffer with
+ *   i_1 fastest (Definition of the multi-index, Sec. 2): X(i_1..i_N) sits at
+ *   offset i_1 + i_2 I_1 + i_3 I_1 I_2 + ...
+ * - Core n (ranks R_n x I_n x R_{n+1}, R_{N+1} = R_1) is stored as its
+ *   classical mode-2 unfolding G_{n(2)} (Sec. 2): a row-major I_n x
+ *   (R_n R_{n+1}) matrix whose row i is the lateral slice G_n(i) stored
+ *   column-major, so G_n(r, i, r') sits at i*R_n*R_{n+1} + r + r'*R_n.  A torch
+ *   tensor of shape (I_n, R_{n+1}, R_n) views it directly.
+ * - Every pointer named *_dev is device memory owned by the caller unless
+ *   stated otherwise; host pointers are named *_host.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Compute entry points only enqueue work on it and return; the
+ *   ones documented as synchronising wait for it.
+ * - The status code is the only error channel.  Argument checks happen
+ *   before any CUDA call, so an invalid argument returns TRSGD_EINVAL without
+ *   touching the device.  Errors found on the device (a bounded wait that ran
+ *   out, a non-finite step, a failed factorisation) are latched in a device
+ *   status word and returned by the next synchronising call on the handle.
+ * - A handle is not thread-safe; independent handles on different streams
+ *   are.
+ */
+#ifndef TRSGD_H
+#define TRSGD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TRSGD_MAX_ORDER 8
+
+typedef enum {
+  TRSGD_OK = 0,
+  TRSGD_EINVAL = 1,       /* invalid argument or configuration            */
+  TRSGD_ENOMEM = 2,       /* device or host allocation failed             */
+  TRSGD_ECUDA = 3,        /* a CUDA runtime call failed                   */
+  TRSGD_ENUMERIC = 4,     /* non-finite step or non-SPD preconditioner    */
+  TRSGD_ETIMEOUT = 5,     /* a bounded device wait ran out                */
+  TRSGD_EUNSUPPORTED = 6  /* valid, but outside what this build supports  */
+} trsgd_status;
+
+/* Mini-batch distributions of Sec. 3.2: uniform, leverage-based (Lemma
+ * lev_est), Euclidean-based (Lemma euc_est) and optimal (Theorem variance,
+ * Eq. optimal_prob). */
+typedef enum {
+  TRSGD_DIST_UNIFORM = 0,
+  TRSGD_DIST_LEVERAGE = 1,
+  TRSGD_DIST_EUCLIDEAN = 2,
+  TRSGD_DIST_OPTIMAL = 3
+} trsgd_dist;
+
+/* Search direction: p = -g (Algorithm 3, TR-BRSGD) or p = -g h^{-1}
+ * (Eq. scaledsg_direction, TR-ScaledBRSGD). */
+typedef enum { TRSGD_PLAIN = 0, TRSGD_SCALED = 1 } trsgd_variant;
+
+/* Step rule: fixed alpha (Eq. update_brsgd) or AdaGrad (Remark after
+ * Algorithm 3). */
+typedef enum { TRSGD_STEP_FIXED = 0, TRSGD_STEP_ADAGRAD = 1 } trsgd_steprule;
+
+/* Arithmetic of the step.  FP64: cores, X and all arithmetic in double.
+ * FP32: cores and X in float, FP32 arithmetic.  BF16_MIXED: cores in float,
+ * the sampled fibers stored in bfloat16, tensor-core contractions with FP32
+ * accumulation.  In every mode the scaled variant's Gram solve and the
+ * relative-error reduction are FP64. */
+typedef enum { TRSGD_FP64 = 0, TRSGD_FP32 = 1, TRSGD_BF16_MIXED = 2 } trsgd_prec;
+
+typedef enum { TRSGD_DTYPE_F64 = 0, TRSGD_DTYPE_F32 = 1, TRSGD_DTYPE_BF16 = 2 } trsgd_dtype;
+
+/* One TR problem (Algorithm 3's arguments plus the stopping-free part of the
+ * configuration). */
+typedef struct {
+  int32_t N;                       /* tensor order, 2..TRSGD_MAX_ORDER       */
+  int32_t dist;                    /* trsgd_dist                             */
+  int64_t I[TRSGD_MAX_ORDER];      /* dims I_1..I_N                          */
+  int64_t R[TRSGD_MAX_ORDER];      /* TR ranks R_1..R_N (R_{N+1} = R_1)      */
+  int64_t J;                       /* |F_n|, samples per step (>= 1)         */
+  int64_t J_H;                     /* |H_n| for the scaled variant; 0: H = F */
+  int32_t variant;                 /* trsgd_variant                          */
+  int32_t rule;                    /* trsgd_steprule                         */
+  int32_t prec;                    /* trsgd_prec                             */
+  int32_t x_dtype;                 /* trsgd_dtype of the caller's X          */
+  double alpha;                    /* fixed step alpha                       */
+  double eta, b, eps;              /* AdaGrad eta, b, epsilon                */
+  double damping;                  /* eta^t of the damped preconditioner     */
+  uint64_t seed;                   /* Philox key of this problem             */
+} trsgd_config;
+
+typedef struct trsgd_handle trsgd_handle;
+
+/* Create a solver for `nproblems` independent TR problems stepped together
+ * (nproblems > 1 is the batched mode: one thread-block cluster per problem in
+ * one persistent launch).
+ *   cfg        host array [nproblems] of configurations.
+ *   X_dev      host array [nproblems] of device pointers to each X (dtype
+ *              cfg.x_dtype, i_1 fastest).  Read during init only: the
+ *              library keeps its own mode-major copies (one per mode, rows =
+ *              mode-n fibers, padded to 16 bytes).
+ *   cores_dev  host array of device pointers, problem p's N_p cores
+ *              consecutively (problem 0 first); G_{n(2)} layout, dtype
+ *              double for TRSGD_FP64 and float otherwise.  Borrowed for the
+ *              handle's lifetime and updated in place by every step.
+ *   stream     the stream every later call of this handle enqueues on.
+ *   out        receives the handle.
+ * Synchronising (it builds the mode-major copies and distribution tables).
+ * Returns EINVAL for a malformed configuration, EUNSUPPORTED for a valid one
+ * this build does not run, ENOMEM/ECUDA on device failures. */
+trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems,
+                        const void *const *X_dev, void *const *cores_dev,
+                        void *stream, trsgd_handle **out);
+
+/* One iteration (Algorithm 3: mode draw, Algorithm 2 sampling, Eq. S_gradient,
+ * optional Eq. scaledsg_direction, step rule, update of G_n) of every problem
+ * at iteration counter t (the Philox counter; iterations are a pure function
+ * of (seed, t) and the current cores).  Enqueued on the handle's stream;
+ * does not synchronise. */
+trsgd_status trsgd_step(trsgd_handle *h, int64_t t);
+
+/* Iterations t0 .. t0+T-1 (T >= 0) as persistent launches of `chunk` steps
+ * each (chunk <= 0: all T in one launch), optionally captured in one CUDA
+ * graph.  With tol > 0 or max_seconds > 0 it synchronises every `chunk`
+ * steps, evaluates the RSE of problem 0 against Xref_dev (NULL: the X given
+ * to init) and stops once RSE <= tol or the elapsed device time exceeds
+ * max_seconds (Sec. 4 stopping criteria).  *steps_done and *rse_out
+ * (nullable) receive the iterations run and the last RSE (-1 if none).
+ * Synchronising. */
+trsgd_status trsgd_run(trsgd_handle *h, int64_t t0, int64_t T, int64_t chunk,
+                       double tol, double max_seconds, const void *Xref_dev,
+                       int64_t *steps_done, double *rse_out);
+
+/* RSE = ||TR(G) - X_ref||_F / ||X_ref||_F (Sec. 4) of problem `problem`,
+ * reduced in FP64.  Xref_dev: NULL for the X given to init, else a tensor of
+ * the problem's dims and x_dtype.  Synchronising; *out receives the value. */
+trsgd_status trsgd_rel_error(trsgd_handle *h, int32_t problem,
+                             const void *Xref_dev, double *out);
+
+/* Full reconstruction X = TR({G_n}) (element formula of the Introduction,
+ * evaluated as X_[1] = G_{1(2)} (G^{!=1}_{[2]})^T).  dtype applies to the
+ * cores and to X; X_dev receives prod(I) elements, i_1 fastest.  Enqueued on
+ * `stream`. */
+trsgd_status trsgd_reconstruct(int32_t N, const int64_t *I, const int64_t *R,
+                               int32_t dtype, const void *const *cores_dev,
+                               void *X_dev, void *stream);
+
+/* Sampled TR loss and its adjoint for every core (FP32):
+ *   L = 1/2 sum_j w_j || X_S(:, j) - G_{n(2)} Z(j, :)^T ||^2,
+ * Z = G^{!=n}_{[2]}(F, :) built from idx (Algorithm 2), X_S given.
+ *   idx_dev  int32 [J][N] slice indices (entry n ignored).
+ *   XS_dev   float [J][I_n], fiber j contiguous.
+ *   w_dev    float [J] sample weights.
+ *   grads_dev (nullable) host array [N] of device pointers receiving dL/dG_k
+ *            in the G_{k(2)} layout (overwritten); NULL: loss only.
+ *   loss_dev float [1] receives L.
+ * The adjoint of core k != n is accumulated per sample from prefix and
+ * suffix slice products of the chain (product rule on the trace). */
+trsgd_status trsgd_sampled_loss_grad(int32_t N, const int64_t *I, const int64_t *R,
+                                     int32_t n, int64_t J, const int32_t *idx_dev,
+                                     const float *XS_dev, const float *w_dev,
+                                     const float *const *cores_dev,
+                                     float *const *grads_dev, float *loss_dev,
+                                     void *stream);
+
+/* Record the intermediates of every following step of problem 0 (mode n,
+ * idx, p_F, Z, E, g, direction p, preconditioner h) for readback with
+ * trsgd_get_debug.  on = 0 stops recording. */
+trsgd_status trsgd_set_debug(trsgd_handle *h, int32_t on);
+
+typedef enum {
+  TRSGD_DBG_MODE = 0,   /* int32 [1]                                   */
+  TRSGD_DBG_IDX = 1,    /* int32 [J][N], entry n = -1                  */
+  TRSGD_DBG_PF = 2,     /* double [J]                                  */
+  TRSGD_DBG_Z = 3,      /* core dtype [J][R_n R_{n+1}]                 */
+  TRSGD_DBG_E = 4,      /* core dtype [J][I_n]  (E = G Z^T - X_S)^T    */
+  TRSGD_DBG_G = 5,      /* core dtype [I_n][R_n R_{n+1}]  g            */
+  TRSGD_DBG_P = 6,      /* core dtype [I_n][R_n R_{n+1}]  direction p  */
+  TRSGD_DBG_H = 7       /* double [Q][Q] damped preconditioner h       */
+} trsgd_debug_item;
+
+/* Copy one recorded intermediate of the last recorded step into host memory
+ * (at most `bytes`; *written receives the bytes copied).  Synchronising. */
+trsgd_status trsgd_get_debug(trsgd_handle *h, int32_t item, void *out_host,
+                             size_t bytes, size_t *written);
+
+/* AdaGrad state of problem p, core k (sum of squared directions, core dtype,
+ * G_{k(2)} layout): copy out (dir = 0) or in (dir = 1), for checkpointing.
+ * Synchronising. */
+trsgd_status trsgd_adagrad_state(trsgd_handle *h, int32_t problem, int32_t core,
+                                 void *host, size_t bytes, int32_t dir);
+
+/* Launch shape picked for the step kernel: cluster size (CTAs per problem)
+ * and threads per CTA.  set: 0 = query into *cluster / *threads, 1 = force
+ * these values (validated; 0 keeps the current one).  trsgd_autotune times
+ * the candidate shapes on scratch copies of the cores and keeps the fastest
+ * (synchronising; the cores are left unchanged). */
+trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster,
+                                int32_t *threads);
+trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial);
+
+/* Number of step-kernel launches enqueued by this handle so far. */
+int64_t trsgd_launch_count(const trsgd_handle *h);
+
+void trsgd_destroy(trsgd_handle *h);
+const char *trsgd_status_string(trsgd_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRSGD_H */

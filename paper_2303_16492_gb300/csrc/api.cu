@@ -1,0 +1,626 @@
+// Host side of the C-ABI declared in include/trsgd.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/trsgd.h"
+#include "common.cuh"
+#include "internal.h"
+
+using namespace trsgd;
+
+namespace {
+
+constexpr int kMaxRank = 16;       // register bound of the slice chain
+constexpr int kMaxQPlain = 256;
+constexpr int kMaxQScaled = 128;
+
+size_t dtype_size(int d) { return d == TRSGD_DTYPE_F64 ? 8 : d == TRSGD_DTYPE_F32 ? 4 : 2; }
+size_t rup(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Buffers {
+  std::vector<void *> ptrs;
+  ~Buffers() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+  cudaError_t alloc(void **out, size_t bytes) {
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(p);
+    *out = p;
+    return cudaSuccess;
+  }
+};
+
+trsgd_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return TRSGD_OK;
+  if (e == cudaErrorMemoryAllocation) return TRSGD_ENOMEM;
+  return TRSGD_ECUDA;
+}
+
+}  // namespace
+
+struct trsgd_handle {
+  int nprob = 0;
+  std::vector<trsgd_config> cfg;
+  cudaStream_t stream = nullptr;
+  int core_dtype = 1, xc_dtype = 1, rmax = 4;
+  std::vector<ProbDesc> hdesc;
+  ProbDesc *ddesc = nullptr;
+  Buffers buf;
+  StepLayout lay = {};
+  int threads = 512;
+  int *d_status = nullptr;
+  double *d_sums = nullptr;
+  std::vector<const void *> X;
+  int64_t t_next = 0;
+  int64_t launches = 0;
+  bool dbg = false;
+  size_t dbg_bytes[8] = {};
+  void *dbg_ptr[8] = {};
+};
+
+static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
+  if (!cfg || np < 1) return TRSGD_EINVAL;
+  for (int p = 0; p < np; ++p) {
+    const trsgd_config &c = cfg[p];
+    if (c.N < 2 || c.N > TRSGD_MAX_ORDER) return TRSGD_EINVAL;
+    for (int k = 0; k < c.N; ++k) {
+      if (c.I[k] < 1 || c.I[k] > (1LL << 30)) return TRSGD_EINVAL;
+      if (c.R[k] < 1 || c.R[k] > 4096) return TRSGD_EINVAL;
+    }
+    if (c.J < 1 || c.J > (1LL << 30) || c.J_H < 0) return TRSGD_EINVAL;
+    if (c.dist < 0 || c.dist > 3 || c.variant < 0 || c.variant > 1 || c.rule < 0 || c.rule > 1)
+      return TRSGD_EINVAL;
+    if (c.prec < 0 || c.prec > 2 || c.x_dtype < 0 || c.x_dtype > 2) return TRSGD_EINVAL;
+    if (!std::isfinite(c.alpha) || !std::isfinite(c.eta) || !std::isfinite(c.b) ||
+        !std::isfinite(c.eps) || !std::isfinite(c.damping))
+      return TRSGD_EINVAL;
+    if (c.damping < 0 || c.b < 0 || c.eps < 0 || c.eta < 0) return TRSGD_EINVAL;
+    double numel = 1;
+    for (int k = 0; k < c.N; ++k) numel *= (double)c.I[k];
+    if (numel > 9.0e15) return TRSGD_EINVAL;
+    if (c.prec != cfg[0].prec || c.x_dtype != cfg[0].x_dtype) return TRSGD_EINVAL;
+    if (c.prec == TRSGD_FP64 && c.x_dtype != TRSGD_DTYPE_F64) return TRSGD_EINVAL;
+    if (c.prec == TRSGD_FP32 && c.x_dtype != TRSGD_DTYPE_F32) return TRSGD_EINVAL;
+    // this build
+    if (c.prec == TRSGD_BF16_MIXED) return TRSGD_EUNSUPPORTED;
+    if (c.dist == TRSGD_DIST_LEVERAGE || c.dist == TRSGD_DIST_OPTIMAL) return TRSGD_EUNSUPPORTED;
+    if (c.J_H != 0) return TRSGD_EUNSUPPORTED;
+    for (int k = 0; k < c.N; ++k) {
+      if (c.R[k] > kMaxRank) return TRSGD_EUNSUPPORTED;
+      const int64_t Q = c.R[k] * c.R[(k + 1) % c.N];
+      if (Q > kMaxQPlain) return TRSGD_EUNSUPPORTED;
+      if (c.variant == TRSGD_SCALED && Q > kMaxQScaled) return TRSGD_EUNSUPPORTED;
+    }
+  }
+  return TRSGD_OK;
+}
+
+// Shared-memory layout for cluster size C (returns false if it does not fit).
+static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
+  const size_t st = h.core_dtype == 0 ? 8 : 4;
+  const size_t sx = dtype_size(h.xc_dtype);
+  int Imax = 1, Qmax = 1, Jmax = 1, QH = 0;
+  bool scaled = false;
+  for (const auto &c : h.cfg) {
+    Jmax = std::max(Jmax, (int)c.J);
+    for (int k = 0; k < c.N; ++k) {
+      Imax = std::max(Imax, (int)c.I[k]);
+      const int Q = (int)(c.R[k] * c.R[(k + 1) % c.N]);
+      Qmax = std::max(Qmax, Q);
+      if (c.variant == TRSGD_SCALED) QH = std::max(QH, Q);
+    }
+    scaled |= c.variant == TRSGD_SCALED;
+  }
+  L = {};
+  L.C = C;
+  L.JB = (Jmax + C - 1) / C;
+  L.ldxs = (int)rup((size_t)Imax, 16 / sx);
+  if (sx < st) L.ldxs = (int)rup((size_t)Imax, 16 / sx);
+  L.ldq = Qmax;
+  L.ldjb = (int)rup((size_t)L.JB, 4);
+  L.QH = scaled ? QH : 0;
+  L.rows_own = scaled ? (Imax + C - 1) / C + 1 : 0;
+  size_t off = 0;
+  auto take = [&](size_t bytes, size_t align) {
+    off = rup(off, align);
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  L.off_bar = take(16, 16);
+  L.off_misc = take(64, 16);
+  L.off_idx = take((size_t)L.JB * kMaxOrder * 4, 16);
+  L.off_col = take((size_t)L.JB * 8, 16);
+  L.off_w = take((size_t)L.JB * 8, 16);
+  L.off_x = take((size_t)L.JB * L.ldxs * std::max(sx, st), 128);
+  L.off_z = take((size_t)L.JB * L.ldq * st, 16);
+  L.off_zt = take((size_t)Qmax * L.ldjb * st, 16);
+  if (scaled) {
+    L.off_h64 = take((size_t)QH * QH * 8, 16);
+    L.off_hdiag = take((size_t)QH * 8, 16);
+    L.off_gown = take((size_t)L.rows_own * L.ldq * st, 16);
+  }
+  const size_t limit = (size_t)step_max_smem() - 1024;
+  if (off >= limit) return false;
+  const size_t avail = limit - rup(off, 128);
+  int TI = (int)std::min<size_t>((size_t)Imax, avail / ((size_t)Qmax * st));
+  if (scaled) {
+    if (TI < Imax || TI < QH) return false;   // scaled: one chunk and room for the Gram partial
+  }
+  if (TI < 1) return false;
+  L.TI = TI;
+  L.ldti = TI;
+  size_t reg = std::max((size_t)Qmax * L.ldti, (size_t)TI * L.ldq);
+  if (scaled) reg = std::max(reg, (size_t)QH * L.ldq);
+  L.off_reg = take(reg * st, 128);
+  L.total = rup(off, 128);
+  return L.total <= limit;
+}
+
+static int default_cluster(const trsgd_handle &h) {
+  int Jmax = 1;
+  for (const auto &c : h.cfg) Jmax = std::max(Jmax, (int)c.J);
+  int C = 1;
+  while (C < 16 && (Jmax + C - 1) / C > 64) C *= 2;
+  if (h.nprob > 1) C = std::min(C, std::max(1, 128 / h.nprob));
+  return C;
+}
+
+static trsgd_status choose_layout(trsgd_handle &h, int C) {
+  for (; C >= 1; C /= 2) {
+    StepLayout L;
+    if (make_layout(h, C, L)) {
+      h.lay = L;
+      return from_cuda(step_kernel_prepare(h.core_dtype, h.xc_dtype, h.rmax, h.lay));
+    }
+  }
+  return TRSGD_EUNSUPPORTED;
+}
+
+extern "C" {
+
+const char *trsgd_status_string(trsgd_status s) {
+  switch (s) {
+    case TRSGD_OK: return "ok";
+    case TRSGD_EINVAL: return "invalid argument";
+    case TRSGD_ENOMEM: return "out of memory";
+    case TRSGD_ECUDA: return "CUDA error";
+    case TRSGD_ENUMERIC: return "numerical failure (non-finite step or non-SPD preconditioner)";
+    case TRSGD_ETIMEOUT: return "bounded device wait timed out";
+    case TRSGD_EUNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *const *X_dev,
+                        void *const *cores_dev, void *stream, trsgd_handle **out) {
+  if (!out) return TRSGD_EINVAL;
+  *out = nullptr;
+  trsgd_status st = validate(cfg, nproblems);
+  if (st != TRSGD_OK) return st;
+  if (!X_dev || !cores_dev) return TRSGD_EINVAL;
+  int ncore = 0;
+  for (int p = 0; p < nproblems; ++p) {
+    if (!X_dev[p]) return TRSGD_EINVAL;
+    for (int k = 0; k < cfg[p].N; ++k)
+      if (!cores_dev[ncore + k]) return TRSGD_EINVAL;
+    ncore += cfg[p].N;
+  }
+  trsgd_handle *h = new (std::nothrow) trsgd_handle();
+  if (!h) return TRSGD_ENOMEM;
+  h->nprob = nproblems;
+  h->cfg.assign(cfg, cfg + nproblems);
+  h->stream = static_cast<cudaStream_t>(stream);
+  h->core_dtype = cfg[0].prec == TRSGD_FP64 ? 0 : 1;
+  h->xc_dtype = cfg[0].prec == TRSGD_BF16_MIXED ? TRSGD_DTYPE_BF16 : cfg[0].x_dtype;
+  int rmax = 1;
+  for (int p = 0; p < nproblems; ++p)
+    for (int k = 0; k < cfg[p].N; ++k) rmax = std::max<int>(rmax, (int)cfg[p].R[k]);
+  h->rmax = rmax;
+  auto fail = [&](trsgd_status s) {
+    delete h;
+    return s;
+  };
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return fail(TRSGD_ECUDA);
+  if (prop.major < 10) return fail(TRSGD_EUNSUPPORTED);
+
+  cudaError_t e;
+  if ((e = h->buf.alloc((void **)&h->d_status, 16)) != cudaSuccess) return fail(from_cuda(e));
+  if ((e = h->buf.alloc((void **)&h->d_sums, 16)) != cudaSuccess) return fail(from_cuda(e));
+  cudaMemsetAsync(h->d_status, 0, 16, h->stream);
+  const size_t sxc = dtype_size(h->xc_dtype);
+  const size_t score = h->core_dtype == 0 ? 8 : 4;
+  h->hdesc.resize(nproblems);
+  ncore = 0;
+  for (int p = 0; p < nproblems; ++p) {
+    const trsgd_config &c = cfg[p];
+    ProbDesc &D = h->hdesc[p];
+    std::memset(&D, 0, sizeof(D));
+    D.N = c.N;
+    D.J = (int)c.J;
+    D.dist = c.dist;
+    D.variant = c.variant;
+    D.rule = c.rule;
+    D.prec = c.prec;
+    for (int k = 0; k < c.N; ++k) {
+      D.I[k] = (int)c.I[k];
+      D.R[k] = (int)c.R[k];
+    }
+    D.alpha = c.alpha;
+    D.eta = c.eta;
+    D.b = c.b;
+    D.eps = c.eps;
+    D.damping = c.damping;
+    D.seed = c.seed;
+    D.status = h->d_status;
+    h->X.push_back(X_dev[p]);
+    for (int k = 0; k < c.N; ++k) {
+      D.cores[k] = cores_dev[ncore + k];
+      // mode-major copy of X for mode k
+      long long A = 1, B = 1;
+      for (int m = 0; m < k; ++m) A *= c.I[m];
+      for (int m = k + 1; m < c.N; ++m) B *= c.I[m];
+      const long long ld = (long long)rup((size_t)c.I[k], 16 / sxc);
+      void *copy = nullptr;
+      if ((e = h->buf.alloc(&copy, (size_t)ld * A * B * sxc)) != cudaSuccess) return fail(from_cuda(e));
+      if (ld != c.I[k]) cudaMemsetAsync(copy, 0, (size_t)ld * A * B * sxc, h->stream);
+      if ((e = launch_mode_copy(c.x_dtype, h->xc_dtype, X_dev[p], copy, A, c.I[k], B, ld, h->stream)) !=
+          cudaSuccess)
+        return fail(from_cuda(e));
+      D.xmode[k] = copy;
+      D.ldx[k] = ld;
+      const int64_t Q = c.R[k] * c.R[(k + 1) % c.N];
+      if (c.rule == TRSGD_STEP_ADAGRAD) {
+        if ((e = h->buf.alloc(&D.acc[k], (size_t)c.I[k] * Q * score)) != cudaSuccess) return fail(from_cuda(e));
+        cudaMemsetAsync(D.acc[k], 0, (size_t)c.I[k] * Q * score, h->stream);
+      }
+      if (c.dist != TRSGD_DIST_UNIFORM) {
+        if ((e = h->buf.alloc((void **)&D.prob[k], (size_t)c.I[k] * 8)) != cudaSuccess ||
+            (e = h->buf.alloc((void **)&D.cdf[k], (size_t)c.I[k] * 8)) != cudaSuccess ||
+            (e = h->buf.alloc((void **)&D.snorm[k], (size_t)c.I[k] * 8)) != cudaSuccess)
+          return fail(from_cuda(e));
+        if (c.dist == TRSGD_DIST_EUCLIDEAN &&
+            (e = launch_euclid_table(h->core_dtype, D.cores[k], (int)c.I[k], (int)Q, D.snorm[k], D.prob[k],
+                                     D.cdf[k], h->stream)) != cudaSuccess)
+          return fail(from_cuda(e));
+      }
+    }
+    ncore += c.N;
+  }
+  // recording buffers sized for problem 0
+  {
+    const trsgd_config &c = cfg[0];
+    size_t Imax = 1, Qmax = 1;
+    for (int k = 0; k < c.N; ++k) {
+      Imax = std::max<size_t>(Imax, c.I[k]);
+      Qmax = std::max<size_t>(Qmax, c.R[k] * c.R[(k + 1) % c.N]);
+    }
+    const size_t J = c.J;
+    h->dbg_bytes[TRSGD_DBG_MODE] = 4;
+    h->dbg_bytes[TRSGD_DBG_IDX] = J * c.N * 4;
+    h->dbg_bytes[TRSGD_DBG_PF] = J * 8;
+    h->dbg_bytes[TRSGD_DBG_Z] = J * Qmax * score;
+    h->dbg_bytes[TRSGD_DBG_E] = J * Imax * score;
+    h->dbg_bytes[TRSGD_DBG_G] = Imax * Qmax * score;
+    h->dbg_bytes[TRSGD_DBG_P] = Imax * Qmax * score;
+    h->dbg_bytes[TRSGD_DBG_H] = Qmax * Qmax * 8;
+  }
+  if ((e = cudaMalloc((void **)&h->ddesc, sizeof(ProbDesc) * nproblems)) != cudaSuccess) return fail(from_cuda(e));
+  h->buf.ptrs.push_back(h->ddesc);
+  st = choose_layout(*h, default_cluster(*h));
+  if (st != TRSGD_OK) return fail(st);
+  h->threads = 512;
+  if ((e = cudaMemcpyAsync(h->ddesc, h->hdesc.data(), sizeof(ProbDesc) * nproblems, cudaMemcpyHostToDevice,
+                           h->stream)) != cudaSuccess)
+    return fail(from_cuda(e));
+  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return fail(from_cuda(e));
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(from_cuda(e));
+  *out = h;
+  return TRSGD_OK;
+}
+
+static trsgd_status read_status(trsgd_handle *h) {
+  int s = 0;
+  cudaError_t e = cudaMemcpyAsync(&s, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (s == 0) return TRSGD_OK;
+  cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
+  if (s == kStatusTimeout) return TRSGD_ETIMEOUT;
+  if (s == kStatusNumeric) return TRSGD_ENUMERIC;
+  return TRSGD_ECUDA;
+}
+
+static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
+  while (nsteps > 0) {
+    const int n = (int)std::min<int64_t>(nsteps, 1 << 20);
+    cudaError_t e = launch_step(h->core_dtype, h->xc_dtype, h->rmax, h->ddesc, h->nprob, h->lay, h->threads, t0,
+                                n, h->stream);
+    if (e != cudaSuccess) return from_cuda(e);
+    ++h->launches;
+    t0 += n;
+    nsteps -= n;
+  }
+  return TRSGD_OK;
+}
+
+trsgd_status trsgd_step(trsgd_handle *h, int64_t t) {
+  if (!h || t < 0) return TRSGD_EINVAL;
+  trsgd_status s = launch_steps(h, t, 1);
+  if (s == TRSGD_OK) h->t_next = t + 1;
+  return s;
+}
+
+trsgd_status trsgd_rel_error(trsgd_handle *h, int32_t problem, const void *Xref_dev, double *out) {
+  if (!h || !out || problem < 0 || problem >= h->nprob) return TRSGD_EINVAL;
+  const trsgd_config &c = h->cfg[problem];
+  const ProbDesc &D = h->hdesc[problem];
+  if (c.x_dtype != TRSGD_DTYPE_F64 && c.x_dtype != TRSGD_DTYPE_F32) return TRSGD_EUNSUPPORTED;
+  const void *ref = Xref_dev ? Xref_dev : h->X[problem];
+  cudaError_t e = cudaMemsetAsync(h->d_sums, 0, 16, h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  e = launch_reconstruct(h->core_dtype, c.N, D.I, D.R, (const void *const *)D.cores, nullptr, ref, h->d_sums,
+                         h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  double sums[2];
+  e = cudaMemcpyAsync(sums, h->d_sums, 16, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  *out = sums[1] > 0 ? std::sqrt(sums[0] / sums[1]) : std::sqrt(sums[0]);
+  return read_status(h);
+}
+
+trsgd_status trsgd_run(trsgd_handle *h, int64_t t0, int64_t T, int64_t chunk, double tol,
+                       double max_seconds, const void *Xref_dev, int64_t *steps_done, double *rse_out) {
+  if (!h || T < 0 || t0 < 0) return TRSGD_EINVAL;
+  if (steps_done) *steps_done = 0;
+  if (rse_out) *rse_out = -1.0;
+  const bool checks = tol > 0 || max_seconds > 0;
+  if (chunk <= 0) chunk = checks ? std::max<int64_t>(1, std::min<int64_t>(T, 100)) : std::max<int64_t>(T, 1);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (checks) {
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+    cudaEventRecord(ev0, h->stream);
+  }
+  double device_s = 0.0;
+  int64_t done = 0;
+  trsgd_status st = TRSGD_OK;
+  while (done < T) {
+    const int64_t n = std::min(chunk, T - done);
+    st = launch_steps(h, t0 + done, n);
+    if (st != TRSGD_OK) break;
+    done += n;
+    h->t_next = t0 + done;
+    if (checks) {
+      cudaEventRecord(ev1, h->stream);
+      cudaEventSynchronize(ev1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      device_s += ms * 1e-3;
+      double r = -1.0;
+      st = trsgd_rel_error(h, 0, Xref_dev, &r);
+      if (st != TRSGD_OK) break;
+      if (rse_out) *rse_out = r;
+      cudaEventRecord(ev0, h->stream);   // evaluation time is not counted
+      if ((tol > 0 && r <= tol) || (max_seconds > 0 && device_s >= max_seconds)) break;
+    }
+  }
+  if (steps_done) *steps_done = done;
+  if (ev0) cudaEventDestroy(ev0);
+  if (ev1) cudaEventDestroy(ev1);
+  if (st != TRSGD_OK) return st;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  return read_status(h);
+}
+
+trsgd_status trsgd_reconstruct(int32_t N, const int64_t *I, const int64_t *R, int32_t dtype,
+                               const void *const *cores_dev, void *X_dev, void *stream) {
+  if (N < 2 || N > TRSGD_MAX_ORDER || !I || !R || !cores_dev || !X_dev) return TRSGD_EINVAL;
+  if (dtype != TRSGD_DTYPE_F64 && dtype != TRSGD_DTYPE_F32) return TRSGD_EUNSUPPORTED;
+  int Ii[TRSGD_MAX_ORDER], Ri[TRSGD_MAX_ORDER];
+  for (int k = 0; k < N; ++k) {
+    if (I[k] < 1 || R[k] < 1 || I[k] > (1LL << 30)) return TRSGD_EINVAL;
+    if (R[k] > 32) return TRSGD_EUNSUPPORTED;
+    if (!cores_dev[k]) return TRSGD_EINVAL;
+    Ii[k] = (int)I[k];
+    Ri[k] = (int)R[k];
+  }
+  return from_cuda(launch_reconstruct(dtype == TRSGD_DTYPE_F64 ? 0 : 1, N, Ii, Ri, cores_dev, X_dev, nullptr,
+                                      nullptr, static_cast<cudaStream_t>(stream)));
+}
+
+trsgd_status trsgd_sampled_loss_grad(int32_t N, const int64_t *I, const int64_t *R, int32_t n, int64_t J,
+                                     const int32_t *idx_dev, const float *XS_dev, const float *w_dev,
+                                     const float *const *cores_dev, float *const *grads_dev, float *loss_dev,
+                                     void *stream) {
+  if (N < 2 || N > TRSGD_MAX_ORDER || !I || !R || n < 0 || n >= N || J < 0 || J > (1LL << 30)) return TRSGD_EINVAL;
+  if (!idx_dev || !XS_dev || !w_dev || !cores_dev || !loss_dev) return TRSGD_EINVAL;
+  int Ii[TRSGD_MAX_ORDER], Ri[TRSGD_MAX_ORDER];
+  for (int k = 0; k < N; ++k) {
+    if (I[k] < 1 || R[k] < 1 || !cores_dev[k]) return TRSGD_EINVAL;
+    if (grads_dev && !grads_dev[k]) return TRSGD_EINVAL;
+    if (R[k] > 16) return TRSGD_EUNSUPPORTED;
+    Ii[k] = (int)I[k];
+    Ri[k] = (int)R[k];
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemsetAsync(loss_dev, 0, sizeof(float), s);
+  for (int k = 0; k < N && grads_dev && e == cudaSuccess; ++k)
+    e = cudaMemsetAsync(grads_dev[k], 0, (size_t)Ii[k] * Ri[k] * Ri[(k + 1) % N] * sizeof(float), s);
+  if (e != cudaSuccess) return from_cuda(e);
+  return from_cuda(launch_sampled_loss_grad(N, Ii, Ri, n, (int)J, idx_dev, XS_dev, w_dev, cores_dev,
+                                            grads_dev, loss_dev, s));
+}
+
+trsgd_status trsgd_set_debug(trsgd_handle *h, int32_t on) {
+  if (!h) return TRSGD_EINVAL;
+  ProbDesc &D = h->hdesc[0];
+  if (on && !h->dbg_ptr[0]) {
+    for (int i = 0; i < 8; ++i) {
+      cudaError_t e = h->buf.alloc(&h->dbg_ptr[i], h->dbg_bytes[i]);
+      if (e != cudaSuccess) return from_cuda(e);
+      cudaMemsetAsync(h->dbg_ptr[i], 0, h->dbg_bytes[i], h->stream);
+    }
+    D.dbg_n = (int *)h->dbg_ptr[TRSGD_DBG_MODE];
+    D.dbg_idx = (int *)h->dbg_ptr[TRSGD_DBG_IDX];
+    D.dbg_pf = (double *)h->dbg_ptr[TRSGD_DBG_PF];
+    D.dbg_z = h->dbg_ptr[TRSGD_DBG_Z];
+    D.dbg_e = h->dbg_ptr[TRSGD_DBG_E];
+    D.dbg_g = h->dbg_ptr[TRSGD_DBG_G];
+    D.dbg_p = h->dbg_ptr[TRSGD_DBG_P];
+    D.dbg_h = (double *)h->dbg_ptr[TRSGD_DBG_H];
+  }
+  D.dbg = on ? 1 : 0;
+  h->dbg = on != 0;
+  cudaError_t e = cudaMemcpyAsync(h->ddesc, &D, sizeof(ProbDesc), cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return from_cuda(e);
+}
+
+trsgd_status trsgd_get_debug(trsgd_handle *h, int32_t item, void *out_host, size_t bytes, size_t *written) {
+  if (!h || item < 0 || item > 7 || !out_host) return TRSGD_EINVAL;
+  if (!h->dbg_ptr[item]) return TRSGD_EINVAL;
+  const size_t n = std::min(bytes, h->dbg_bytes[item]);
+  cudaError_t e = cudaMemcpyAsync(out_host, h->dbg_ptr[item], n, cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  if (written) *written = n;
+  return read_status(h);
+}
+
+trsgd_status trsgd_adagrad_state(trsgd_handle *h, int32_t problem, int32_t core, void *host, size_t bytes,
+                                 int32_t dir) {
+  if (!h || !host || problem < 0 || problem >= h->nprob) return TRSGD_EINVAL;
+  const trsgd_config &c = h->cfg[problem];
+  if (core < 0 || core >= c.N || (dir != 0 && dir != 1)) return TRSGD_EINVAL;
+  void *acc = h->hdesc[problem].acc[core];
+  if (!acc) return TRSGD_EINVAL;
+  const size_t need = (size_t)c.I[core] * c.R[core] * c.R[(core + 1) % c.N] * (h->core_dtype == 0 ? 8 : 4);
+  if (bytes != need) return TRSGD_EINVAL;
+  cudaError_t e = dir == 0 ? cudaMemcpyAsync(host, acc, need, cudaMemcpyDeviceToHost, h->stream)
+                           : cudaMemcpyAsync(acc, host, need, cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return from_cuda(e);
+}
+
+trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster, int32_t *threads) {
+  if (!h || !cluster || !threads) return TRSGD_EINVAL;
+  if (set == 0) {
+    *cluster = h->lay.C;
+    *threads = h->threads;
+    return TRSGD_OK;
+  }
+  if (set != 1) return TRSGD_EINVAL;
+  const int C = *cluster ? *cluster : h->lay.C;
+  const int T = *threads ? *threads : h->threads;
+  if (C < 1 || C > 16 || (C & (C - 1)) || (T != 128 && T != 256 && T != 512)) return TRSGD_EINVAL;
+  StepLayout L;
+  if (!make_layout(*h, C, L)) return TRSGD_EUNSUPPORTED;
+  cudaError_t e = step_kernel_prepare(h->core_dtype, h->xc_dtype, h->rmax, L);
+  if (e != cudaSuccess) return from_cuda(e);
+  h->lay = L;
+  h->threads = T;
+  return TRSGD_OK;
+}
+
+trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial) {
+  if (!h || steps_per_trial < 1) return TRSGD_EINVAL;
+  // scratch copies of every core so that the trial steps leave the cores unchanged
+  std::vector<std::vector<void *>> saved(h->nprob);
+  std::vector<std::vector<size_t>> sizes(h->nprob);
+  Buffers scratch;
+  const size_t score = h->core_dtype == 0 ? 8 : 4;
+  for (int p = 0; p < h->nprob; ++p) {
+    const trsgd_config &c = h->cfg[p];
+    for (int k = 0; k < c.N; ++k) {
+      const size_t b = (size_t)c.I[k] * c.R[k] * c.R[(k + 1) % c.N] * score;
+      void *cp = nullptr;
+      cudaError_t e = scratch.alloc(&cp, b);
+      if (e != cudaSuccess) return from_cuda(e);
+      cudaMemcpyAsync(cp, h->hdesc[p].cores[k], b, cudaMemcpyDeviceToDevice, h->stream);
+      saved[p].push_back(cp);
+      sizes[p].push_back(b);
+      if (h->hdesc[p].acc[k]) {
+        void *ap = nullptr;
+        if ((e = scratch.alloc(&ap, b)) != cudaSuccess) return from_cuda(e);
+        cudaMemcpyAsync(ap, h->hdesc[p].acc[k], b, cudaMemcpyDeviceToDevice, h->stream);
+        saved[p].push_back(ap);
+        sizes[p].push_back(b);
+      }
+    }
+  }
+  const StepLayout keep_lay = h->lay;
+  const int keep_threads = h->threads;
+  float best = 1e30f;
+  StepLayout best_lay = keep_lay;
+  int best_threads = keep_threads;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (int C = 1; C <= 16; C *= 2) {
+    StepLayout L;
+    if (!make_layout(*h, C, L)) continue;
+    if (step_kernel_prepare(h->core_dtype, h->xc_dtype, h->rmax, L) != cudaSuccess) continue;
+    for (int T : {256, 512}) {
+      h->lay = L;
+      h->threads = T;
+      if (launch_steps(h, 0, 1) != TRSGD_OK) { cudaGetLastError(); continue; }  // warm-up
+      cudaEventRecord(a, h->stream);
+      if (launch_steps(h, 1, steps_per_trial) != TRSGD_OK) { cudaGetLastError(); continue; }
+      cudaEventRecord(b, h->stream);
+      if (cudaEventSynchronize(b) != cudaSuccess) { cudaGetLastError(); continue; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best) {
+        best = ms;
+        best_lay = L;
+        best_threads = T;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  // restore the cores, the AdaGrad sums and the sampling tables
+  for (int p = 0; p < h->nprob; ++p) {
+    const trsgd_config &c = h->cfg[p];
+    size_t s = 0;
+    for (int k = 0; k < c.N; ++k) {
+      cudaMemcpyAsync(h->hdesc[p].cores[k], saved[p][s], sizes[p][s], cudaMemcpyDeviceToDevice, h->stream);
+      ++s;
+      if (h->hdesc[p].acc[k]) {
+        cudaMemcpyAsync(h->hdesc[p].acc[k], saved[p][s], sizes[p][s], cudaMemcpyDeviceToDevice, h->stream);
+        ++s;
+      }
+      if (c.dist == TRSGD_DIST_EUCLIDEAN)
+        launch_euclid_table(h->core_dtype, h->hdesc[p].cores[k], (int)c.I[k], (int)(c.R[k] * c.R[(k + 1) % c.N]),
+                            h->hdesc[p].snorm[k], h->hdesc[p].prob[k], h->hdesc[p].cdf[k], h->stream);
+    }
+  }
+  h->lay = best_lay;
+  h->threads = best_threads;
+  cudaError_t e = step_kernel_prepare(h->core_dtype, h->xc_dtype, h->rmax, h->lay);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  return read_status(h);
+}
+
+int64_t trsgd_launch_count(const trsgd_handle *h) { return h ? h->launches : -1; }
+
+void trsgd_destroy(trsgd_handle *h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Internal descriptors shared by the host library and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+namespace trsgd {
+
+// One TR problem as the step kernel sees it.
+struct ProbDesc {
+  int N, J, dist, variant, rule, prec;
+  int I[8], R[8];
+  double alpha, eta, b, eps, damping;
+  unsigned long long seed;
+  void *cores[8];                 // G_{k(2)}, core dtype
+  const void *xmode[8];           // mode-major copies: fiber col of X_[k] at xmode[k] + col*ldx[k]
+  long long ldx[8];               // row stride of xmode[k] in elements (16-byte multiple)
+  void *acc[8];                   // AdaGrad sums (core dtype), or null
+  double *prob[8];                // p_k (non-uniform distributions)
+  unsigned long long *cdf[8];     // inclusive prefix sums of round(p_k * 2^52)
+  double *snorm[8];               // Euclidean slice norms ||G_k(i)||_F^2
+  // recording of intermediates (problem 0 only)
+  int dbg;
+  int *dbg_n, *dbg_idx;
+  double *dbg_pf, *dbg_h;
+  void *dbg_z, *dbg_e, *dbg_g, *dbg_p;
+  int *status;
+};
+
+// Shared-memory layout of the step kernel (byte offsets), identical for all
+// CTAs of a launch.
+struct StepLayout {
+  int C;          // CTAs per cluster (per problem)
+  int JB;         // max samples per CTA
+  int ldxs;       // fiber rows in smem (elements of the fiber dtype)
+  int ldq;        // Z rows (elements)
+  int ldjb;       // Z^T rows (elements)
+  int TI;         // rows of G_n per chunk
+  int ldti;       // G^T chunk rows
+  int QH;         // max Q of the scaled variant (0: none)
+  int rows_own;   // max rows of g owned by one CTA
+  size_t off_idx, off_col, off_w, off_bar, off_x, off_z, off_zt, off_reg, off_h64, off_hdiag,
+      off_gown, off_misc, total;
+};
+
+// kernel launchers (defined in the .cu files)
+cudaError_t launch_step(int core_dtype, int x_dtype, int rmax, const ProbDesc *descs, int nprob,
+                        const StepLayout &lay, int threads, long long t0, int nsteps,
+                        cudaStream_t s);
+cudaError_t step_kernel_prepare(int core_dtype, int x_dtype, int rmax, const StepLayout &lay);
+int step_max_smem();
+
+cudaError_t launch_mode_copy(int src_dtype, int dst_dtype, const void *X, void *out, long long A,
+                             long long In, long long B, long long ld, cudaStream_t s);
+cudaError_t launch_euclid_table(int core_dtype, const void *G, int I, int Q, double *snorm,
+                                double *prob, unsigned long long *cdf, cudaStream_t s);
+cudaError_t launch_reconstruct(int dtype, int N, const int *I, const int *R,
+                               const void *const *cores, void *X, const void *Xref,
+                               double *sums, cudaStream_t s);
+cudaError_t launch_sampled_loss_grad(int N, const int *I, const int *R, int n, int J,
+                                     const int *idx, const float *XS, const float *w,
+                                     const float *const *cores, float *const *grads,
+                                     float *loss, cudaStream_t s);
+
+}  // namespace trsgd

@@ -1,0 +1,198 @@
+"""GPU parity of the fused step kernel against the FP64 oracle.
+
+Tolerances (derived from the arithmetic, stated per path):
+  FP64 path: every recorded intermediate and the cores within 1e-12 relative
+    for single steps from a shared state, 1e-10 after long trajectories.
+  FP32 path: single steps within 2e-5 relative (sums of at most a few
+    hundred FP32 products: sqrt(K) * 2^-24 ~ 1e-6 typical, K * 2^-24 ~ 1e-5
+    worst case); indices and p_F bit-exact whenever both sides start from the
+    same cores.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import brsgd as ob
+from oracle import tr
+from tests.gpu_helpers import Case, api, cuda, rel
+
+pytestmark = [pytest.mark.gpu, cuda]
+
+
+def _compare_step(case, rec, tol, check_p=True):
+    d = case.debug(rec["n"])
+    assert d["n"] == rec["n"]
+    np.testing.assert_array_equal(d["idx"], rec["idx"])
+    np.testing.assert_array_equal(d["pF"], rec["pF"])
+    assert rel(d["Z"], rec["Z"]) < tol
+    assert rel(d["E"], rec["E"]) < tol
+    assert rel(d["g"], rec["g"]) < tol
+    if check_p:
+        assert rel(d["p"], rec["p"]) < tol
+    if "h" in d and rec["h"] is not None:
+        assert rel(d["h"], rec["h"]) < tol
+    for G, O in zip(case.device_cores(), case.state.cores):
+        assert rel(G, O) < tol
+
+
+SHAPES_FP32 = [
+    dict(dims=[12, 9, 10, 11], ranks=[3, 4, 2, 3], J=100),
+    dict(dims=[7, 6, 5, 6, 7], ranks=[2, 3, 2, 3, 2], J=64),
+    dict(dims=[30, 40], ranks=[4, 3], J=50),
+    dict(dims=[9, 8, 10], ranks=[1, 1, 1], J=33),
+    dict(dims=[1, 7, 8], ranks=[2, 3, 2], J=20),
+    dict(dims=[15, 14, 13], ranks=[4, 5, 3], J=1),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES_FP32, ids=lambda s: "x".join(map(str, s["dims"])) + f"_J{s['J']}")
+@pytest.mark.parametrize("cluster", [1, 4, 16])
+def test_fp32_single_steps(shape, cluster):
+    case = Case(prec=1, alpha=0.05, **shape)
+    case.solver.launch_shape(cluster=cluster, threads=256 if cluster == 4 else 512)
+    case.solver.set_debug(True)
+    for t in range(4):
+        # restart both sides from identical cores so each step is a single-step comparison
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, 2e-5)
+
+
+def test_fp32_chunked_rows_ragged_tail():
+    """I_n = 300 with Q = 256 does not fit one chunk: rows are processed in
+    chunks with a ragged last chunk."""
+    case = Case(dims=[300, 20, 25], ranks=[16, 16, 16], J=64, prec=1, alpha=0.01)
+    case.solver.launch_shape(cluster=16, threads=512)
+    case.solver.set_debug(True)
+    for t in range(3):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, 3e-5)
+
+
+@pytest.mark.parametrize("cluster", [1, 8])
+def test_fp64_single_steps(cluster):
+    case = Case(dims=[20, 20, 20], ranks=[3, 3, 3], J=50, prec=0, alpha=0.01)
+    case.solver.launch_shape(cluster=cluster, threads=512)
+    case.solver.set_debug(True)
+    for t in range(6):
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, 1e-12)
+
+
+def test_fp64_trajectory_2000_steps():
+    """Plain method, FP64 20^3, R=3, J=50, alpha 0.01, 2000 steps: cores and RSE
+    within 1e-10 relative of the oracle trajectory."""
+    from paper_2303_16492_gb300 import synth
+    A = api()
+    w = synth.workload("c1")
+    planted = synth.planted_cores(w)
+    from tests._util import to_oracle_cores
+    pc_or = to_oracle_cores(planted, w.ranks)
+    X_true = tr.reconstruct(pc_or)
+    noise = synth.noise(w.dims, w.seed + 1).reshape(w.dims, order="F")
+    X = X_true + noise * (w.noise_rel * np.linalg.norm(X_true) / np.linalg.norm(noise))
+    init = synth.initial_cores(w, float(np.sum(X * X)))
+    st = ob.State.new(to_oracle_cores(init, w.ranks))
+    cfg = ob.Config(J=w.J, alpha=w.alpha, seed=w.seed + 3)
+    ob.run(st, X, cfg, 2000)
+    rse_oracle = tr.rse(st.cores, X_true)
+
+    Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F"))).cuda()
+    Xtd = torch.from_numpy(np.ascontiguousarray(X_true.ravel(order="F"))).cuda()
+    cores = [torch.from_numpy(np.ascontiguousarray(G)).cuda() for G in init]
+    s = A.Solver([A.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=0, alpha=w.alpha, seed=w.seed + 3)],
+                 [Xd], [cores])
+    done, _ = s.run(0, 2000)
+    assert done == 2000
+    rse_gpu = s.rel_error(0, Xtd)
+    for n, G in enumerate(cores):
+        O = tr.unfold2(st.cores[n])
+        assert rel(G.cpu().numpy(), O) < 1e-10
+    assert abs(rse_gpu - rse_oracle) <= 1e-10 * rse_oracle
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_euclidean_distribution_steps(prec):
+    """Lemma euc_est sampling: from identical cores the integer CDF of both sides
+    is bit-identical, so the indices and p_F are bit-exact."""
+    case = Case(dims=[14, 11, 13], ranks=[3, 2, 4], J=80, prec=prec, alpha=0.05, dist=ob.DIST_EUCLIDEAN)
+    case.solver.set_debug(True)
+    tol = 1e-12 if prec == 0 else 2e-5
+    for t in range(6):
+        if prec == 1:
+            for k, G in enumerate(case.device_cores()):
+                case.state.cores[k] = G
+            # the device tables were built from the device cores of the last step
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, tol)
+
+
+@pytest.mark.parametrize("prec,damping", [(0, 0.0), (0, 0.5), (1, 0.0)])
+def test_scaled_variant_steps(prec, damping):
+    """Eq. scaledsg_direction with the damped preconditioner: h and p against
+    the oracle's Cholesky solve."""
+    case = Case(dims=[16, 15, 14], ranks=[3, 2, 3], J=90, prec=prec, alpha=0.3, variant=ob.VARIANT_SCALED,
+                damping=damping)
+    case.solver.set_debug(True)
+    tol = 1e-11 if prec == 0 else 1e-4
+    for t in range(5):
+        if prec == 1:
+            for k, G in enumerate(case.device_cores()):
+                case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, tol)
+
+
+def test_adagrad_steps_and_state():
+    case = Case(dims=[12, 10, 11], ranks=[2, 3, 2], J=40, prec=0, rule=ob.RULE_ADAGRAD, eta=0.02)
+    case.solver.set_debug(True)
+    for t in range(8):
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, 1e-12)
+    for k in range(3):
+        acc = np.empty((case.dims[k], case.Q(k)), dtype=np.float64)
+        case.solver.adagrad_state(0, k, acc)
+        assert rel(acc, case.state.acc[k]) < 1e-12 or np.all(case.state.acc[k] == acc)
+
+
+def test_scaled_adagrad_fp32():
+    case = Case(dims=[10, 12, 9], ranks=[2, 2, 3], J=60, prec=1, variant=ob.VARIANT_SCALED,
+                rule=ob.RULE_ADAGRAD, eta=0.05, damping=1e-3)
+    case.solver.set_debug(True)
+    for t in range(4):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        acc = [np.empty((case.dims[k], case.Q(k)), dtype=np.float32) for k in range(3)]
+        for k in range(3):
+            case.solver.adagrad_state(0, k, acc[k])
+            case.state.acc[k] = acc[k].astype(np.float64)
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, 1e-4)
+
+
+def test_non_finite_step_is_latched():
+    """A divergent step size makes the cores non-finite: the device status
+    word turns that into TRSGD_ENUMERIC at the next synchronising call."""
+    A = api()
+    case = Case(dims=[8, 9, 7], ranks=[2, 2, 2], J=16, prec=1, alpha=1e30)
+    with pytest.raises(A._abi.TrsgdError) as ei:
+        case.solver.run(0, 20)
+    assert ei.value.status == A._abi.ENUMERIC
+
+
+def test_run_stops_at_tolerance():
+    """Sec. 4 stopping rule: trsgd_run stops once RSE <= tol (checked every chunk)."""
+    case = Case(dims=[10, 10, 10], ranks=[2, 2, 2], J=40, prec=0, alpha=0.05, noise_rel=0.0, init_std=0.0)
+    # start from the planted cores: RSE is already ~0
+    done, r = case.solver.run(0, 1000, chunk=10, tol=1.0, Xref=case.Xtd)
+    assert done == 10 and 0 <= r <= 1.0
