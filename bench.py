@@ -270,6 +270,12 @@ def run_extras(args, device):
     try:
         w = synth.workload(args.workload)
         X, Xtrue, init = device_problem(w, device)
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=2, x_dtype=1, alpha=w.alpha, seed=w.seed + 3)
+        initb = [c.clone() for c in init]
+        s = api.Solver([pc], [X], [initb])
+        out["c2_bf16_mixed_tensor_core_steps_per_s"] = round(timed(s, 20000), 1)
+        out["c2_bf16_mixed_rse_after"] = s.rel_error(0, Xtrue)
+        s.close()
         pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=0.5, variant=1, damping=1e-9,
                                seed=w.seed + 3)
         s = api.Solver([pc], [X], [init])

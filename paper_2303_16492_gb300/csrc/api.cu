@@ -6,7 +6,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/trsgd.h"
+#include "trsgd.h"
 #include "common.cuh"
 #include "internal.h"
 
@@ -87,8 +87,8 @@ static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
     if (c.prec != cfg[0].prec || c.x_dtype != cfg[0].x_dtype) return TRSGD_EINVAL;
     if (c.prec == TRSGD_FP64 && c.x_dtype != TRSGD_DTYPE_F64) return TRSGD_EINVAL;
     if (c.prec == TRSGD_FP32 && c.x_dtype != TRSGD_DTYPE_F32) return TRSGD_EINVAL;
+    if (c.prec == TRSGD_BF16_MIXED && c.x_dtype == TRSGD_DTYPE_F64) return TRSGD_EINVAL;
     // this build
-    if (c.prec == TRSGD_BF16_MIXED) return TRSGD_EUNSUPPORTED;
     if (c.dist == TRSGD_DIST_LEVERAGE || c.dist == TRSGD_DIST_OPTIMAL) return TRSGD_EUNSUPPORTED;
     if (c.J_H != 0) return TRSGD_EUNSUPPORTED;
     for (int k = 0; k < c.N; ++k) {
@@ -102,30 +102,50 @@ static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
 }
 
 // Shared-memory layout for cluster size C (returns false if it does not fit).
+// Fixed part: barrier, scalars, per-sample indices/columns/weights, fibers,
+// Z and Z^T.  Tail region [off_reg, total): G_n chunk / partial gradient
+// (reg), the FP64 Gram (scaled), the owned rows; the staged slices of the
+// chain and the CDF scratch alias the same tail.
 static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   const size_t st = h.core_dtype == 0 ? 8 : 4;
   const size_t sx = dtype_size(h.xc_dtype);
   int Imax = 1, Qmax = 1, Jmax = 1, QH = 0;
+  size_t sbq = 0;   // max over problems and modes of sum_{k != n} padded Q_k
+  int pst = 1;      // max over problems and modes of R_{n+1} * max_k R_k
   bool scaled = false;
   for (const auto &c : h.cfg) {
     Jmax = std::max(Jmax, (int)c.J);
+    size_t qsum = 0;
+    for (int k = 0; k < c.N; ++k) qsum += rup((size_t)(c.R[k] * c.R[(k + 1) % c.N]), 16 / st);
     for (int k = 0; k < c.N; ++k) {
       Imax = std::max(Imax, (int)c.I[k]);
       const int Q = (int)(c.R[k] * c.R[(k + 1) % c.N]);
       Qmax = std::max(Qmax, Q);
       if (c.variant == TRSGD_SCALED) QH = std::max(QH, Q);
+      sbq = std::max(sbq, qsum - rup((size_t)Q, 16 / st));
     }
+    int rmx = 1;
+    for (int k = 0; k < c.N; ++k) rmx = std::max<int>(rmx, (int)c.R[k]);
+    for (int k = 0; k < c.N; ++k) pst = std::max<int>(pst, (int)c.R[(k + 1) % c.N] * rmx);
     scaled |= c.variant == TRSGD_SCALED;
   }
   L = {};
   L.C = C;
   L.JB = (Jmax + C - 1) / C;
-  L.ldxs = (int)rup((size_t)Imax, 16 / sx);
-  if (sx < st) L.ldxs = (int)rup((size_t)Imax, 16 / sx);
-  L.ldq = Qmax;
-  L.ldjb = (int)rup((size_t)L.JB, 4);
+  const bool tc = h.xc_dtype == TRSGD_DTYPE_BF16;   // tensor-core path
+  const size_t JB4 = rup((size_t)L.JB, 4);
+  L.ldxs = (int)rup((size_t)Imax, tc ? 8 : 4);
+  {
+    int q = (int)rup((size_t)Qmax, 4);
+    if (st == 4) { while (q % 32 != 4) ++q; }
+    else { while (q % 16 != 2) ++q; }
+    L.ldq = q;
+  }
+  L.ldg = (int)rup((size_t)Qmax, 4);
   L.QH = scaled ? QH : 0;
-  L.rows_own = scaled ? (Imax + C - 1) / C + 1 : 0;
+  L.qp = (int)rup((size_t)Qmax, 16);
+  L.jbp = (int)rup((size_t)L.JB, 16);
+  if (tc && (L.qp > 256 || L.jbp > 256)) return false;
   size_t off = 0;
   auto take = [&](size_t bytes, size_t align) {
     off = rup(off, align);
@@ -135,31 +155,64 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   };
   L.off_bar = take(16, 16);
   L.off_misc = take(64, 16);
+  L.off_const = take(16 * 8, 16);
+  L.off_desc = take(rup(sizeof(ProbDesc), 16), 16);
   L.off_idx = take((size_t)L.JB * kMaxOrder * 4, 16);
   L.off_col = take((size_t)L.JB * 8, 16);
   L.off_w = take((size_t)L.JB * 8, 16);
-  L.off_x = take((size_t)L.JB * L.ldxs * std::max(sx, st), 128);
-  L.off_z = take((size_t)L.JB * L.ldq * st, 16);
-  L.off_zt = take((size_t)Qmax * L.ldjb * st, 16);
-  if (scaled) {
-    L.off_h64 = take((size_t)QH * QH * 8, 16);
-    L.off_hdiag = take((size_t)QH * 8, 16);
-    L.off_gown = take((size_t)L.rows_own * L.ldq * st, 16);
+  L.off_wt = take(JB4 * st, 16);
+  L.off_x = take(JB4 * L.ldxs * (tc ? sx : std::max(sx, st)), 128);
+  L.off_z = take(JB4 * L.ldq * st, 128);
+  if (tc) {
+    L.off_zh = take((size_t)L.jbp * L.qp * 2, 128);
+    L.off_zl = take((size_t)L.jbp * L.qp * 2, 128);
   }
   const size_t limit = (size_t)step_max_smem() - 1024;
-  if (off >= limit) return false;
-  const size_t avail = limit - rup(off, 128);
-  int TI = (int)std::min<size_t>((size_t)Imax, avail / ((size_t)Qmax * st));
-  if (scaled) {
-    if (TI < Imax || TI < QH) return false;   // scaled: one chunk and room for the Gram partial
-  }
-  if (TI < 1) return false;
+  const size_t tail0 = rup(off, 128);
+  if (tail0 >= limit) return false;
+  const size_t avail = limit - tail0;
+  const size_t h64b = scaled ? (size_t)QH * QH * 8 : 0;
+  const size_t hdb = scaled ? (size_t)QH * 8 : 0;
+  auto own_rows_for = [&](int TI) { return scaled ? (Imax + C - 1) / C + 1 : (TI + C - 1) / C + 1; };
+  auto reg_bytes = [&](int ti) {
+    size_t reg = std::max((size_t)ti * L.ldg, (size_t)ti * L.ldq);
+    if (scaled) reg = std::max(reg, (size_t)QH * L.ldq);
+    size_t b = reg * st;
+    if (tc)   // split-BF16 G chunk (hi, lo) | partial gradient FP32 + Ew tile
+      b = std::max(std::max(b, (size_t)2 * 128 * L.qp * 2),
+                   rup((size_t)128 * L.ldq * st, 128) + (size_t)128 * L.jbp * 2);
+    return b;
+  };
+  auto tail_bytes = [&](int ti) {
+    return rup(reg_bytes(ti), 128) + rup(h64b, 16) + rup(hdb, 16) + (size_t)own_rows_for(ti) * L.ldq * st + 64;
+  };
+  int TI = tc ? 128 : (int)rup((size_t)Imax, 4);
+  while (!tc && TI > 4 && tail_bytes(TI) > avail) TI = std::max(4, (TI * 7 / 8) & ~3);
+  if (tail_bytes(TI) > avail) return false;
+  if (scaled && TI < Imax) return false;   // scaled: one chunk
   L.TI = TI;
-  L.ldti = TI;
-  size_t reg = std::max((size_t)Qmax * L.ldti, (size_t)TI * L.ldq);
-  if (scaled) reg = std::max(reg, (size_t)QH * L.ldq);
-  L.off_reg = take(reg * st, 128);
-  L.total = rup(off, 128);
+  L.rows_own = own_rows_for(TI);
+  off = tail0;
+  L.off_reg = take(reg_bytes(TI), 128);
+  L.off_ew = L.off_reg + rup((size_t)128 * L.ldq * st, 128);
+  L.off_sb = L.off_reg;
+  if (scaled) {
+    L.off_h64 = take(h64b, 16);
+    L.off_hdiag = take(hdb, 16);
+  }
+  L.off_gown = take((size_t)L.rows_own * L.ldq * st, 16);
+  size_t end = std::max(off, tail0 + (size_t)Imax * 16);
+  // staged slices followed by the two chain buffers, all aliasing the tail
+  L.pstride = pst;
+  const size_t sb_bytes = rup((size_t)L.JB * sbq * st, 128);
+  const size_t pb_bytes = rup((size_t)L.JB * pst * st, 128);
+  L.off_p0 = tail0 + sb_bytes;
+  L.off_p1 = L.off_p0 + pb_bytes;
+  L.sb_ok = (tail0 + sb_bytes + 2 * pb_bytes <= limit) ? 1 : 0;
+  if (L.sb_ok) end = std::max(end, tail0 + sb_bytes + 2 * pb_bytes);
+  // the tensor-core path allocates all 512 TMEM columns: keep one CTA per SM
+  if (tc) end = std::max(end, (size_t)120 * 1024);
+  L.total = rup(end, 128);
   return L.total <= limit;
 }
 
@@ -262,6 +315,10 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
     D.damping = c.damping;
     D.seed = c.seed;
     D.status = h->d_status;
+    for (int k = 0; k < c.N; ++k) {
+      const size_t qb = (size_t)c.R[k] * c.R[(k + 1) % c.N] * score;
+      if (qb % 16 == 0 && ((uintptr_t)cores_dev[ncore + k] % 16) == 0) D.slice_tma |= 1 << k;
+    }
     h->X.push_back(X_dev[p]);
     for (int k = 0; k < c.N; ++k) {
       D.cores[k] = cores_dev[ncore + k];

@@ -20,6 +20,7 @@ struct ProbDesc {
   double *prob[8];                // p_k (non-uniform distributions)
   unsigned long long *cdf[8];     // inclusive prefix sums of round(p_k * 2^52)
   double *snorm[8];               // Euclidean slice norms ||G_k(i)||_F^2
+  int slice_tma;                  // bit k set: core k's slices can be bulk-copied (16-byte rows)
   // recording of intermediates (problem 0 only)
   int dbg;
   int *dbg_n, *dbg_idx;
@@ -33,15 +34,19 @@ struct ProbDesc {
 struct StepLayout {
   int C;          // CTAs per cluster (per problem)
   int JB;         // max samples per CTA
-  int ldxs;       // fiber rows in smem (elements of the fiber dtype)
-  int ldq;        // Z rows (elements)
-  int ldjb;       // Z^T rows (elements)
-  int TI;         // rows of G_n per chunk
-  int ldti;       // G^T chunk rows
+  int ldxs;       // fiber rows in smem (elements of the fiber dtype; multiple of 4)
+  int ldq;        // Z rows (elements; = 4 mod 32 for conflict-free n-major reads)
+  int ldg;        // G_n chunk rows (elements; multiple of 4)
+  int TI;         // rows of G_n per chunk (multiple of 4)
   int QH;         // max Q of the scaled variant (0: none)
   int rows_own;   // max rows of g owned by one CTA
-  size_t off_idx, off_col, off_w, off_bar, off_x, off_z, off_zt, off_reg, off_h64, off_hdiag,
-      off_gown, off_misc, total;
+  int sb_ok;      // sampled slices staged in shared memory (else read through L2)
+  int pstride;    // per-sample stride of the chain intermediates
+  int qp, jbp;    // tensor-core path: Q and samples padded to 16 (tile extents)
+  // off_sb aliases the region [off_reg, total): the staged slices are dead
+  // before the Gram / chunk buffers and the CDF scratch are written
+  size_t off_desc, off_idx, off_col, off_w, off_wt, off_bar, off_x, off_z, off_reg, off_h64,
+      off_hdiag, off_gown, off_misc, off_const, off_sb, off_p0, off_p1, off_zh, off_zl, off_ew, total;
 };
 
 // kernel launchers (defined in the .cu files)

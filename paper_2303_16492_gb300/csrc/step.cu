@@ -4,28 +4,36 @@
 // (Algorithm 3 with Algorithm 2).  The CTAs of a cluster split the |F|
 // samples of each step; everything a step needs stays on chip:
 //
-//   A  draws (Philox, Algorithm 2), p_F, weights 1/(|F| J_n p_F), the fiber
-//      gather by TMA bulk copies from the mode-major copy of X, and the
-//      sampled subchain rows Z (slice chain, one thread per row of P_j).
-//   S  (scaled variant) partial Gram Z^T D Z, reduced over the cluster in
-//      FP64 into CTA 0, which factors h + eta^t I (Cholesky, FP64).
+//   A1 slice indices (Philox, Algorithm 2) of this CTA's samples;
+//   A2 p_F (product in ring order), weights 1/(|F| J_n p_F), fiber columns;
+//   A3 gather: the mode-n fibers of X from its mode-major copy and every
+//      sampled slice G_k(i_k), by per-thread 16-byte asynchronous copies
+//      (large fibers: TMA bulk copies completing on an mbarrier);
+//   A4 sampled subchain rows Z(j, r + r' R_n) = P_j(r', r), one thread per
+//      row of P_j = G_{n+1}(i_{n+1}) ... G_{n-1}(i_{n-1});
+//   S  (scaled variant) partial Gram Z^T D Z, reduced over the cluster into
+//      CTA 0, which factors h + eta^t I in FP64 (Cholesky, damping grown on
+//      failure);
 //   B  per chunk of G_n rows: residual E = G_n Z^T - X_S (Eq. S_gradient),
 //      weighted in place over the fibers;
-//   C  partial gradient E D Z of this CTA's samples;
-//   R  cluster reduction of the partials through distributed shared memory
-//      in a fixed CTA order (deterministic), then the step rule (fixed alpha
-//      or AdaGrad) on the rows this CTA owns, written to G_n in HBM.
-//   Scaled: p = -g h^{-1} per owned row by two FP64 triangular solves
-//      against CTA 0's factor (Eq. scaledsg_direction, damped form).
+//   C  partial gradient (E D) Z of this CTA's samples;
+//   R  reduction of the partials over the cluster through distributed shared
+//      memory in fixed CTA order (deterministic), then the step rule (fixed
+//      alpha or AdaGrad) on the rows this CTA owns, written to G_n in HBM;
+//   scaled: p = -g h^{-1} on the owned rows by two FP64 triangular solves
+//      against CTA 0's factor (Eq. scaledsg_direction, damped form);
 //   Euclidean distribution: slice norms of the updated rows and CTA 0's
 //      integer CDF of core n for the next iteration (Lemma euc_est).
 //
-// Cluster barriers (barrier.cluster, release/acquire) separate the phases;
-// cores and distribution tables are read through L2 only because other CTAs
-// of the cluster rewrite them between steps.  The only spin-wait (the TMA
-// mbarrier) is bounded and latches TRSGD_ETIMEOUT.
+// Cluster barriers (barrier.cluster, release/acquire) separate the phases.
+// Cores and sampling tables are read through L2 only (ld.global.cg /
+// cp.async.cg) because other CTAs of the cluster rewrite them between steps.
+// The only spin-wait (the TMA mbarrier) is bounded and latches
+// TRSGD_ETIMEOUT.
 #include "blocks.cuh"
 #include "internal.h"
+
+#include <type_traits>
 
 namespace cg = cooperative_groups;
 
@@ -33,14 +41,14 @@ namespace trsgd {
 
 static constexpr long long kWaitLimit = 1LL << 22;
 static constexpr int kMaxThreads = 512;
+static constexpr uint32_t kTmaFiberBytes = 1024;   // fibers at least this long go through TMA
 
 __host__ __device__ inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // In-place lower Cholesky of the Q x Q matrix A (leading dim ld) by one CTA;
 // the strict upper triangle is left untouched.  Returns false at the first
 // non-positive or non-finite pivot (the same decision in every thread).
-template <typename Dummy = void>
-__device__ bool cholesky_cta(double *A, int Q, int ld) {
+__device__ __noinline__ bool cholesky_cta(double *A, int Q, int ld) {
   const int tid = threadIdx.x, NT = blockDim.x;
   for (int k = 0; k < Q; ++k) {
     __syncthreads();
@@ -61,6 +69,20 @@ __device__ bool cholesky_cta(double *A, int Q, int ld) {
   return true;
 }
 
+// Step rule on one entry of G_n: fixed alpha (Eq. update_brsgd) or AdaGrad
+// (Remark after Algorithm 3: A += p^2, step eta (b + A)^-(1/2 + eps) p, zero
+// where b + A = 0), in the core precision.
+template <typename T>
+__device__ __forceinline__ T step_delta(int rule, T alpha, T eta, T b, double eps, T *accn, size_t gi, T p) {
+  if (rule == 0) return alpha * p;
+  const T a = ld_l2(accn + gi) + p * p;
+  accn[gi] = a;
+  const T base = b + a;
+  if (!(base > T(0))) return T(0);
+  const T sc = (eps == 0.0) ? eta / sqrt(base) : eta * pow(base, (T)(-(0.5 + eps)));
+  return sc * p;
+}
+
 template <typename T, typename XT, int RMAX>
 __global__ void __launch_bounds__(kMaxThreads)
     step_cluster_kernel(const ProbDesc *__restrict__ descs, StepLayout lay, long long t0, int nsteps) {
@@ -68,60 +90,236 @@ __global__ void __launch_bounds__(kMaxThreads)
   const int C = lay.C;
   const int c = (int)cluster.block_rank();
   const int pidx = blockIdx.x / C;
-  const ProbDesc &D = descs[pidx];
 
   extern __shared__ __align__(128) unsigned char smem[];
+  ProbDesc *desc_s = reinterpret_cast<ProbDesc *>(smem + lay.off_desc);
   int *idx_s = reinterpret_cast<int *>(smem + lay.off_idx);
   long long *col_s = reinterpret_cast<long long *>(smem + lay.off_col);
   double *w_s = reinterpret_cast<double *>(smem + lay.off_w);
+  T *wt_s = reinterpret_cast<T *>(smem + lay.off_wt);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + lay.off_bar);
   XT *xs = reinterpret_cast<XT *>(smem + lay.off_x);
   T *zs = reinterpret_cast<T *>(smem + lay.off_z);
-  T *zt = reinterpret_cast<T *>(smem + lay.off_zt);
   T *reg = reinterpret_cast<T *>(smem + lay.off_reg);
   double *h64 = reinterpret_cast<double *>(smem + lay.off_h64);
   double *hdiag = reinterpret_cast<double *>(smem + lay.off_hdiag);
   T *gown = reinterpret_cast<T *>(smem + lay.off_gown);
   double *misc = reinterpret_cast<double *>(smem + lay.off_misc);
+  double *cst = reinterpret_cast<double *>(smem + lay.off_const);   // [0,8): 1/I_k, [8,16): |F| J_n
+  T *sb = reinterpret_cast<T *>(smem + lay.off_sb);                 // staged slices (aliases the tail)
 
   const int tid = threadIdx.x, NT = blockDim.x;
+  {   // the problem descriptor, once per launch
+    const int *src = reinterpret_cast<const int *>(descs + pidx);
+    int *dst = reinterpret_cast<int *>(desc_s);
+    for (int i = tid; i < (int)(sizeof(ProbDesc) / 4); i += NT) dst[i] = src[i];
+  }
+  constexpr bool kTC = std::is_same<XT, __nv_bfloat16>::value;   // tensor-core path
+  uint64_t *bar_mma = bar + 1;
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(misc + 6);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_init(bar_mma, 1);
+    fence_mbar_init();
+  }
+  if constexpr (kTC) {
+    if (tid < 32) tmem_alloc(tslot, 512);
+    tc_fence_before();
+  }
+  __syncthreads();
+  if constexpr (kTC) tc_fence_after();
+  const uint32_t tbase = kTC ? *tslot : 0u;
+  uint32_t mphase = 0;
+  const ProbDesc &D = *desc_s;
   const int N = D.N, J = D.J;
   int I[kMaxOrder], R[kMaxOrder];
 #pragma unroll
   for (int k = 0; k < kMaxOrder; ++k) { I[k] = D.I[k]; R[k] = D.R[k]; }
-  const T *cores_c[kMaxOrder];
-#pragma unroll
-  for (int k = 0; k < kMaxOrder; ++k) cores_c[k] = static_cast<const T *>(D.cores[k]);
   const bool scaled = D.variant == 1;
   const bool rec = D.dbg && pidx == 0;
   const int ldq = lay.ldq;
-
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
+  const T alpha_t = (T)D.alpha, eta_t = (T)D.eta, b_t = (T)D.b;
+  if (tid < N) {   // FP64 constants, once per launch (FP64 throughput is scarce)
+    cst[tid] = __ddiv_rn(1.0, (double)I[tid]);
+    double jn = 1.0;
+    for (int k = 0; k < N; ++k)
+      if (k != tid) jn = __dmul_rn(jn, (double)I[k]);
+    cst[8 + tid] = __dmul_rn((double)J, jn);
   }
   __syncthreads();
   uint32_t phase = 0;
+
+  // sum of one element of a shared-memory buffer over the cluster's CTAs in
+  // fixed CTA order 0..C-1 (deterministic); the C remote loads are issued together
+  auto cluster_sum = [&](T *local, size_t off) -> T {
+    T v[16];
+#pragma unroll
+    for (int cc = 0; cc < 16; ++cc) v[cc] = (cc < C) ? cluster.map_shared_rank(local, cc)[off] : T(0);
+    T g = T(0);
+#pragma unroll
+    for (int cc = 0; cc < 16; ++cc)
+      if (cc < C) g += v[cc];
+    return g;
+  };
+
+  int cur_n = 0, cur_Q = 0, cur_jb = 0, cur_j0 = 0;
+  // Tensor-core residual and partial gradient of one chunk of <= 128 rows of
+  // G_n (operands split BF16, FP32 accumulation in TMEM):
+  //   D_R(i, jl) = G(i, :) Z(jl, :)^T  as hi*hi + hi*lo + lo*hi,
+  //   Ew(i, jl)  = w_jl (D_R(i, jl) - X_S(jl, i))              (epilogue),
+  //   D_P(i, q)  = sum_jl Ew(i, jl) Z(jl, q)   (Z_hi read MN-major),
+  // then D_P -> reg[i][q] (FP32) for the cluster reduction.
+  auto tc_chunk = [&](int ti, int i0) {
+    if constexpr (kTC) {
+      const int n = cur_n, In = I[n], Q = cur_Q, jb = cur_jb;
+      T *Gn = static_cast<T *>(D.cores[n]);
+      const int QC = lay.qp / 8;
+      unsigned char *ghi = smem + lay.off_reg;
+      unsigned char *glo = ghi + (size_t)128 * lay.qp * 2;
+      unsigned char *ew = smem + lay.off_ew;
+      unsigned char *zh = smem + lay.off_zh, *zl = smem + lay.off_zl;
+      for (int e = tid; e < 128 * QC; e += NT) {
+        const int ii = e / QC, qb = e - ii * QC;
+        uint32_t hw[4], lw[4];
+  #pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          float v[2];
+  #pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int q = qb * 8 + j + u;
+            v[u] = (ii < ti && q < Q) ? (float)ld_l2(Gn + (size_t)(i0 + ii) * Q + q) : 0.f;
+          }
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(v[0] - hf.x, v[1] - hf.y);
+          hw[j / 2] = *reinterpret_cast<const uint32_t *>(&h);
+          lw[j / 2] = *reinterpret_cast<const uint32_t *>(&l);
+        }
+        const uint32_t o = kmaj_off(ii, qb * 8, QC);
+        *reinterpret_cast<uint4 *>(ghi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(glo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      const int NR = max(16, (jb + 15) & ~15);   // columns of D_R (samples, padded)
+      const int KQ = (Q + 15) & ~15;             // contraction length of D_R
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t idr = umma_idesc_bf16(128, NR, 0, 0);
+        const uint32_t sbo = (uint32_t)QC * 128;
+        for (int kb = 0; kb < KQ / 16; ++kb) {
+          const uint32_t ko = (uint32_t)kb * 256;
+          const uint64_t ah = umma_desc(smem_u32(ghi) + ko, 128, sbo), al = umma_desc(smem_u32(glo) + ko, 128, sbo);
+          const uint64_t bh = umma_desc(smem_u32(zh) + ko, 128, sbo), bl = umma_desc(smem_u32(zl) + ko, 128, sbo);
+          umma_bf16(tbase, ah, bh, idr, kb > 0);
+          umma_bf16(tbase, ah, bl, idr, true);
+          umma_bf16(tbase, al, bh, idr, true);
+        }
+        umma_commit(bar_mma);
+      }
+      if (!mbar_wait_bounded(bar_mma, mphase, kWaitLimit)) latch_status(D.status, kStatusTimeout);
+      mphase ^= 1u;
+      tc_fence_after();
+      const int warp = tid >> 5, lane = tid & 31, qd = warp & 3, wg = warp >> 2, nwg = NT >> 7;
+      const int row = 32 * qd + lane;
+      const int JC = NR / 8;
+      T *dbg_e = rec ? static_cast<T *>(D.dbg_e) : nullptr;
+      for (int c8 = wg; c8 < NR / 8; c8 += nwg) {
+        float v[8];
+        tmem_ld8(tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(c8 * 8), v);
+        if (row < ti) {
+          uint32_t pw[4];
+  #pragma unroll
+          for (int j = 0; j < 8; j += 2) {
+            float ev[2];
+  #pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int jl = c8 * 8 + j + u;
+              ev[u] = 0.f;
+              if (jl < jb) {
+                const float x = __bfloat162float(xs[(size_t)jl * lay.ldxs + i0 + row]);
+                const float e = v[j + u] - x;
+                if (dbg_e) dbg_e[(size_t)(cur_j0 + jl) * In + i0 + row] = e;
+                ev[u] = e * wt_s[jl];
+              }
+            }
+            const __nv_bfloat162 h = __floats2bfloat162_rn(ev[0], ev[1]);
+            pw[j / 2] = *reinterpret_cast<const uint32_t *>(&h);
+          }
+          *reinterpret_cast<uint4 *>(ew + kmaj_off(row, c8 * 8, JC)) = make_uint4(pw[0], pw[1], pw[2], pw[3]);
+        }
+      }
+      fence_proxy_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      const int NP = (Q + 15) & ~15;
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t idp = umma_idesc_bf16(128, NP, 0, 1);
+        for (int kb = 0; kb < NR / 16; ++kb) {
+          const uint64_t a = umma_desc(smem_u32(ew) + (uint32_t)kb * 256, 128, (uint32_t)JC * 128);
+          const uint64_t b = umma_desc(smem_u32(zh) + (uint32_t)kb * 2 * QC * 128, (uint32_t)QC * 128, 128);
+          umma_bf16(tbase + 256, a, b, idp, kb > 0);
+        }
+        umma_commit(bar_mma);
+      }
+      if (!mbar_wait_bounded(bar_mma, mphase, kWaitLimit)) latch_status(D.status, kStatusTimeout);
+      mphase ^= 1u;
+      tc_fence_after();
+      for (int c8 = wg; c8 < NP / 8; c8 += nwg) {
+        float v[8];
+        tmem_ld8(tbase + 256 + ((uint32_t)(32 * qd) << 16) + (uint32_t)(c8 * 8), v);
+        if (row < ti) {
+  #pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int q = c8 * 8 + j;
+            if (q < Q) reg[(size_t)row * lay.ldq + q] = v[j];
+          }
+        }
+      }
+      tc_fence_before();
+    }
+  };
 
   for (int s = 0; s < nsteps; ++s) {
     const long long t = t0 + s;
     const int n = draw_mode(D.seed, t, N);
     const int In = I[n], Rn = R[n], Rn1 = R[(n + 1) % N], Q = Rn * Rn1;
+    const int Q4 = (Q + 3) & ~3;
     const int L = N - 1;
+    const int j0 = (int)((long long)J * c / C), j1 = (int)((long long)J * (c + 1) / C);
+    const int jb = j1 - j0, jb4 = (jb + 3) & ~3;
+    cur_n = n;
+    cur_Q = Q;
+    cur_jb = jb;
+    cur_j0 = j0;
     int order[kMaxOrder];
-    double Jn = 1.0;
 #pragma unroll
     for (int q = 0; q < kMaxOrder; ++q) order[q] = (q < L) ? (n + 1 + q) % N : 0;
-    for (int k = 0; k < N; ++k)
-      if (k != n) Jn *= (double)I[k];
-    const int j0 = (int)((long long)J * c / C), j1 = (int)((long long)J * (c + 1) / C);
-    const int jb = j1 - j0;
+    // staged slice layout: factor s at sb + soff[s], sample jl at + jl * qpad[s]
+    int soff[kMaxOrder], qpad[kMaxOrder];
+    bool sl_async = true;
+    {
+      int off = 0;
+#pragma unroll
+      for (int q = 0; q < kMaxOrder; ++q) {
+        const int k = order[q];
+        const int qs = R[k] * R[(k + 1) % N];
+        qpad[q] = (int)round_up((size_t)qs, 16 / sizeof(T));
+        soff[q] = off;
+        if (q < L) {
+          off += jb * qpad[q];
+          if (!((D.slice_tma >> k) & 1)) sl_async = false;
+        }
+      }
+    }
     T *Gn = static_cast<T *>(D.cores[n]);
     T *accn = static_cast<T *>(D.acc[n]);
 
     // ---- A1: slice indices (Algorithm 2) -----------------------------------
     for (int e = tid; e < jb * L; e += NT) {
-      const int jl = e / L, sp = e % L, k = order[sp];
+      const int jl = e / L, sp = e - jl * L, k = order[sp];
       const uint64_t u = draw_u64(D.seed, t, kStreamF, k, (uint32_t)(j0 + jl));
       int i;
       if (D.dist == 0) {
@@ -136,17 +334,23 @@ __global__ void __launch_bounds__(kMaxThreads)
     __syncthreads();
 
     // ---- A2: p_F (product in ring order), weights, fiber column -------------
-    for (int jl = tid; jl < jb; jl += NT) {
+    for (int jl = tid; jl < jb4; jl += NT) {
+      if (jl >= jb) {
+        wt_s[jl] = T(0);
+        continue;
+      }
       double pF = 1.0;
       long long col = 0, st = 1;
       for (int sp = 0; sp < L; ++sp) {
         const int k = order[sp], i = idx_s[jl * kMaxOrder + k];
-        const double pk = (D.dist == 0) ? __ddiv_rn(1.0, (double)I[k]) : __ldcg(D.prob[k] + i);
+        const double pk = (D.dist == 0) ? cst[k] : __ldcg(D.prob[k] + i);
         pF = __dmul_rn(pF, pk);
         col += (long long)i * st;
         st *= I[k];
       }
-      w_s[jl] = __ddiv_rn(1.0, __dmul_rn(__dmul_rn((double)J, Jn), pF));
+      const double w = __ddiv_rn(1.0, __dmul_rn(cst[8 + n], pF));
+      w_s[jl] = w;
+      wt_s[jl] = (T)w;
       col_s[jl] = col;
       if (rec) {
         D.dbg_pf[j0 + jl] = pF;
@@ -157,36 +361,54 @@ __global__ void __launch_bounds__(kMaxThreads)
     if (rec && c == 0 && tid == 0) *D.dbg_n = n;
     __syncthreads();
 
-    // ---- A3: fiber gather, one TMA bulk copy per sample -------------------
+    // ---- A3: gather fibers and sampled slices into shared memory -----------
     const uint32_t fbytes = (uint32_t)round_up((size_t)In * sizeof(XT), 16);
-    if (tid == 0 && jb > 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(bar, (uint32_t)jb * fbytes);
+    const bool fiber_tma = fbytes >= kTmaFiberBytes;
+    {
       const XT *base = static_cast<const XT *>(D.xmode[n]);
       const long long ldg = D.ldx[n];
-      for (int jl = 0; jl < jb; ++jl)
-        tma_load_1d(xs + (size_t)jl * lay.ldxs, base + col_s[jl] * ldg, fbytes, bar);
+      if (fiber_tma) {
+        if (tid < 32 && jb > 0) {
+          if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)jb * fbytes);
+          __syncwarp();
+          fence_proxy_async_smem();
+          for (int jl = tid; jl < jb; jl += 32)
+            tma_load_1d(xs + (size_t)jl * lay.ldxs, base + col_s[jl] * ldg, fbytes, bar);
+        }
+      } else {
+        const int nch = (int)(fbytes / 16);
+        for (int e = tid; e < jb * nch; e += NT) {
+          const int jl = e / nch, ch = e - jl * nch;
+          cp_async16(reinterpret_cast<char *>(xs + (size_t)jl * lay.ldxs) + 16 * ch,
+                     reinterpret_cast<const char *>(base + col_s[jl] * ldg) + 16 * ch);
+        }
+      }
+      // pad fiber rows [jb, jb4) read as zeros by the partial-gradient GEMM
+      for (int e = tid; e < (jb4 - jb) * lay.ldxs; e += NT)
+        xs[(size_t)(jb + e / lay.ldxs) * lay.ldxs + e % lay.ldxs] = XT(0);
     }
-
-    // ---- A4: sampled subchain rows, Z(j, r + r' R_n) = P_j(r', r) ----------
-    for (int e = tid; e < jb * Rn1; e += NT) {
-      const int jl = e / Rn1, rp = e % Rn1;
-      int sidx[kMaxOrder];
-#pragma unroll
-      for (int q = 0; q < kMaxOrder; ++q) sidx[q] = (q < L) ? idx_s[jl * kMaxOrder + order[q]] : 0;
-      T row[RMAX];
-      chain_row<RMAX, T>(cores_c, R, N, order, sidx, L, rp, row);
-#pragma unroll
-      for (int r = 0; r < RMAX; ++r) {
-        if (r < Rn) {
-          const int q = r + rp * Rn;
-          zs[(size_t)jl * ldq + q] = row[r];
-          zt[(size_t)q * lay.ldjb + jl] = row[r];
-          if (rec) static_cast<T *>(D.dbg_z)[(size_t)(j0 + jl) * Q + q] = row[r];
+    if (lay.sb_ok) {
+      for (int q = 0; q < L; ++q) {
+        const int k = order[q], qs = R[k] * R[(k + 1) % N];
+        const T *G = static_cast<const T *>(D.cores[k]);
+        if (sl_async) {
+          const int nch = qs * (int)sizeof(T) / 16;
+          for (int e = tid; e < jb * nch; e += NT) {
+            const int jl = e / nch, ch = e - jl * nch;
+            cp_async16(reinterpret_cast<char *>(sb + soff[q] + (size_t)jl * qpad[q]) + 16 * ch,
+                       reinterpret_cast<const char *>(G + (size_t)idx_s[jl * kMaxOrder + k] * qs) + 16 * ch);
+          }
+        } else {
+#pragma unroll 4
+          for (int e = tid; e < jb * qs; e += NT) {
+            const int jl = e / qs, off = e - jl * qs;
+            sb[soff[q] + (size_t)jl * qpad[q] + off] = ld_l2(G + (size_t)idx_s[jl * kMaxOrder + k] * qs + off);
+          }
         }
       }
     }
-    if (jb > 0) {
+    cp_async_wait_all();
+    if (fiber_tma && jb > 0) {
       if (!mbar_wait_bounded(bar, phase, kWaitLimit)) {
         latch_status(D.status, kStatusTimeout);
         mbar_wait_bounded(bar, phase, kWaitLimit);
@@ -195,19 +417,115 @@ __global__ void __launch_bounds__(kMaxThreads)
     }
     __syncthreads();
 
+    // ---- A4: sampled subchain rows, Z(j, r + r' R_n) = P_j(r', r) ----------
+    if (lay.sb_ok) {
+      // P_1 = G_{n+1}(i) (staged, column-major); P_{s+1} = P_s G_{k_s}(i_s), one
+      // thread per entry (jl, r', b), row-major [r'][b] per sample; the last
+      // product lands in Z.  Intermediates ping-pong between two buffers.
+      T *pbuf[2] = {reinterpret_cast<T *>(smem + lay.off_p0), reinterpret_cast<T *>(smem + lay.off_p1)};
+      const int pst = lay.pstride;
+      for (int q = 1; q < L; ++q) {
+        const int k = order[q], Ra = R[k], Rb = R[(k + 1) % N];
+        const bool last = q == L - 1;
+        T *dst = last ? zs : pbuf[q & 1];
+        const int dstride = last ? ldq : pst;
+        const T *src = (q == 1) ? sb + soff[0] : pbuf[(q - 1) & 1];
+        const int sstride = (q == 1) ? qpad[0] : pst;
+        const int per = Rn1 * Rb;
+        for (int e = tid; e < jb * per; e += NT) {
+          const int jl = e / per, rem = e - jl * per, rp = rem / Rb, b = rem - rp * Rb;
+          const T *prow = src + (size_t)jl * sstride;
+          const T *S = sb + soff[q] + (size_t)jl * qpad[q] + b * Ra;
+          T acc = T(0);
+          if (q == 1) {
+#pragma unroll 4
+            for (int a = 0; a < Ra; ++a) acc = fma(prow[rp + a * Rn1], S[a], acc);
+          } else {
+#pragma unroll 4
+            for (int a = 0; a < Ra; ++a) acc = fma(prow[rp * Ra + a], S[a], acc);
+          }
+          dst[(size_t)jl * dstride + rp * Rb + b] = acc;
+        }
+        __syncthreads();
+      }
+      if (L == 1) {   // N = 2: Z row is the single staged slice, transposed
+        for (int e = tid; e < jb * Q; e += NT) {
+          const int jl = e / Q, rem = e - jl * Q, rp = rem / Rn, r = rem - rp * Rn;
+          zs[(size_t)jl * ldq + rem] = sb[soff[0] + (size_t)jl * qpad[0] + rp + r * Rn1];
+        }
+      }
+      if (rec) {
+        __syncthreads();
+        for (int e = tid; e < jb * Q; e += NT)
+          static_cast<T *>(D.dbg_z)[(size_t)(j0 + e / Q) * Q + e % Q] = zs[(size_t)(e / Q) * ldq + e % Q];
+      }
+    } else {
+      for (int e = tid; e < jb * Rn1; e += NT) {
+        const int jl = e / Rn1, rp = e - jl * Rn1;
+        T row[RMAX];
+        int sidx[kMaxOrder];
+#pragma unroll
+        for (int q = 0; q < kMaxOrder; ++q) sidx[q] = (q < L) ? idx_s[jl * kMaxOrder + order[q]] : 0;
+        const T *cores_c[kMaxOrder];
+#pragma unroll
+        for (int q = 0; q < kMaxOrder; ++q) cores_c[q] = static_cast<const T *>(D.cores[q]);
+        chain_row<RMAX, T>(cores_c, R, N, order, sidx, L, rp, row);
+        T *zrow = zs + (size_t)jl * ldq + rp * Rn;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) {
+          if (r < Rn) {
+            zrow[r] = row[r];
+            if (rec) static_cast<T *>(D.dbg_z)[(size_t)(j0 + jl) * Q + rp * Rn + r] = row[r];
+          }
+        }
+      }
+    }
+    // zero padding of Z: columns [Q, Q4) of rows < jb, and rows [jb, jb4)
+    if (Q4 > Q)
+      for (int e = tid; e < jb * (Q4 - Q); e += NT) zs[(size_t)(e / (Q4 - Q)) * ldq + Q + e % (Q4 - Q)] = T(0);
+    for (int e = tid; e < (jb4 - jb) * Q4; e += NT) zs[(size_t)(jb + e / Q4) * ldq + e % Q4] = T(0);
+    __syncthreads();
+    if constexpr (kTC) {
+      // Z as split BF16 (hi + lo) in the no-swizzle K-major tile [JBP rows jl][QP cols q]
+      const int QC = lay.qp / 8;
+      unsigned char *zh = smem + lay.off_zh, *zl = smem + lay.off_zl;
+      for (int e = tid; e < lay.jbp * QC; e += NT) {
+        const int jl = e / QC, qb = e - jl * QC;
+        uint32_t hw[4], lw[4];
+#pragma unroll
+        for (int j = 0; j < 8; j += 2) {
+          float v[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int q = qb * 8 + j + u;
+            v[u] = (jl < jb && q < Q) ? (float)zs[(size_t)jl * ldq + q] : 0.f;
+          }
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v[0], v[1]);
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(v[0] - hf.x, v[1] - hf.y);
+          hw[j / 2] = *reinterpret_cast<const uint32_t *>(&h);
+          lw[j / 2] = *reinterpret_cast<const uint32_t *>(&l);
+        }
+        const uint32_t o = kmaj_off(jl, qb * 8, QC);
+        *reinterpret_cast<uint4 *>(zh + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+        *reinterpret_cast<uint4 *>(zl + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+      }
+      fence_proxy_async_smem();
+      __syncthreads();
+    }
+
     // ---- S: preconditioner h = Z^T D Z / (|F| J_n) + eta^t I (FP64 solve) ---
     if (scaled) {
       const int QH = lay.QH;
-      gemm_tn<8, 4, T>(Q, Q, jb, zs, ldq, zs, ldq, w_s,
-                       [&](int a, int b, T v) { reg[(size_t)a * ldq + b] = v; });
+      gemm_s<4, true, true, T>(Q, Q, jb, zs, ldq, zs, ldq, wt_s,
+                               [=](int a, int b, T v) { reg[(size_t)a * ldq + b] = v; });
       cluster.sync();
       double *h0 = cluster.map_shared_rank(h64, 0);
       double *hd0 = cluster.map_shared_rank(hdiag, 0);
       const int q0 = Q * c / C, q1 = Q * (c + 1) / C;
       for (int e = tid; e < (q1 - q0) * Q; e += NT) {
         const int a = q0 + e / Q, b = e % Q;
-        double v = 0.0;
-        for (int cc = 0; cc < C; ++cc) v += (double)cluster.map_shared_rank(reg, cc)[(size_t)a * ldq + b];
+        double v = (double)cluster_sum(reg, (size_t)a * ldq + b);
         if (a == b) {
           v += D.damping;
           hd0[a] = v;
@@ -218,17 +536,17 @@ __global__ void __launch_bounds__(kMaxThreads)
       cluster.sync();
       if (c == 0) {
         // factor, growing the damping on failure (1e-12 tr(h)/Q * 10^m, m = 0..6)
-        __shared__ double tr_s;
         if (tid == 0) {
           double tr = 0.0;
           for (int q = 0; q < Q; ++q) tr += hdiag[q] - D.damping;
-          tr_s = tr;
+          misc[2] = tr;
         }
         __syncthreads();
+        const double tr = misc[2];
         bool ok = cholesky_cta(h64, Q, QH);
         double extra = 0.0;
         for (int m = 0; m < 7 && !ok; ++m) {
-          extra = 1e-12 * tr_s / Q * pow(10.0, (double)m);
+          extra = 1e-12 * tr / Q * pow(10.0, (double)m);
           __syncthreads();
           for (int e = tid; e < Q * Q; e += NT) {
             const int a = e / Q, b = e % Q;
@@ -248,61 +566,74 @@ __global__ void __launch_bounds__(kMaxThreads)
 
     // ---- B/C/R: per chunk of rows of G_n ------------------------------------
     int own_rows = 0;
+    T *gs = reg;   // G_n chunk [ti][ldg]; the partial gradient reuses the same region
+    const int ldg = lay.ldg;
     for (int i0 = 0; i0 < In; i0 += lay.TI) {
       const int ti = min(lay.TI, In - i0);
-      for (int e = tid; e < ti * Q; e += NT) {
-        const int ii = e / Q, q = e % Q;
-        reg[(size_t)q * lay.ldti + ii] = ld_l2(Gn + (size_t)(i0 + ii) * Q + q);
+      if constexpr (kTC) {
+        tc_chunk(ti, i0);
+      } else {
+        if ((Q * (int)sizeof(T)) % 16 == 0 && ((D.slice_tma >> n) & 1)) {
+          const int nch = Q * (int)sizeof(T) / 16;
+          for (int e = tid; e < ti * nch; e += NT) {
+            const int ii = e / nch, ch = e - ii * nch;
+            cp_async16(reinterpret_cast<char *>(gs + (size_t)ii * ldg) + 16 * ch,
+                       reinterpret_cast<const char *>(Gn + (size_t)(i0 + ii) * Q) + 16 * ch);
+          }
+        } else {
+  #pragma unroll 4
+          for (int e = tid; e < ti * Q; e += NT) {
+            const int ii = e / Q, q = e - ii * Q;
+            gs[(size_t)ii * ldg + q] = ld_l2(Gn + (size_t)(i0 + ii) * Q + q);
+          }
+        }
+        if (Q4 > Q)
+          for (int e = tid; e < ti * (Q4 - Q); e += NT) gs[(size_t)(e / (Q4 - Q)) * ldg + Q + e % (Q4 - Q)] = T(0);
+        cp_async_wait_all();
+        __syncthreads();
+        // residual, weighted in place: X_s(jl, i) <- w_j (G Z^T - X_S)(i, jl)
+        {
+          XT *xsp = xs;
+          const int ldxs = lay.ldxs;
+          T *dbg_e = rec ? static_cast<T *>(D.dbg_e) : nullptr;
+          const T *wt = wt_s;
+          gemm_s<2, false, false, T>(ti, jb, Q, gs, ldg, zs, ldq, nullptr, [=](int ii, int jl, T v) {
+            T *xp = reinterpret_cast<T *>(xsp) + (size_t)jl * ldxs + i0 + ii;
+            const T e = v - *xp;
+            if (dbg_e) dbg_e[(size_t)(j0 + jl) * In + i0 + ii] = e;
+            *xp = e * wt[jl];
+          });
+        }
+        __syncthreads();
+        // partial gradient of this CTA's samples: Gp(i, q) = sum_jl Ew(jl, i) Z(jl, q)
+        gemm_s<4, true, true, T>(ti, Q, jb, reinterpret_cast<T *>(xs) + i0, lay.ldxs, zs, ldq, nullptr,
+                                 [=](int ii, int q, T v) { reg[(size_t)ii * ldq + q] = v; });
       }
-      __syncthreads();
-      // residual, weighted in place: X_s <- w_j (G Z^T - X_S)
-      gemm_tn<8, 4, T>(jb, ti, Q, zt, lay.ldjb, reg, lay.ldti, nullptr, [&](int jl, int ii, T v) {
-        T *xp = reinterpret_cast<T *>(xs) + (size_t)jl * lay.ldxs + i0 + ii;
-        const T e = v - *xp;
-        if (rec) static_cast<T *>(D.dbg_e)[(size_t)(j0 + jl) * In + i0 + ii] = e;
-        *xp = e * (T)w_s[jl];
-      });
-      __syncthreads();
-      // partial gradient of this CTA's samples
-      gemm_tn<8, 4, T>(ti, Q, jb, reinterpret_cast<T *>(xs) + i0, lay.ldxs, zs, ldq, nullptr,
-                       [&](int ii, int q, T v) { reg[(size_t)ii * ldq + q] = v; });
       cluster.sync();
       const int r0 = ti * c / C, r1 = ti * (c + 1) / C;
       for (int e = tid; e < (r1 - r0) * Q; e += NT) {
         const int ii = r0 + e / Q, q = e % Q;
-        T g = T(0);
-        for (int cc = 0; cc < C; ++cc) g += cluster.map_shared_rank(reg, cc)[(size_t)ii * ldq + q];
+        const T g = cluster_sum(reg, (size_t)ii * ldq + q);
         const size_t gi = (size_t)(i0 + ii) * Q + q;
         if (rec) static_cast<T *>(D.dbg_g)[gi] = g;
         if (scaled) {
           gown[(size_t)(own_rows + ii - r0) * ldq + q] = g;
         } else {
           const T p = -g;
-          T delta;
-          if (D.rule == 0) {
-            delta = (T)D.alpha * p;
-          } else {
-            const T a = ld_l2(accn + gi) + p * p;
-            accn[gi] = a;
-            const double base = D.b + (double)a;
-            const double sc = base > 0.0 ? (D.eps == 0.0 ? D.eta / sqrt(base)
-                                                         : D.eta * pow(base, -(0.5 + D.eps)))
-                                         : 0.0;
-            delta = (T)sc * p;
-          }
-          const T nv = ld_l2(Gn + gi) + delta;
-          if (!isfinite((double)nv)) latch_status(D.status, kStatusNumeric);
+          const T nv = ld_l2(Gn + gi) + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
+          if (!isfinite(nv)) latch_status(D.status, kStatusNumeric);
           Gn[gi] = nv;
+          gown[(size_t)(ii - r0) * ldq + q] = nv;
           if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
         }
       }
       if (!scaled && D.dist == 2) {
         __syncthreads();
         for (int ii = r0 + tid; ii < r1; ii += NT) {
-          const T *row = Gn + (size_t)(i0 + ii) * Q;
+          const T *row = gown + (size_t)(ii - r0) * ldq;
           double sn = 0.0;
           for (int q = 0; q < Q; ++q) {
-            const double v = (double)ld_l2(row + q);
+            const double v = (double)row[q];
             sn = __dadd_rn(sn, __dmul_rn(v, v));
           }
           D.snorm[n][i0 + ii] = sn;
@@ -359,37 +690,27 @@ __global__ void __launch_bounds__(kMaxThreads)
 #pragma unroll
           for (int m = 0; m < QM; ++m) y[m] = 0.0;
         }
+        __syncwarp();
 #pragma unroll
         for (int m = 0; m < QM; ++m) {
           const int q = lane + 32 * m;
           if (q >= Q) continue;
           const size_t gi = (size_t)i * Q + q;
           const T p = (T)y[m];
-          T delta;
-          if (D.rule == 0) {
-            delta = (T)D.alpha * p;
-          } else {
-            const T a = ld_l2(accn + gi) + p * p;
-            accn[gi] = a;
-            const double base = D.b + (double)a;
-            const double sc = base > 0.0 ? (D.eps == 0.0 ? D.eta / sqrt(base)
-                                                         : D.eta * pow(base, -(0.5 + D.eps)))
-                                         : 0.0;
-            delta = (T)sc * p;
-          }
-          const T nv = ld_l2(Gn + gi) + delta;
-          if (!isfinite((double)nv)) latch_status(D.status, kStatusNumeric);
+          const T nv = ld_l2(Gn + gi) + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
+          if (!isfinite(nv)) latch_status(D.status, kStatusNumeric);
           Gn[gi] = nv;
+          gown[(size_t)rr * ldq + q] = nv;
           if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
         }
       }
       if (D.dist == 2) {
         __syncthreads();
         for (int rr = tid; rr < own_rows; rr += NT) {
-          const T *row = Gn + (size_t)(r0 + rr) * Q;
+          const T *row = gown + (size_t)rr * ldq;
           double sn = 0.0;
           for (int q = 0; q < Q; ++q) {
-            const double v = (double)ld_l2(row + q);
+            const double v = (double)row[q];
             sn = __dadd_rn(sn, __dmul_rn(v, v));
           }
           D.snorm[n][r0 + rr] = sn;
@@ -401,32 +722,42 @@ __global__ void __launch_bounds__(kMaxThreads)
     // ---- Euclidean table of core n for the next iteration (CTA 0) ---------
     if (D.dist == 2) {
       if (c == 0) {
+        double *scr = reinterpret_cast<double *>(smem + lay.off_reg);   // dead after the last barrier
+        unsigned long long *wsc = reinterpret_cast<unsigned long long *>(scr + In);
         const double *sn = D.snorm[n];
+        for (int i = tid; i < In; i += NT) scr[i] = __ldcg(sn + i);
+        __syncthreads();
         if (tid == 0) {
           double tot = 0.0;
-          for (int i = 0; i < In; ++i) tot = __dadd_rn(tot, __ldcg(sn + i));
+          for (int i = 0; i < In; ++i) tot = __dadd_rn(tot, scr[i]);
           misc[1] = tot;
           if (!(tot > 0.0)) latch_status(D.status, kStatusNumeric);
         }
         __syncthreads();
         const double tot = misc[1];
-        unsigned long long *cdf = D.cdf[n];
         for (int i = tid; i < In; i += NT) {
-          const double p = __ddiv_rn(__ldcg(sn + i), tot);
+          const double p = __ddiv_rn(scr[i], tot);
           D.prob[n][i] = p;
-          cdf[i] = __double2ull_rn(__dmul_rn(p, 4503599627370496.0));  // * 2^52, exact
+          wsc[i] = __double2ull_rn(__dmul_rn(p, 4503599627370496.0));  // * 2^52, exact
         }
         __syncthreads();
         if (tid == 0) {
           unsigned long long run = 0;
           for (int i = 0; i < In; ++i) {
-            run += __ldcg(cdf + i);
-            cdf[i] = run;
+            run += wsc[i];
+            wsc[i] = run;
           }
         }
+        __syncthreads();
+        for (int i = tid; i < In; i += NT) D.cdf[n][i] = wsc[i];
       }
       cluster.sync();
     }
+  }
+  if constexpr (kTC) {
+    tc_fence_before();
+    __syncthreads();
+    if (tid < 32) tmem_dealloc(tbase, 512);
   }
 }
 
@@ -456,28 +787,35 @@ static cudaError_t launch_one(const ProbDesc *descs, int nprob, const StepLayout
   return cudaLaunchKernelEx(&cfg, step_cluster_kernel<T, XT, RMAX>, descs, lay, t0, nsteps);
 }
 
+// RMAX: register length of one chain row; the smallest of 4, 8, 12, 16 that
+// holds every rank of the problem.
 #define TRSGD_DISPATCH(FN, ...)                                                        \
   do {                                                                                 \
     if (core_dtype == 0) {                                                             \
       if (rmax <= 4) return FN<double, double, 4>(__VA_ARGS__);                        \
       if (rmax <= 8) return FN<double, double, 8>(__VA_ARGS__);                        \
+      if (rmax <= 12) return FN<double, double, 12>(__VA_ARGS__);                      \
       return FN<double, double, 16>(__VA_ARGS__);                                      \
+    } else if (x_dtype == 2) {                                                         \
+      if (rmax <= 4) return FN<float, __nv_bfloat16, 4>(__VA_ARGS__);                  \
+      if (rmax <= 8) return FN<float, __nv_bfloat16, 8>(__VA_ARGS__);                  \
+      if (rmax <= 12) return FN<float, __nv_bfloat16, 12>(__VA_ARGS__);                \
+      return FN<float, __nv_bfloat16, 16>(__VA_ARGS__);                                \
     } else {                                                                           \
       if (rmax <= 4) return FN<float, float, 4>(__VA_ARGS__);                          \
       if (rmax <= 8) return FN<float, float, 8>(__VA_ARGS__);                          \
+      if (rmax <= 12) return FN<float, float, 12>(__VA_ARGS__);                        \
       return FN<float, float, 16>(__VA_ARGS__);                                        \
     }                                                                                  \
   } while (0)
 
 cudaError_t step_kernel_prepare(int core_dtype, int x_dtype, int rmax, const StepLayout &lay) {
-  (void)x_dtype;
   TRSGD_DISPATCH(prepare_one, lay);
 }
 
 cudaError_t launch_step(int core_dtype, int x_dtype, int rmax, const ProbDesc *descs, int nprob,
                         const StepLayout &lay, int threads, long long t0, int nsteps,
                         cudaStream_t s) {
-  (void)x_dtype;
   TRSGD_DISPATCH(launch_one, descs, nprob, lay, threads, t0, nsteps, s);
 }
 

@@ -125,10 +125,10 @@ def test_euclidean_distribution_steps(prec):
     case.solver.set_debug(True)
     tol = 1e-12 if prec == 0 else 2e-5
     for t in range(6):
-        if prec == 1:
-            for k, G in enumerate(case.device_cores()):
-                case.state.cores[k] = G
-            # the device tables were built from the device cores of the last step
+        # restart the oracle from the device cores: its tables are then built from
+        # the same values as the kernel's in-kernel table update, so p_F is bit-exact
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, tol)
@@ -196,3 +196,45 @@ def test_run_stops_at_tolerance():
     # start from the planted cores: RSE is already ~0
     done, r = case.solver.run(0, 1000, chunk=10, tol=1.0, Xref=case.Xtd)
     assert done == 10 and 0 <= r <= 1.0
+
+
+def _bf16_round(a):
+    t = torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64)
+    return t.numpy()
+
+
+@pytest.mark.parametrize("shape,cluster", [
+    (dict(dims=[12, 9, 10, 11], ranks=[3, 4, 2, 3], J=100), 4),
+    (dict(dims=[40, 30, 20], ranks=[4, 4, 4], J=90), 16),
+    (dict(dims=[150, 20, 25], ranks=[8, 8, 8], J=64), 2),     # 2 row chunks of the 128-row tile
+    (dict(dims=[30, 40], ranks=[4, 3], J=17), 1),
+])
+def test_bf16_mixed_tensor_core_steps(shape, cluster):
+    """BF16_MIXED: fibers stored in bfloat16, residual on tensor cores with
+    split-BF16 operands (hi*hi + hi*lo + lo*hi, about 2^-16 relative per
+    product), gradient on tensor cores with the weighted residual in BF16
+    (2^-9 relative per entry), FP32 accumulation.  The oracle gets the same
+    BF16-rounded X.  Bounds: Z 2e-5, E 2e-4, g 1e-2, cores 1e-4 (one step)."""
+    A = api()
+    case = Case(prec=1, alpha=0.05, **shape)
+    Xb = _bf16_round(case.X)
+    case.X = Xb
+    pc = A.ProblemConfig(dims=case.dims, ranks=case.ranks, J=case.J, prec=A._abi.BF16_MIXED,
+                         x_dtype=A._abi.DTYPE_F32, alpha=0.05, seed=case.ocfg.seed)
+    case.solver.close()
+    case.solver = A.Solver([pc], [case.Xd], [case.cores_d])
+    case.pc = pc
+    case.solver.launch_shape(cluster=cluster, threads=512)
+    case.solver.set_debug(True)
+    for t in range(4):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        d = case.debug(rec["n"])
+        np.testing.assert_array_equal(d["idx"], rec["idx"])
+        assert rel(d["Z"], rec["Z"]) < 2e-5
+        assert rel(d["E"], rec["E"]) < 2e-4
+        assert rel(d["g"], rec["g"]) < 1e-2
+        for G, O in zip(case.device_cores(), case.state.cores):
+            assert rel(G, O) < 1e-4
