@@ -144,6 +144,33 @@ trsgd_status trsgd_run(trsgd_handle *h, int64_t t0, int64_t T, int64_t chunk,
 trsgd_status trsgd_rel_error(trsgd_handle *h, int32_t problem,
                              const void *Xref_dev, double *out);
 
+/* Relative error without any device allocation.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc or
+ * cudaFree, for example code whose device memory is owned entirely by another
+ * allocator (a framework's caching pool or a fixed per-process budget), or a
+ * latency-sensitive caller that cannot accept the implicit device
+ * synchronisation an allocation or free may cause.  It needs no handle.
+ *   Same result as trsgd_rel_error: RSE = ||TR(G) - X_ref||_F / ||X_ref||_F
+ *   (Sec. 4), reduced in FP64 in a fixed order.  N, I, R, dtype (F64 or F32,
+ *   for the cores and X_ref) and cores_dev as in trsgd_reconstruct; Xref_dev
+ *   a tensor of dims I (i_1 fastest); out_dev receives one double on the
+ *   device.  Enqueued on `stream`, no synchronisation.
+ * Scratch: one pair of FP64 partial sums per tile of 64 columns of X_[1],
+ *   held in a fixed array inside the library (1 MiB on every GPU that loads
+ *   the library, kept until the process exits).  Sizes beyond it, i.e.
+ *   prod_{k>1} I_k > 4,194,304, return TRSGD_EINVAL; ranks above 16 return
+ *   TRSGD_EUNSUPPORTED.  Every call overwrites the entries it uses, so nothing
+ *   needs clearing, but all calls share the array: calls that can overlap on
+ *   the GPU (different streams without ordering between them) race and must
+ *   be serialised by the caller.
+ * The first call on each device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  No cudaMalloc, cudaFree or allocating library routine is
+ * called. */
+trsgd_status trsgd_rel_error_static(int32_t N, const int64_t *I, const int64_t *R, int32_t dtype,
+                                    const void *const *cores_dev, const void *Xref_dev,
+                                    double *out_dev, void *stream);
+
 /* Full reconstruction X = TR({G_n}) (element formula of the Introduction,
  * evaluated as X_[1] = G_{1(2)} (G^{!=1}_{[2]})^T).  dtype applies to the
  * cores and to X; X_dev receives prod(I) elements, i_1 fastest.  Enqueued on

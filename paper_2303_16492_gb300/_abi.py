@@ -57,6 +57,10 @@ _SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),
     "trsgd_rel_error": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
                                        ctypes.POINTER(ctypes.c_double)]),
+    "trsgd_rel_error_static": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_void_p]),
     "trsgd_reconstruct": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int64), ctypes.c_int32,
                                          ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p]),
