@@ -9,6 +9,7 @@
 #include "trsgd.h"
 #include "common.cuh"
 #include "internal.h"
+#include "tables.cuh"
 
 using namespace trsgd;
 
@@ -89,8 +90,7 @@ static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
     if (c.prec == TRSGD_FP32 && c.x_dtype != TRSGD_DTYPE_F32) return TRSGD_EINVAL;
     if (c.prec == TRSGD_BF16_MIXED && c.x_dtype == TRSGD_DTYPE_F64) return TRSGD_EINVAL;
     // this build
-    if (c.dist == TRSGD_DIST_LEVERAGE || c.dist == TRSGD_DIST_OPTIMAL) return TRSGD_EUNSUPPORTED;
-    if (c.J_H != 0) return TRSGD_EUNSUPPORTED;
+    if (c.dist == TRSGD_DIST_OPTIMAL) return TRSGD_EUNSUPPORTED;
     for (int k = 0; k < c.N; ++k) {
       if (c.R[k] > kMaxRank) return TRSGD_EUNSUPPORTED;
       const int64_t Q = c.R[k] * c.R[(k + 1) % c.N];
@@ -155,7 +155,7 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   };
   L.off_bar = take(16, 16);
   L.off_misc = take(64, 16);
-  L.off_const = take(16 * 8, 16);
+  L.off_const = take(32 * 8, 16);
   L.off_desc = take(rup(sizeof(ProbDesc), 16), 16);
   L.off_idx = take((size_t)L.JB * kMaxOrder * 4, 16);
   L.off_col = take((size_t)L.JB * 8, 16);
@@ -163,6 +163,18 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   L.off_wt = take(JB4 * st, 16);
   L.off_x = take(JB4 * L.ldxs * (tc ? sx : std::max(sx, st)), 128);
   L.off_z = take(JB4 * L.ldq * st, 128);
+  {
+    int JHmax = 0;
+    for (const auto &c : h.cfg)
+      if (c.variant == TRSGD_SCALED) JHmax = std::max(JHmax, (int)c.J_H);
+    L.JBH = (JHmax + C - 1) / C;
+    if (L.JBH > 0) {
+      const size_t JBH4 = rup((size_t)L.JBH, 4);
+      L.off_hz = take(JBH4 * L.ldq * st, 128);
+      L.off_hidx = take((size_t)L.JBH * kMaxOrder * 4, 16);
+      L.off_hw = take(JBH4 * st, 16);
+    }
+  }
   if (tc) {
     L.off_zh = take((size_t)L.jbp * L.qp * 2, 128);
     L.off_zl = take((size_t)L.jbp * L.qp * 2, 128);
@@ -210,6 +222,12 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   L.off_p1 = L.off_p0 + pb_bytes;
   L.sb_ok = (tail0 + sb_bytes + 2 * pb_bytes <= limit) ? 1 : 0;
   if (L.sb_ok) end = std::max(end, tail0 + sb_bytes + 2 * pb_bytes);
+  // the leverage table of the updated core is rebuilt in the tail by CTA 0
+  for (const auto &c : h.cfg) {
+    if (c.dist != TRSGD_DIST_LEVERAGE) continue;
+    for (int k = 0; k < c.N; ++k)
+      end = std::max(end, tail0 + leverage_scratch_bytes((int)c.I[k], (int)(c.R[k] * c.R[(k + 1) % c.N]), st));
+  }
   // the tensor-core path allocates all 512 TMEM columns: keep one CTA per SM
   if (tc) end = std::max(end, (size_t)120 * 1024);
   L.total = rup(end, 128);
@@ -300,6 +318,7 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
     std::memset(&D, 0, sizeof(D));
     D.N = c.N;
     D.J = (int)c.J;
+    D.JH = c.variant == TRSGD_SCALED ? (int)c.J_H : 0;
     D.dist = c.dist;
     D.variant = c.variant;
     D.rule = c.rule;
@@ -344,6 +363,10 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
         if ((e = h->buf.alloc((void **)&D.prob[k], (size_t)c.I[k] * 8)) != cudaSuccess ||
             (e = h->buf.alloc((void **)&D.cdf[k], (size_t)c.I[k] * 8)) != cudaSuccess ||
             (e = h->buf.alloc((void **)&D.snorm[k], (size_t)c.I[k] * 8)) != cudaSuccess)
+          return fail(from_cuda(e));
+        if (c.dist == TRSGD_DIST_LEVERAGE &&
+            (e = launch_leverage_table(h->core_dtype, D.cores[k], (int)c.I[k], (int)Q, D.prob[k], D.cdf[k],
+                                       h->d_status, h->stream)) != cudaSuccess)
           return fail(from_cuda(e));
         if (c.dist == TRSGD_DIST_EUCLIDEAN &&
             (e = launch_euclid_table(h->core_dtype, D.cores[k], (int)c.I[k], (int)Q, D.snorm[k], D.prob[k],

@@ -10,6 +10,7 @@ namespace trsgd {
 // One TR problem as the step kernel sees it.
 struct ProbDesc {
   int N, J, dist, variant, rule, prec;
+  int JH;                         // |H| of the scaled variant (0: H = F)
   int I[8], R[8];
   double alpha, eta, b, eps, damping;
   unsigned long long seed;
@@ -46,7 +47,9 @@ struct StepLayout {
   // off_sb aliases the region [off_reg, total): the staged slices are dead
   // before the Gram / chunk buffers and the CDF scratch are written
   size_t off_desc, off_idx, off_col, off_w, off_wt, off_bar, off_x, off_z, off_reg, off_h64,
-      off_hdiag, off_gown, off_misc, off_const, off_sb, off_p0, off_p1, off_zh, off_zl, off_ew, total;
+      off_hdiag, off_gown, off_misc, off_const, off_sb, off_p0, off_p1, off_zh, off_zl, off_ew,
+      off_hz, off_hidx, off_hw, total;
+  int JBH;        // max Hessian-batch samples per CTA
 };
 
 // kernel launchers (defined in the .cu files)
@@ -60,6 +63,8 @@ cudaError_t launch_mode_copy(int src_dtype, int dst_dtype, const void *X, void *
                              long long In, long long B, long long ld, cudaStream_t s);
 cudaError_t launch_euclid_table(int core_dtype, const void *G, int I, int Q, double *snorm,
                                 double *prob, unsigned long long *cdf, cudaStream_t s);
+cudaError_t launch_leverage_table(int core_dtype, const void *G, int I, int Q, double *prob,
+                                  unsigned long long *cdf, int *status, cudaStream_t s);
 cudaError_t launch_reconstruct(int dtype, int N, const int *I, const int *R,
                                const void *const *cores, void *X, const void *Xref,
                                double *sums, cudaStream_t s);

@@ -2,6 +2,7 @@
 // tables, full reconstruction TR({G_n}) and the relative error (RSE).
 #include "blocks.cuh"
 #include "internal.h"
+#include "tables.cuh"
 
 namespace trsgd {
 
@@ -125,6 +126,30 @@ cudaError_t launch_euclid_table(int core_dtype, const void *G, int I, int Q, dou
   else
     euclid_table_kernel<float><<<1, 256, 0, s>>>(static_cast<const float *>(G), I, Q, snorm, prob, cdf, nullptr);
   return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) leverage_init_kernel(const T *G, int I, int Q, double *prob,
+                                                            unsigned long long *cdf, int *status) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  leverage_table_cta<T>(G, I, Q, smem, prob, cdf, status);
+}
+
+cudaError_t launch_leverage_table(int core_dtype, const void *G, int I, int Q, double *prob,
+                                  unsigned long long *cdf, int *status, cudaStream_t s) {
+  const size_t bytes = leverage_scratch_bytes(I, Q, core_dtype == 0 ? 8 : 4);
+  if (bytes > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (core_dtype == 0) {
+    e = cudaFuncSetAttribute(leverage_init_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      leverage_init_kernel<double><<<1, 512, bytes, s>>>(static_cast<const double *>(G), I, Q, prob, cdf, status);
+  } else {
+    e = cudaFuncSetAttribute(leverage_init_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      leverage_init_kernel<float><<<1, 512, bytes, s>>>(static_cast<const float *>(G), I, Q, prob, cdf, status);
+  }
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 // ---------------------------------------------------------------------------

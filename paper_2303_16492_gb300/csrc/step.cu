@@ -32,6 +32,7 @@
 // TRSGD_ETIMEOUT.
 #include "blocks.cuh"
 #include "internal.h"
+#include "tables.cuh"
 
 #include <type_traits>
 
@@ -67,6 +68,55 @@ __device__ __noinline__ bool cholesky_cta(double *A, int Q, int ld) {
   }
   __syncthreads();
   return true;
+}
+
+// sum_{a < LEN} p[a * PS] * s[a] with compile-time length and stride
+template <int LEN, int PS, typename T>
+__device__ __forceinline__ T dotk(const T *p, const T *s) {
+  T acc = T(0);
+#pragma unroll
+  for (int a = 0; a < LEN; ++a) acc = fma(p[a * PS], s[a], acc);
+  return acc;
+}
+
+// One factor of the batched slice chain for a uniform rank RU: P_{q+1} =
+// P_q S_q for the samples jl = warp, warp + nwarps, ... of this CTA, lane l
+// computing entries l, l + 32, ... (row-major [r'][b]).  All of a lane's
+// dot products are issued together (independent FMA chains); rows past the
+// last entry are computed from clamped addresses and not stored.
+template <int RU, bool FIRST, typename T>
+__device__ __noinline__ void chain_factor_uniform(const T *src, int sstride, const T *sfac, int qpad, T *dst,
+                                                  int dstride, int jb) {
+  constexpr int PER = RU * RU, NU = (PER + 31) / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  int po[NU], so[NU], dof[NU];
+  bool ok[NU];
+#pragma unroll
+  for (int u = 0; u < NU; ++u) {
+    const int it0 = lane + 32 * u;
+    ok[u] = it0 < PER;
+    const int it = ok[u] ? it0 : PER - 1;
+    const int rp = it / RU, b = it - rp * RU;
+    po[u] = FIRST ? rp : rp * RU;
+    so[u] = b * RU;
+    dof[u] = it;
+  }
+  for (int jl = warp; jl < jb; jl += nwarps) {
+    const T *prow = src + (size_t)jl * sstride;
+    const T *S = sfac + (size_t)jl * qpad;
+    T acc[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) acc[u] = T(0);
+#pragma unroll
+    for (int a = 0; a < RU; ++a) {
+#pragma unroll
+      for (int u = 0; u < NU; ++u) acc[u] = fma(prow[po[u] + a * (FIRST ? RU : 1)], S[so[u] + a], acc[u]);
+    }
+    T *drow = dst + (size_t)jl * dstride;
+#pragma unroll
+    for (int u = 0; u < NU; ++u)
+      if (ok[u]) drow[dof[u]] = acc[u];
+  }
 }
 
 // Step rule on one entry of G_n: fixed alpha (Eq. update_brsgd) or AdaGrad
@@ -137,6 +187,9 @@ __global__ void __launch_bounds__(kMaxThreads)
   for (int k = 0; k < kMaxOrder; ++k) { I[k] = D.I[k]; R[k] = D.R[k]; }
   const bool scaled = D.variant == 1;
   const bool rec = D.dbg && pidx == 0;
+  int ru = R[0];   // the common rank when all ranks are equal, else 0
+  for (int k = 1; k < N; ++k)
+    if (R[k] != ru) ru = 0;
   const int ldq = lay.ldq;
   const T alpha_t = (T)D.alpha, eta_t = (T)D.eta, b_t = (T)D.b;
   if (tid < N) {   // FP64 constants, once per launch (FP64 throughput is scarce)
@@ -145,8 +198,11 @@ __global__ void __launch_bounds__(kMaxThreads)
     for (int k = 0; k < N; ++k)
       if (k != tid) jn = __dmul_rn(jn, (double)I[k]);
     cst[8 + tid] = __dmul_rn((double)J, jn);
+    cst[24 + tid] = __dmul_rn((double)D.JH, jn);   // |H| J_n
   }
+  if (tid == 0) cst[16] = __ddiv_rn(1.0, (double)J);
   __syncthreads();
+  const T wt_uni = (T)cst[16];
   uint32_t phase = 0;
 
   // sum of one element of a shared-memory buffer over the cluster's CTAs in
@@ -317,40 +373,43 @@ __global__ void __launch_bounds__(kMaxThreads)
     T *Gn = static_cast<T *>(D.cores[n]);
     T *accn = static_cast<T *>(D.acc[n]);
 
-    // ---- A1: slice indices (Algorithm 2) -----------------------------------
-    for (int e = tid; e < jb * L; e += NT) {
-      const int jl = e / L, sp = e - jl * L, k = order[sp];
-      const uint64_t u = draw_u64(D.seed, t, kStreamF, k, (uint32_t)(j0 + jl));
-      int i;
-      if (D.dist == 0) {
-        i = (int)mulhi64(u, (uint64_t)I[k]);
-      } else {
-        const unsigned long long *cdf = D.cdf[k];
-        const uint64_t W = __ldcg(cdf + I[k] - 1);
-        i = cdf_search(cdf, I[k], mulhi64(u, W));
-      }
-      idx_s[jl * kMaxOrder + k] = i;
-    }
-    __syncthreads();
-
-    // ---- A2: p_F (product in ring order), weights, fiber column -------------
+    // ---- A1/A2: per sample, slice indices (Algorithm 2), p_F (product in ring
+    // order), weight 1/(|F| J_n p_F) and fiber column -------------------------
     for (int jl = tid; jl < jb4; jl += NT) {
       if (jl >= jb) {
         wt_s[jl] = T(0);
         continue;
       }
+      const bool uni = D.dist == 0;
+      const bool need_pf = !uni || rec;   // uniform: every p_F = 1/J_n, weight 1/|F| (to rounding)
       double pF = 1.0;
       long long col = 0, st = 1;
-      for (int sp = 0; sp < L; ++sp) {
-        const int k = order[sp], i = idx_s[jl * kMaxOrder + k];
-        const double pk = (D.dist == 0) ? cst[k] : __ldcg(D.prob[k] + i);
-        pF = __dmul_rn(pF, pk);
+      uint64_t us[kMaxOrder];
+#pragma unroll
+      for (int sp = 0; sp < kMaxOrder; ++sp)
+        us[sp] = (sp < L) ? draw_u64(D.seed, t, kStreamF, order[sp], (uint32_t)(j0 + jl)) : 0ull;
+#pragma unroll
+      for (int sp = 0; sp < kMaxOrder; ++sp) {
+        if (sp >= L) break;
+        const int k = order[sp], Ik = I[k];
+        const uint64_t u = us[sp];
+        int i;
+        if (uni) {
+          i = (int)mulhi64(u, (uint64_t)Ik);
+          if (need_pf) pF = __dmul_rn(pF, cst[k]);
+        } else {
+          const unsigned long long *cdf = D.cdf[k];
+          const uint64_t W = __ldcg(cdf + Ik - 1);
+          i = cdf_search(cdf, Ik, mulhi64(u, W));
+          pF = __dmul_rn(pF, __ldcg(D.prob[k] + i));
+        }
+        idx_s[jl * kMaxOrder + k] = i;
         col += (long long)i * st;
-        st *= I[k];
+        st *= Ik;
       }
-      const double w = __ddiv_rn(1.0, __dmul_rn(cst[8 + n], pF));
+      const double w = need_pf ? __ddiv_rn(1.0, __dmul_rn(cst[8 + n], pF)) : cst[16];
       w_s[jl] = w;
-      wt_s[jl] = (T)w;
+      wt_s[jl] = need_pf ? (T)w : wt_uni;
       col_s[jl] = col;
       if (rec) {
         D.dbg_pf[j0 + jl] = pF;
@@ -424,6 +483,7 @@ __global__ void __launch_bounds__(kMaxThreads)
       // product lands in Z.  Intermediates ping-pong between two buffers.
       T *pbuf[2] = {reinterpret_cast<T *>(smem + lay.off_p0), reinterpret_cast<T *>(smem + lay.off_p1)};
       const int pst = lay.pstride;
+      const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
       for (int q = 1; q < L; ++q) {
         const int k = order[q], Ra = R[k], Rb = R[(k + 1) % N];
         const bool last = q == L - 1;
@@ -431,20 +491,47 @@ __global__ void __launch_bounds__(kMaxThreads)
         const int dstride = last ? ldq : pst;
         const T *src = (q == 1) ? sb + soff[0] : pbuf[(q - 1) & 1];
         const int sstride = (q == 1) ? qpad[0] : pst;
-        const int per = Rn1 * Rb;
-        for (int e = tid; e < jb * per; e += NT) {
-          const int jl = e / per, rem = e - jl * per, rp = rem / Rb, b = rem - rp * Rb;
-          const T *prow = src + (size_t)jl * sstride;
-          const T *S = sb + soff[q] + (size_t)jl * qpad[q] + b * Ra;
-          T acc = T(0);
-          if (q == 1) {
-#pragma unroll 4
-            for (int a = 0; a < Ra; ++a) acc = fma(prow[rp + a * Rn1], S[a], acc);
-          } else {
-#pragma unroll 4
-            for (int a = 0; a < Ra; ++a) acc = fma(prow[rp * Ra + a], S[a], acc);
+        const int per = Rn1 * Rb;              // entries of P_{q+1} per sample (<= 256)
+        bool done = true;
+        switch (ru) {
+          case 4: q == 1 ? chain_factor_uniform<4, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
+                         : chain_factor_uniform<4, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
+          case 8: q == 1 ? chain_factor_uniform<8, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
+                         : chain_factor_uniform<8, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
+          case 10: q == 1 ? chain_factor_uniform<10, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
+                          : chain_factor_uniform<10, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
+          case 16: q == 1 ? chain_factor_uniform<16, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
+                          : chain_factor_uniform<16, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
+          default: done = false;
+        }
+        if (!done) {
+          // general ranks: this lane's entries it = lane + 32 u, row r' and column b
+          int pofs[8], pstep[8], sofs[8], dofs[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int it = lane + 32 * u;
+            const int rp = it / Rb, bb = it - rp * Rb;
+            pofs[u] = (q == 1) ? rp : rp * Ra;
+            pstep[u] = (q == 1) ? Rn1 : 1;
+            sofs[u] = bb * Ra;
+            dofs[u] = rp * Rb + bb;
           }
-          dst[(size_t)jl * dstride + rp * Rb + b] = acc;
+          for (int jl = warp; jl < jb; jl += nwarps) {
+            const T *prow = src + (size_t)jl * sstride;
+            const T *S = sb + soff[q] + (size_t)jl * qpad[q];
+            T *drow = dst + (size_t)jl * dstride;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              if (lane + 32 * u < per) {
+                const T *pp = prow + pofs[u];
+                const T *sc = S + sofs[u];
+                const int ps = pstep[u];
+                T acc = T(0);
+                for (int a = 0; a < Ra; ++a) acc = fma(pp[a * ps], sc[a], acc);
+                drow[dofs[u]] = acc;
+              }
+            }
+          }
         }
         __syncthreads();
       }
@@ -517,7 +604,67 @@ __global__ void __launch_bounds__(kMaxThreads)
     // ---- S: preconditioner h = Z^T D Z / (|F| J_n) + eta^t I (FP64 solve) ---
     if (scaled) {
       const int QH = lay.QH;
-      gemm_s<4, true, true, T>(Q, Q, jb, zs, ldq, zs, ldq, wt_s,
+      const T *gz = zs;     // rows of the Hessian batch: F itself, or an independent H
+      const T *gw = wt_s;
+      int gjb = jb;
+      if (D.JH > 0) {
+        // |H| rows drawn on their own Philox stream with the same distributions;
+        // weights 1/(|H| J_n p_H) (Eq. S_hessian)
+        const int JH = D.JH;
+        const int h0 = (int)((long long)JH * c / C), h1 = (int)((long long)JH * (c + 1) / C);
+        const int jbh = h1 - h0, jbh4 = (jbh + 3) & ~3;
+        int *hidx = reinterpret_cast<int *>(smem + lay.off_hidx);
+        T *hw = reinterpret_cast<T *>(smem + lay.off_hw);
+        T *hz = reinterpret_cast<T *>(smem + lay.off_hz);
+        for (int jl = tid; jl < jbh4; jl += NT) {
+          if (jl >= jbh) {
+            hw[jl] = T(0);
+            continue;
+          }
+          double pH = 1.0;
+          for (int sp = 0; sp < L; ++sp) {
+            const int k = order[sp], Ik = I[k];
+            const uint64_t u = draw_u64(D.seed, t, kStreamH, k, (uint32_t)(h0 + jl));
+            int i;
+            if (D.dist == 0) {
+              i = (int)mulhi64(u, (uint64_t)Ik);
+              pH = __dmul_rn(pH, cst[k]);
+            } else {
+              const unsigned long long *cdf = D.cdf[k];
+              const uint64_t W = __ldcg(cdf + Ik - 1);
+              i = cdf_search(cdf, Ik, mulhi64(u, W));
+              pH = __dmul_rn(pH, __ldcg(D.prob[k] + i));
+            }
+            hidx[jl * kMaxOrder + k] = i;
+          }
+          hw[jl] = (T)__ddiv_rn(1.0, __dmul_rn(cst[24 + n], pH));
+        }
+        __syncthreads();
+        const T *cores_c[kMaxOrder];
+#pragma unroll
+        for (int q = 0; q < kMaxOrder; ++q) cores_c[q] = static_cast<const T *>(D.cores[q]);
+        for (int e = tid; e < jbh * Rn1; e += NT) {
+          const int jl = e / Rn1, rp = e - jl * Rn1;
+          int sidx[kMaxOrder];
+#pragma unroll
+          for (int q = 0; q < kMaxOrder; ++q) sidx[q] = (q < L) ? hidx[jl * kMaxOrder + order[q]] : 0;
+          T row[RMAX];
+          chain_row<RMAX, T>(cores_c, R, N, order, sidx, L, rp, row);
+          T *zrow = hz + (size_t)jl * ldq + rp * Rn;
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r)
+            if (r < Rn) zrow[r] = row[r];
+        }
+        for (int e = tid; e < jbh4 * Q4; e += NT) {
+          const int jl = e / Q4, q = e - jl * Q4;
+          if (jl >= jbh || q >= Q) hz[(size_t)jl * ldq + q] = T(0);
+        }
+        __syncthreads();
+        gz = hz;
+        gw = hw;
+        gjb = jbh;
+      }
+      gemm_s<4, true, true, T>(Q, Q, gjb, gz, ldq, gz, ldq, gw,
                                [=](int a, int b, T v) { reg[(size_t)a * ldq + b] = v; });
       cluster.sync();
       double *h0 = cluster.map_shared_rank(h64, 0);
@@ -611,9 +758,8 @@ __global__ void __launch_bounds__(kMaxThreads)
       }
       cluster.sync();
       const int r0 = ti * c / C, r1 = ti * (c + 1) / C;
-      for (int e = tid; e < (r1 - r0) * Q; e += NT) {
-        const int ii = r0 + e / Q, q = e % Q;
-        const T g = cluster_sum(reg, (size_t)ii * ldq + q);
+      // reduced gradient of one owned entry -> step rule and update (or kept for the solve)
+      auto own_entry = [&](int ii, int q, T g) {
         const size_t gi = (size_t)(i0 + ii) * Q + q;
         if (rec) static_cast<T *>(D.dbg_g)[gi] = g;
         if (scaled) {
@@ -625,6 +771,42 @@ __global__ void __launch_bounds__(kMaxThreads)
           Gn[gi] = nv;
           gown[(size_t)(ii - r0) * ldq + q] = nv;
           if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
+        }
+      };
+      if constexpr (sizeof(T) == 4) {
+        if ((Q & 3) == 0) {   // 16-byte remote loads, same fixed CTA order per entry
+          const int Qv = Q >> 2;
+          for (int e = tid; e < (r1 - r0) * Qv; e += NT) {
+            const int ii = r0 + e / Qv, q0 = (e - (e / Qv) * Qv) * 4;
+            float4 v[16];
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc)
+              v[cc] = (cc < C) ? *reinterpret_cast<const float4 *>(cluster.map_shared_rank(reg, cc) + (size_t)ii * ldq + q0)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int cc = 0; cc < 16; ++cc)
+              if (cc < C) {
+                g.x += v[cc].x;
+                g.y += v[cc].y;
+                g.z += v[cc].z;
+                g.w += v[cc].w;
+              }
+            own_entry(ii, q0, g.x);
+            own_entry(ii, q0 + 1, g.y);
+            own_entry(ii, q0 + 2, g.z);
+            own_entry(ii, q0 + 3, g.w);
+          }
+        } else {
+          for (int e = tid; e < (r1 - r0) * Q; e += NT) {
+            const int ii = r0 + e / Q, q = e % Q;
+            own_entry(ii, q, cluster_sum(reg, (size_t)ii * ldq + q));
+          }
+        }
+      } else {
+        for (int e = tid; e < (r1 - r0) * Q; e += NT) {
+          const int ii = r0 + e / Q, q = e % Q;
+          own_entry(ii, q, cluster_sum(reg, (size_t)ii * ldq + q));
         }
       }
       if (!scaled && D.dist == 2) {
@@ -716,6 +898,12 @@ __global__ void __launch_bounds__(kMaxThreads)
           D.snorm[n][r0 + rr] = sn;
         }
       }
+      cluster.sync();
+    }
+
+    // ---- leverage table of core n for the next iteration (CTA 0) ----------
+    if (D.dist == 1) {
+      if (c == 0) leverage_table_cta<T>(Gn, In, Q, smem + lay.off_reg, D.prob[n], D.cdf[n], D.status);
       cluster.sync();
     }
 

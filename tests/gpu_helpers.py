@@ -49,14 +49,14 @@ class Case:
         ocfg = dict(cfg)
         self.ocfg = ob.Config(J=J, seed=cfg.get("seed_key", 3), **{k: v for k, v in ocfg.items()
                                                                   if k in ("dist", "variant", "rule", "alpha",
-                                                                           "eta", "b", "eps", "damping")})
+                                                                           "eta", "b", "eps", "damping", "J_H")})
         dev = "cuda"
         self.Xd = torch.from_numpy(np.ascontiguousarray(self.X.ravel(order="F")).astype(self.dtype_np)).to(dev)
         self.Xtd = torch.from_numpy(np.ascontiguousarray(self.X_true.ravel(order="F")).astype(self.dtype_np)).to(dev)
         self.cores_d = [torch.from_numpy(G.astype(self.dtype_np)).to(dev) for G in to_lib_cores(start)]
         pc = A.ProblemConfig(dims=self.dims, ranks=self.ranks, J=J, prec=prec, seed=self.ocfg.seed,
                              **{k: v for k, v in ocfg.items() if k in ("dist", "variant", "rule", "alpha", "eta",
-                                                                       "b", "eps", "damping")})
+                                                                       "b", "eps", "damping", "J_H")})
         self.pc = pc
         self.solver = A.Solver([pc], [self.Xd], [self.cores_d])
 

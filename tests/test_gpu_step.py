@@ -238,3 +238,44 @@ def test_bf16_mixed_tensor_core_steps(shape, cluster):
         assert rel(d["g"], rec["g"]) < 1e-2
         for G, O in zip(case.device_cores(), case.state.cores):
             assert rel(G, O) < 1e-4
+
+
+@pytest.mark.parametrize("prec,dims,ranks", [
+    (0, [20, 18, 22], [3, 3, 3]),        # tall cores (I > Q): l_i from the Cholesky factor of A^T A
+    (0, [8, 30, 9], [3, 4, 3]),          # mixed: core 0 wide (8 <= 12), cores 1, 2 tall
+    (1, [10, 12, 9], [4, 4, 4]),         # all wide (I <= Q): leverage is exactly uniform
+])
+def test_leverage_distribution_steps(prec, dims, ranks):
+    """Lemma lev_est: p_k(i) = l_i(G_{k(2)}) / rank, rebuilt for the updated
+    core after every step.  FP64 leverage scores agree with the oracle's SVD to
+    ~1e-15, so the integer CDFs agree and indices and p_F match."""
+    case = Case(dims=dims, ranks=ranks, J=60, prec=prec, alpha=0.05, dist=ob.DIST_LEVERAGE)
+    case.solver.set_debug(True)
+    tol = 1e-12 if prec == 0 else 2e-5
+    for t in range(6):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        d = case.debug(rec["n"])
+        np.testing.assert_array_equal(d["idx"], rec["idx"])
+        assert rel(d["pF"], rec["pF"]) < 1e-12
+        assert rel(d["g"], rec["g"]) < tol
+        for G, O in zip(case.device_cores(), case.state.cores):
+            assert rel(G, O) < tol
+
+
+@pytest.mark.parametrize("prec,dist", [(0, ob.DIST_UNIFORM), (0, ob.DIST_EUCLIDEAN), (1, ob.DIST_UNIFORM)])
+def test_scaled_independent_hessian_batch(prec, dist):
+    """Eq. S_hessian with H independent of F: |H| = 70 rows drawn on the H
+    stream (same distributions), weights 1/(|H| J_n p_H)."""
+    case = Case(dims=[16, 15, 14], ranks=[3, 2, 3], J=45, prec=prec, alpha=0.3, variant=ob.VARIANT_SCALED,
+                damping=1e-3, J_H=70, dist=dist)
+    case.solver.set_debug(True)
+    tol = 1e-11 if prec == 0 else 1e-4
+    for t in range(4):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, tol)
