@@ -61,6 +61,8 @@ struct trsgd_handle {
   int64_t t_next = 0;
   int64_t launches = 0;
   bool dbg = false;
+  bool optimal = false;   // problem 0 samples from the optimal distribution
+  OptBuffers opt = {};
   size_t dbg_bytes[8] = {};
   void *dbg_ptr[8] = {};
 };
@@ -90,7 +92,7 @@ static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
     if (c.prec == TRSGD_FP32 && c.x_dtype != TRSGD_DTYPE_F32) return TRSGD_EINVAL;
     if (c.prec == TRSGD_BF16_MIXED && c.x_dtype == TRSGD_DTYPE_F64) return TRSGD_EINVAL;
     // this build
-    if (c.dist == TRSGD_DIST_OPTIMAL) return TRSGD_EUNSUPPORTED;
+    if (c.dist == TRSGD_DIST_OPTIMAL && np > 1) return TRSGD_EUNSUPPORTED;
     for (int k = 0; k < c.N; ++k) {
       if (c.R[k] > kMaxRank) return TRSGD_EUNSUPPORTED;
       const int64_t Q = c.R[k] * c.R[(k + 1) % c.N];
@@ -376,6 +378,34 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
     }
     ncore += c.N;
   }
+  if (cfg[0].dist == TRSGD_DIST_OPTIMAL) {
+    const trsgd_config &c = cfg[0];
+    long long jnmax = 1;
+    for (int n = 0; n < c.N; ++n) {
+      long long jn = 1;
+      for (int k = 0; k < c.N; ++k)
+        if (k != n) jn *= c.I[k];
+      jnmax = std::max(jnmax, jn);
+    }
+    const long long nb = (jnmax + 1023) / 1024;
+    OptBuffers &b = h->opt;
+    if ((e = h->buf.alloc((void **)&b.a, jnmax * 8)) != cudaSuccess ||
+        (e = h->buf.alloc((void **)&b.q, jnmax * 8)) != cudaSuccess ||
+        (e = h->buf.alloc((void **)&b.cdf, jnmax * 8)) != cudaSuccess ||
+        (e = h->buf.alloc((void **)&b.bsum, nb * 8)) != cudaSuccess ||
+        (e = h->buf.alloc((void **)&b.btot, nb * 8)) != cudaSuccess ||
+        (e = h->buf.alloc((void **)&b.total, 16)) != cudaSuccess ||
+        (e = h->buf.alloc((void **)&b.idx, (size_t)c.J * c.N * 4)) != cudaSuccess ||
+        (e = h->buf.alloc((void **)&b.pf, (size_t)c.J * 8)) != cudaSuccess ||
+        (e = h->buf.alloc((void **)&b.dims, kMaxOrder * 4)) != cudaSuccess)
+      return fail(from_cuda(e));
+    int dims[kMaxOrder] = {};
+    for (int k = 0; k < c.N; ++k) dims[k] = (int)c.I[k];
+    cudaMemcpyAsync(b.dims, dims, sizeof(dims), cudaMemcpyHostToDevice, h->stream);
+    h->hdesc[0].ext_idx = b.idx;
+    h->hdesc[0].ext_pf = b.pf;
+    h->optimal = true;
+  }
   // recording buffers sized for problem 0
   {
     const trsgd_config &c = cfg[0];
@@ -421,6 +451,20 @@ static trsgd_status read_status(trsgd_handle *h) {
 }
 
 static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
+  if (h->optimal) {   // per step: the optimal distribution of this step's mode, its draws, then the step
+    const ProbDesc &D = h->hdesc[0];
+    for (int64_t t = t0; t < t0 + nsteps; ++t) {
+      const int n = draw_mode(D.seed, t, D.N);
+      cudaError_t e = launch_optimal_sampling(h->core_dtype, h->xc_dtype, D.N, n, D.I, D.R,
+                                              (const void *const *)D.cores, D.xmode[n], D.ldx[n], D.seed, t, D.J,
+                                              h->opt, h->stream);
+      if (e == cudaSuccess)
+        e = launch_step(h->core_dtype, h->xc_dtype, h->rmax, h->ddesc, h->nprob, h->lay, h->threads, t, 1, h->stream);
+      if (e != cudaSuccess) return from_cuda(e);
+      ++h->launches;
+    }
+    return TRSGD_OK;
+  }
   while (nsteps > 0) {
     const int n = (int)std::min<int64_t>(nsteps, 1 << 20);
     cudaError_t e = launch_step(h->core_dtype, h->xc_dtype, h->rmax, h->ddesc, h->nprob, h->lay, h->threads, t0,

@@ -22,6 +22,8 @@ struct ProbDesc {
   unsigned long long *cdf[8];     // inclusive prefix sums of round(p_k * 2^52)
   double *snorm[8];               // Euclidean slice norms ||G_k(i)||_F^2
   int slice_tma;                  // bit k set: core k's slices can be bulk-copied (16-byte rows)
+  const int *ext_idx;             // optimal distribution: this step's indices [J][N] and p_F [J]
+  const double *ext_pf;
   // recording of intermediates (problem 0 only)
   int dbg;
   int *dbg_n, *dbg_idx;
@@ -52,7 +54,17 @@ struct StepLayout {
   int JBH;        // max Hessian-batch samples per CTA
 };
 
+// Device buffers of the optimal distribution (sized for the largest J_n).
+struct OptBuffers {
+  double *a, *bsum, *total, *q, *pf;
+  unsigned long long *cdf, *btot;
+  int *idx, *dims;
+};
+
 // kernel launchers (defined in the .cu files)
+cudaError_t launch_optimal_sampling(int core_dtype, int x_dtype, int N, int n, const int *I, const int *R,
+                                    const void *const *cores, const void *xmode, long long ldx,
+                                    unsigned long long seed, long long t, int J, OptBuffers &b, cudaStream_t s);
 cudaError_t launch_step(int core_dtype, int x_dtype, int rmax, const ProbDesc *descs, int nprob,
                         const StepLayout &lay, int threads, long long t0, int nsteps,
                         cudaStream_t s);

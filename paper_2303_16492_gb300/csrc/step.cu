@@ -384,6 +384,16 @@ __global__ void __launch_bounds__(kMaxThreads)
       const bool need_pf = !uni || rec;   // uniform: every p_F = 1/J_n, weight 1/|F| (to rounding)
       double pF = 1.0;
       long long col = 0, st = 1;
+      if (D.dist == 3) {   // optimal distribution: indices and p_F drawn by the sampling kernels
+        for (int sp = 0; sp < L; ++sp) {
+          const int k = order[sp];
+          const int i = __ldcg(D.ext_idx + (size_t)(j0 + jl) * N + k);
+          idx_s[jl * kMaxOrder + k] = i;
+          col += (long long)i * st;
+          st *= I[k];
+        }
+        pF = __ldcg(D.ext_pf + j0 + jl);
+      } else {
       uint64_t us[kMaxOrder];
 #pragma unroll
       for (int sp = 0; sp < kMaxOrder; ++sp)
@@ -406,6 +416,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         idx_s[jl * kMaxOrder + k] = i;
         col += (long long)i * st;
         st *= Ik;
+      }
       }
       const double w = need_pf ? __ddiv_rn(1.0, __dmul_rn(cst[8 + n], pF)) : cst[16];
       w_s[jl] = w;

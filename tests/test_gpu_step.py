@@ -279,3 +279,60 @@ def test_scaled_independent_hessian_batch(prec, dist):
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, tol)
+
+
+def _encode_col(row, n, dims):
+    col, stride = 0, 1
+    N = len(dims)
+    for s in range(1, N):
+        k = (n + s) % N
+        col += int(row[k]) * stride
+        stride *= dims[k]
+    return col
+
+
+def test_optimal_distribution_fp64_steps():
+    """Theorem variance / Eq. optimal_prob: the full residual of mode n is
+    evaluated every step and |F| whole columns are drawn with the integer CDF;
+    in FP64 the weights agree with the oracle to ~1e-15, so the draws match."""
+    case = Case(dims=[9, 8, 10], ranks=[2, 3, 2], J=40, prec=0, alpha=0.05, dist=ob.DIST_OPTIMAL, noise_rel=0.2)
+    case.solver.set_debug(True)
+    for t in range(5):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        d = case.debug(rec["n"])
+        np.testing.assert_array_equal(d["idx"], rec["idx"])
+        assert rel(d["pF"], rec["pF"]) < 1e-12
+        assert rel(d["g"], rec["g"]) < 1e-11
+        for G, O in zip(case.device_cores(), case.state.cores):
+            assert rel(G, O) < 1e-11
+
+
+def test_optimal_distribution_fp32_draws_valid():
+    """FP32 residuals move the integer CDF by up to ~1e-6 of its total, so a
+    draw may land in a neighbouring column near a boundary: every device draw
+    must lie within that tolerance of the oracle's CDF interval, and its p_F
+    must equal the oracle's q of the drawn column to FP32 accuracy."""
+    from oracle import philox as px
+    case = Case(dims=[12, 10, 11], ranks=[3, 3, 3], J=64, prec=1, alpha=0.05, dist=ob.DIST_OPTIMAL, noise_rel=0.2)
+    case.solver.set_debug(True)
+    for t in range(3):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        n = ob.draw_mode(case.ocfg.seed, t, 3)
+        q = ob.optimal_dist(case.state.cores, case.X, n)
+        _, cdf = px.integer_weights(q)
+        W = int(cdf[-1])
+        case.solver.step(t)
+        d = case.debug(n)
+        u = px.draw_u64(case.ocfg.seed, t, px.STREAM_OPT, 0, np.arange(case.J, dtype=np.uint64))
+        for j in range(case.J):
+            col = _encode_col(d["idx"][j], n, case.dims)
+            target = (int(u[j]) * W) >> 64
+            lo = int(cdf[col - 1]) if col > 0 else 0
+            tol = int(1e-5 * W)
+            assert lo - tol <= target < int(cdf[col]) + tol
+            assert abs(d["pF"][j] - q[col]) <= 1e-4 * q[col]
+        ob.step(case.state, case.X, case.ocfg, t)
