@@ -289,7 +289,56 @@ def run_extras(args, device):
         del X, Xtrue
     except Exception as e:  # extras never hide the headline
         out["error"] = repr(e)
+    try:
+        out.update(run_batched(args, device))
+    except Exception as e:
+        out["batched_error"] = repr(e)
     return out
+
+
+def batched_problems(device, count=64):
+    """Batched recipe: 64 independent N=3 problems, I_n ~ U{30..200},
+    R_n ~ U{4..16}, Gaussian planted cores, noise 1e-3, |F| = 256 each."""
+    import torch
+
+    from paper_2303_16492_gb300 import api, synth
+    ws = synth.batched_workloads(count)
+    Xs, inits, pcs, Xts = [], [], [], []
+    for w in ws:
+        planted = [torch.from_numpy(G).to(device=device, dtype=torch.float32) for G in synth.planted_cores(w)]
+        Xt = api.reconstruct(planted, w.dims, w.ranks)
+        gen = torch.Generator(device=device)
+        gen.manual_seed(w.seed + 1)
+        nz = torch.randn(Xt.numel(), generator=gen, device=device, dtype=torch.float32)
+        X = Xt + nz * (w.noise_rel * torch.linalg.vector_norm(Xt) / torch.linalg.vector_norm(nz))
+        x2 = float(torch.linalg.vector_norm(X.double()) ** 2)
+        inits.append([torch.from_numpy(G).to(device=device, dtype=torch.float32) for G in synth.initial_cores(w, x2)])
+        Xs.append(X)
+        Xts.append(Xt)
+        pcs.append(api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, seed=w.seed + 3))
+    return ws, pcs, Xs, Xts, inits
+
+
+def run_batched(args, device, steps=2000):
+    import torch
+
+    from paper_2303_16492_gb300 import api
+    ws, pcs, Xs, Xts, inits = batched_problems(device)
+    s = api.Solver(pcs, Xs, inits)
+    shape = s.launch_shape()
+    s.run(0, 50)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    s.run(50, steps)
+    b.record()
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) * 1e-3
+    rse = [s.rel_error(p, Xts[p]) for p in range(0, len(ws), 16)]
+    s.close()
+    return {"c4_batched_problem_steps_per_s": round(len(ws) * steps / sec, 1),
+            "c4_batched_rounds_per_s": round(steps / sec, 1), "c4_launch_shape": list(shape),
+            "c4_rse_sample": [float(f"{r:.3e}") for r in rse]}
 
 
 def cpu_baseline(args, w, budget_s=None):

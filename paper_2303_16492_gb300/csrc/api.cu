@@ -245,10 +245,15 @@ static int default_cluster(const trsgd_handle &h) {
   return C;
 }
 
+// The preferred cluster size first, then smaller ones, then larger ones (a
+// larger cluster splits the samples finer, so its per-CTA buffers shrink).
 static trsgd_status choose_layout(trsgd_handle &h, int C) {
-  for (; C >= 1; C /= 2) {
+  int order[10], n = 0;
+  for (int c = C; c >= 1; c /= 2) order[n++] = c;
+  for (int c = C * 2; c <= 16; c *= 2) order[n++] = c;
+  for (int i = 0; i < n; ++i) {
     StepLayout L;
-    if (make_layout(h, C, L)) {
+    if (make_layout(h, order[i], L)) {
       h.lay = L;
       return from_cuda(step_kernel_prepare(h.core_dtype, h.xc_dtype, h.rmax, h.lay));
     }

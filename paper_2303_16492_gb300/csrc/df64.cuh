@@ -1,0 +1,70 @@
+// Double-float ("df64") arithmetic on the FP32 pipes: a value is the
+// unevaluated sum hi + lo of two floats (about 48 significant bits).  Built
+// from the error-free transformations of Knuth (two-sum, TAOCP vol. 2) and
+// Dekker (fast two-sum; two-product, here through a fused multiply-add), with
+// one Newton correction for division and square root.  Used for the scaled
+// variant's Gram factorisation and triangular solves, where native FP64 is
+// about 60x slower than FP32 on this GPU.
+#pragma once
+
+namespace trsgd {
+
+struct df64 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df64 df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  const float e = (a - (s - bb)) + (b - bb);
+  return df64{s, e};
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return df64{s, b - (s - a)};
+}
+
+__device__ __forceinline__ df64 df_add(df64 a, df64 b) {
+  const df64 s = df_two_sum(a.hi, b.hi);
+  const df64 t = df_two_sum(a.lo, b.lo);
+  const df64 u = df_fast_two_sum(s.hi, s.lo + t.hi);
+  return df_fast_two_sum(u.hi, u.lo + t.lo);
+}
+
+__device__ __forceinline__ df64 df_neg(df64 a) { return df64{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df64 df_mul(df64 a, df64 b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+
+// c - a * b
+__device__ __forceinline__ df64 df_fnms(df64 a, df64 b, df64 c) { return df_add(c, df_neg(df_mul(a, b))); }
+
+__device__ __forceinline__ df64 df_div(df64 a, df64 b) {
+  const float q1 = a.hi / b.hi;
+  const df64 r = df_add(a, df_neg(df_mul(df64{q1, 0.f}, b)));
+  const float q2 = r.hi / b.hi;
+  return df_fast_two_sum(q1, q2);
+}
+
+__device__ __forceinline__ df64 df_sqrt(df64 a) {
+  const float s = sqrtf(a.hi);
+  if (!(s > 0.f)) return df64{s, 0.f};
+  const df64 r = df_add(a, df_neg(df_mul(df64{s, 0.f}, df64{s, 0.f})));
+  return df_fast_two_sum(s, r.hi / (2.f * s));
+}
+
+__device__ __forceinline__ df64 df_from_double(double d) {
+  const float h = __double2float_rn(d);
+  return df64{h, __double2float_rn(d - (double)h)};
+}
+
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+}  // namespace trsgd

@@ -33,6 +33,7 @@
 #include "blocks.cuh"
 #include "internal.h"
 #include "tables.cuh"
+#include "df64.cuh"
 
 #include <type_traits>
 
@@ -77,6 +78,34 @@ __device__ __forceinline__ T dotk(const T *p, const T *s) {
 #pragma unroll
   for (int a = 0; a < LEN; ++a) acc = fma(p[a * PS], s[a], acc);
   return acc;
+}
+
+// In-place lower Cholesky in double-float arithmetic by one CTA; the strict
+// upper triangle is left untouched and the reciprocals of the pivots go to
+// inv[k].  Returns false at the first non-positive or non-finite pivot.
+__device__ __noinline__ bool cholesky_cta_df(df64 *A, int Q, int ld, df64 *inv) {
+  const int tid = threadIdx.x, NT = blockDim.x;
+  for (int k = 0; k < Q; ++k) {
+    __syncthreads();
+    const df64 d = A[k * ld + k];
+    if (!(d.hi > 0.f) || !isfinite(d.hi)) return false;
+    const df64 l = df_sqrt(d);
+    const df64 il = df_div(df64{1.f, 0.f}, l);
+    __syncthreads();
+    if (tid == 0) {
+      A[k * ld + k] = l;
+      inv[k] = il;
+    }
+    for (int i = k + 1 + tid; i < Q; i += NT) A[i * ld + k] = df_mul(A[i * ld + k], il);
+    __syncthreads();
+    const int m = Q - k - 1;
+    for (int e = tid; e < m * m; e += NT) {
+      const int i = k + 1 + e / m, j = k + 1 + e % m;
+      if (j <= i) A[i * ld + j] = df_fnms(A[i * ld + k], A[j * ld + k], A[i * ld + j]);
+    }
+  }
+  __syncthreads();
+  return true;
 }
 
 // One factor of the batched slice chain for a uniform rank RU: P_{q+1} =
@@ -165,6 +194,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     for (int i = tid; i < (int)(sizeof(ProbDesc) / 4); i += NT) dst[i] = src[i];
   }
   constexpr bool kTC = std::is_same<XT, __nv_bfloat16>::value;   // tensor-core path
+  constexpr bool kDF = std::is_same<T, float>::value;             // Gram solve in double-float
   uint64_t *bar_mma = bar + 1;
   uint32_t *tslot = reinterpret_cast<uint32_t *>(misc + 6);
   if (tid == 0) {
@@ -678,47 +708,97 @@ __global__ void __launch_bounds__(kMaxThreads)
       gemm_s<4, true, true, T>(Q, Q, gjb, gz, ldq, gz, ldq, gw,
                                [=](int a, int b, T v) { reg[(size_t)a * ldq + b] = v; });
       cluster.sync();
-      double *h0 = cluster.map_shared_rank(h64, 0);
-      double *hd0 = cluster.map_shared_rank(hdiag, 0);
       const int q0 = Q * c / C, q1 = Q * (c + 1) / C;
-      for (int e = tid; e < (q1 - q0) * Q; e += NT) {
-        const int a = q0 + e / Q, b = e % Q;
-        double v = (double)cluster_sum(reg, (size_t)a * ldq + b);
-        if (a == b) {
-          v += D.damping;
-          hd0[a] = v;
+      if constexpr (kDF) {   // FP32 cores: the Gram solve in double-float arithmetic
+        df64 *h0 = reinterpret_cast<df64 *>(cluster.map_shared_rank(h64, 0));
+        df64 *hd0 = reinterpret_cast<df64 *>(cluster.map_shared_rank(hdiag, 0));
+        const df64 damp = df_from_double(D.damping);
+        for (int e = tid; e < (q1 - q0) * Q; e += NT) {
+          const int a = q0 + e / Q, b = e % Q;
+          df64 v = df64{(float)cluster_sum(reg, (size_t)a * ldq + b), 0.f};
+          if (a == b) {
+            v = df_add(v, damp);
+            hd0[a] = v;
+          }
+          h0[a * QH + b] = v;
+          if (rec) D.dbg_h[a * Q + b] = df_to_double(v);
         }
-        h0[a * QH + b] = v;
-        if (rec) D.dbg_h[a * Q + b] = v;
+      } else {
+        double *h0 = cluster.map_shared_rank(h64, 0);
+        double *hd0 = cluster.map_shared_rank(hdiag, 0);
+        for (int e = tid; e < (q1 - q0) * Q; e += NT) {
+          const int a = q0 + e / Q, b = e % Q;
+          double v = (double)cluster_sum(reg, (size_t)a * ldq + b);
+          if (a == b) {
+            v += D.damping;
+            hd0[a] = v;
+          }
+          h0[a * QH + b] = v;
+          if (rec) D.dbg_h[a * Q + b] = v;
+        }
       }
       cluster.sync();
       if (c == 0) {
         // factor, growing the damping on failure (1e-12 tr(h)/Q * 10^m, m = 0..6)
-        if (tid == 0) {
-          double tr = 0.0;
-          for (int q = 0; q < Q; ++q) tr += hdiag[q] - D.damping;
-          misc[2] = tr;
-        }
-        __syncthreads();
-        const double tr = misc[2];
-        bool ok = cholesky_cta(h64, Q, QH);
-        double extra = 0.0;
-        for (int m = 0; m < 7 && !ok; ++m) {
-          extra = 1e-12 * tr / Q * pow(10.0, (double)m);
-          __syncthreads();
-          for (int e = tid; e < Q * Q; e += NT) {
-            const int a = e / Q, b = e % Q;
-            if (a == b) h64[a * QH + a] = hdiag[a] + extra;
-            else if (a > b) h64[a * QH + b] = h64[b * QH + a];
+        if constexpr (kDF) {
+          df64 *A = reinterpret_cast<df64 *>(h64);
+          df64 *hd = reinterpret_cast<df64 *>(hdiag);
+          df64 *inv = reinterpret_cast<df64 *>(smem + lay.off_reg);   // reciprocal pivots (reg is free here)
+          if (tid == 0) {
+            double tr = 0.0;
+            for (int q = 0; q < Q; ++q) tr += df_to_double(hd[q]) - D.damping;
+            misc[2] = tr;
           }
-          ok = cholesky_cta(h64, Q, QH);
+          __syncthreads();
+          const double tr = misc[2];
+          bool ok = cholesky_cta_df(A, Q, QH, inv);
+          double extra = 0.0;
+          for (int m = 0; m < 7 && !ok; ++m) {
+            extra = 1e-12 * tr / Q * pow(10.0, (double)m);
+            const df64 ex = df_from_double(extra);
+            __syncthreads();
+            for (int e = tid; e < Q * Q; e += NT) {
+              const int a = e / Q, b = e % Q;
+              if (a == b) A[a * QH + a] = df_add(hd[a], ex);
+              else if (a > b) A[a * QH + b] = A[b * QH + a];
+            }
+            ok = cholesky_cta_df(A, Q, QH, inv);
+          }
+          if (rec && ok && extra > 0.0)
+            for (int q = tid; q < Q; q += NT) D.dbg_h[q * Q + q] = df_to_double(hd[q]) + extra;
+          __syncthreads();
+          for (int q = tid; q < Q; q += NT) hd[q] = inv[q];   // the diagonal copy is no longer needed
+          if (tid == 0) {
+            misc[0] = ok ? 1.0 : 0.0;
+            if (!ok) latch_status(D.status, kStatusNumeric);
+          }
+        } else {
+          if (tid == 0) {
+            double tr = 0.0;
+            for (int q = 0; q < Q; ++q) tr += hdiag[q] - D.damping;
+            misc[2] = tr;
+          }
+          __syncthreads();
+          const double tr = misc[2];
+          bool ok = cholesky_cta(h64, Q, QH);
+          double extra = 0.0;
+          for (int m = 0; m < 7 && !ok; ++m) {
+            extra = 1e-12 * tr / Q * pow(10.0, (double)m);
+            __syncthreads();
+            for (int e = tid; e < Q * Q; e += NT) {
+              const int a = e / Q, b = e % Q;
+              if (a == b) h64[a * QH + a] = hdiag[a] + extra;
+              else if (a > b) h64[a * QH + b] = h64[b * QH + a];
+            }
+            ok = cholesky_cta(h64, Q, QH);
+          }
+          if (tid == 0) {
+            misc[0] = ok ? 1.0 : 0.0;
+            if (!ok) latch_status(D.status, kStatusNumeric);
+          }
+          if (rec && ok && extra > 0.0)
+            for (int q = tid; q < Q; q += NT) D.dbg_h[q * Q + q] = hdiag[q] + extra;
         }
-        if (tid == 0) {
-          misc[0] = ok ? 1.0 : 0.0;
-          if (!ok) latch_status(D.status, kStatusNumeric);
-        }
-        if (rec && ok && extra > 0.0)
-          for (int q = tid; q < Q; q += NT) D.dbg_h[q * Q + q] = hdiag[q] + extra;
       }
     }
 
@@ -844,6 +924,76 @@ __global__ void __launch_bounds__(kMaxThreads)
       const int warp = tid >> 5, lane = tid & 31, nw = NT >> 5;
       const int r0 = In * c / C;   // single chunk: owned rows [r0, r0 + own_rows)
       constexpr int QM = 4;        // Q <= 128 = 32 * QM
+      if constexpr (kDF) {
+        // local copy of the factor (lower triangle) and the reciprocal pivots
+        df64 *Lc = reinterpret_cast<df64 *>(h64);
+        df64 *ivc = reinterpret_cast<df64 *>(hdiag);
+        if (c != 0 && ok) {
+          const df64 *Lr = reinterpret_cast<const df64 *>(L0);
+          const df64 *ivr = reinterpret_cast<const df64 *>(cluster.map_shared_rank(hdiag, 0));
+          for (int e = tid; e < Q * Q; e += NT) {
+            const int a = e / Q, b = e - a * Q;
+            if (b <= a) Lc[a * QH + b] = Lr[a * QH + b];
+          }
+          for (int q = tid; q < Q; q += NT) ivc[q] = ivr[q];
+        }
+        __syncthreads();
+        for (int rr = warp; rr < own_rows; rr += nw) {
+          const int i = r0 + rr;
+          df64 y[QM];
+#pragma unroll
+          for (int m = 0; m < QM; ++m) {
+            const int q = lane + 32 * m;
+            y[m] = df64{(q < Q) ? -(float)gown[(size_t)rr * ldq + q] : 0.f, 0.f};
+          }
+          if (ok) {
+            for (int k = 0; k < Q; ++k) {        // L y = -g^T
+              df64 yk = df64{0.f, 0.f};
+#pragma unroll
+              for (int m = 0; m < QM; ++m)
+                if ((k >> 5) == m && lane == (k & 31)) yk = df_mul(y[m], ivc[k]);
+              yk.hi = __shfl_sync(0xffffffffu, yk.hi, k & 31);
+              yk.lo = __shfl_sync(0xffffffffu, yk.lo, k & 31);
+#pragma unroll
+              for (int m = 0; m < QM; ++m) {
+                const int q = lane + 32 * m;
+                if (q == k) y[m] = yk;
+                else if (q > k && q < Q) y[m] = df_fnms(Lc[q * QH + k], yk, y[m]);
+              }
+            }
+            for (int k = Q - 1; k >= 0; --k) {   // L^T x = y
+              df64 xk = df64{0.f, 0.f};
+#pragma unroll
+              for (int m = 0; m < QM; ++m)
+                if ((k >> 5) == m && lane == (k & 31)) xk = df_mul(y[m], ivc[k]);
+              xk.hi = __shfl_sync(0xffffffffu, xk.hi, k & 31);
+              xk.lo = __shfl_sync(0xffffffffu, xk.lo, k & 31);
+#pragma unroll
+              for (int m = 0; m < QM; ++m) {
+                const int q = lane + 32 * m;
+                if (q == k) y[m] = xk;
+                else if (q < k) y[m] = df_fnms(Lc[k * QH + q], xk, y[m]);
+              }
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < QM; ++m) y[m] = df64{0.f, 0.f};
+          }
+          __syncwarp();
+#pragma unroll
+          for (int m = 0; m < QM; ++m) {
+            const int q = lane + 32 * m;
+            if (q >= Q) continue;
+            const size_t gi = (size_t)i * Q + q;
+            const T p = (T)(y[m].hi + y[m].lo);
+            const T nv = ld_l2(Gn + gi) + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
+            if (!isfinite(nv)) latch_status(D.status, kStatusNumeric);
+            Gn[gi] = nv;
+            gown[(size_t)rr * ldq + q] = nv;
+            if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
+          }
+        }
+      } else {
       for (int rr = warp; rr < own_rows; rr += nw) {
         const int i = r0 + rr;
         double y[QM];
@@ -896,6 +1046,7 @@ __global__ void __launch_bounds__(kMaxThreads)
           gown[(size_t)rr * ldq + q] = nv;
           if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
         }
+      }
       }
       if (D.dist == 2) {
         __syncthreads();
