@@ -118,6 +118,11 @@ def device_problem(w, device, seed_offset=0):
     return X, Xtrue, init
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per step, from the ncu capture
+# summarised in profiles/step_cluster_kernel_c2_fp32.md (102.12 MB over 200 steps)
+MEASURED_TRAFFIC_PER_STEP = {("c2", "step_cluster_kernel<float,float,12>"): 510616}
+
+
 def algorithmic_per_step(w):
     """Algorithmic bytes and flops of one iteration averaged over the modes
     (uniform mode draw): fibers J*I_n*4 B, G_n read+write, the N-1 sampled
@@ -187,14 +192,22 @@ def run_ours(args):
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
     alu_peak = fp32_alu_peak_tflops(sm_mhz)
     achieved_tflops = fl / (ms_per_step * 1e-3) / 1e12
+    rmax = next(r for r in (4, 8, 12, 16) if r >= max(w.ranks))
+    kernel = f"step_cluster_kernel<float,float,{rmax}>"
+    # DRAM read+write per step of this kernel on this workload, from one ncu capture
+    # (a 200-step launch; the per-step figure is scaled to the timed launch)
+    traffic_step = MEASURED_TRAFFIC_PER_STEP.get((args.workload, kernel))
     roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(alu_peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved_tflops / alu_peak, 5), "traffic": None,
-                "kernel": "step_cluster_kernel<float,float,16>",
+                "unit": "TFLOP/s", "frac": round(achieved_tflops / alu_peak, 5),
+                "traffic": None if traffic_step is None else int(traffic_step * args.steps),
+                "traffic_per_step": traffic_step,
+                "kernel": kernel,
                 "peak_note": f"FP32 FMA unit count x {sm_mhz:.0f} MHz (derived; {pk_kind} clock)",
                 "hbm_frac": round(by / (ms_per_step * 1e-3) / 1e9 / pk.get("hbm_gbs", 6652.0), 5),
                 "algorithmic_bytes_per_step": int(by), "algorithmic_flops_per_step": int(fl)}
 
     e2e = run_e2e(args, w, solver, X, init, device) if rank == 0 and not args.no_e2e else None
+    ttr = time_to_rse(args, w, device, ms_per_step) if rank == 0 and args.time_to_rse else None
     extras = run_extras(args, device) if rank == 0 and args.extras else None
     cpu = cpu_baseline(args, w) if rank == 0 and world == 1 and not args.no_cpu_baseline else None
     if rank == 0:
@@ -209,7 +222,7 @@ def run_ours(args):
                           "l2": "inputs larger than L2 (X 400 MB, mode-major copies 1.6 GB; fibers sampled "
                                 "at random each step; the 160 KB of cores stay resident as the iterate)"},
                "rse_after": rse, "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
-               "e2e": e2e, "cpu_baseline": cpu, "extras": extras}
+               "e2e": e2e, "cpu_baseline": cpu, "time_to_rse": ttr, "extras": extras}
         print(json.dumps(out), flush=True)
     solver.close()
     if world > 1:
@@ -248,6 +261,35 @@ def run_e2e(args, w, solver_dev, X_dev, init_dev, device):
             "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
             "note": "X and the initial cores copied from pinned host memory, trsgd_init, K iterations and "
                     "the cores read back, all inside the timed region (bytes amortised per step)"}
+
+
+def time_to_rse(args, w, device, ms_fp32, target=1e-3, chunk=500, max_steps=60000):
+    """Iterations and device seconds until RSE(X_true) <= target (Sec. 4
+    stopping rule, checked every `chunk` iterations by trsgd_run; the RSE
+    evaluations are not timed), FP32 and BF16-mixed, same inputs and seed."""
+    import torch
+
+    from paper_2303_16492_gb300 import api
+    out = {"target": target, "check_every": chunk}
+    X, Xtrue, init = device_problem(w, device)
+    for name, prec in (("fp32", 1), ("bf16_mixed", 2)):
+        cores = [c.clone() for c in init]
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=prec, x_dtype=1, alpha=w.alpha, seed=w.seed + 3)
+        s = api.Solver([pc], [X], [cores])
+        s.run(0, 200)     # warm-up launch (counts toward the iterations)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        s.run(200, 2000)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 2000
+        done, r = s.run(2200, max_steps, chunk=chunk, tol=target, Xref=Xtrue)
+        steps = 2200 + done
+        out[name] = {"iterations": steps, "reached": bool(0 <= r <= target), "rse": r,
+                     "ms_per_iteration": round(ms, 6), "seconds": round(steps * ms * 1e-3, 4)}
+        s.close()
+    return out
 
 
 def run_extras(args, device):
@@ -404,6 +446,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--extras", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--time-to-rse", action=argparse.BooleanOptionalAction, default=True)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -128,7 +128,7 @@ def batched_workloads(count: int = 64, seed: int = 0, J: int = 256):
         dims = [int(v) for v in rng.integers(30, 201, size=3)]
         ranks = [int(v) for v in rng.integers(4, 17, size=3)]
         out.append(Workload(f"c4[{p}]", dims, ranks, J, "gaussian", 0.0,
-                            noise_rel=1e-3, alpha=0.2, prec=1, seed=seed + p))
+                            noise_rel=1e-3, alpha=1.5, prec=1, seed=seed + p))
     return out
 
 
