@@ -71,8 +71,10 @@ typedef enum { TRSGD_STEP_FIXED = 0, TRSGD_STEP_ADAGRAD = 1 } trsgd_steprule;
 /* Arithmetic of the step.  FP64: cores, X and all arithmetic in double.
  * FP32: cores and X in float, FP32 arithmetic.  BF16_MIXED: cores in float,
  * the sampled fibers stored in bfloat16, tensor-core contractions with FP32
- * accumulation.  In every mode the scaled variant's Gram solve and the
- * relative-error reduction are FP64. */
+ * accumulation.  The scaled variant's Gram matrix is reduced, factorised and
+ * applied in FP64 for FP64 cores and in double-float arithmetic (a float
+ * pair, about 48 significant bits, on the FP32 pipes) for float cores; the
+ * relative-error reduction is FP64 in every mode. */
 typedef enum { TRSGD_FP64 = 0, TRSGD_FP32 = 1, TRSGD_BF16_MIXED = 2 } trsgd_prec;
 
 typedef enum { TRSGD_DTYPE_F64 = 0, TRSGD_DTYPE_F32 = 1, TRSGD_DTYPE_BF16 = 2 } trsgd_dtype;
