@@ -139,6 +139,23 @@ def algorithmic_per_step(w):
     return by / N, fl / N
 
 
+def max_over_ranks(ms, device):
+    """The slowest rank's timed milliseconds (all ranks receive it), then a
+    barrier; the job's clock is the max over ranks."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_throughput(world, steps, ms):
+    """Whole-job steps/s: every rank runs `steps` iterations of its own
+    problem (replicas, weak scaling) within the max-over-ranks time."""
+    return world * steps / (ms * 1e-3)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -178,12 +195,9 @@ def run_ours(args):
     launches = solver.launch_count() - l0
     clocks = clk.stop()
     if world > 1:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+        ms = max_over_ranks(ms, device)
     rse = solver.rel_error(0, Xtrue)
-    value = world * args.steps / (ms * 1e-3)
+    value = job_throughput(world, args.steps, ms)
     ms_per_step = ms / args.steps
 
     # roofline of the dominant kernel (the fused step kernel; it is the only kernel in the timed region)

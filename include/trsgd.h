@@ -129,16 +129,27 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems,
 trsgd_status trsgd_step(trsgd_handle *h, int64_t t);
 
 /* Iterations t0 .. t0+T-1 (T >= 0) as persistent launches of `chunk` steps
- * each (chunk <= 0: all T in one launch), optionally captured in one CUDA
- * graph.  With tol > 0 or max_seconds > 0 it synchronises every `chunk`
- * steps, evaluates the RSE of problem 0 against Xref_dev (NULL: the X given
- * to init) and stops once RSE <= tol or the elapsed device time exceeds
- * max_seconds (Sec. 4 stopping criteria).  *steps_done and *rse_out
- * (nullable) receive the iterations run and the last RSE (-1 if none).
- * Synchronising. */
+ * each (chunk <= 0: all T in one launch).  With tol > 0 or max_seconds > 0
+ * it synchronises every `chunk` steps, evaluates the RSE of problem 0
+ * against Xref_dev (NULL: the X given to init) and stops once RSE <= tol or
+ * the elapsed device time exceeds max_seconds (Sec. 4 stopping criteria).
+ * *steps_done and *rse_out (nullable) receive the iterations run and the
+ * last RSE (-1 if none).  Synchronising. */
 trsgd_status trsgd_run(trsgd_handle *h, int64_t t0, int64_t T, int64_t chunk,
                        double tol, double max_seconds, const void *Xref_dev,
                        int64_t *steps_done, double *rse_out);
+
+/* Iterations c .. c+T-1 (1 <= T <= 2^20; T = 0 does nothing), where c is a
+ * device-resident iteration counter of the handle (0 after init), followed
+ * by c += T on the device.  No host-side iteration number is involved, so
+ * the call can be recorded in a CUDA graph (stream capture of the handle's
+ * stream) and each replay continues the sequence where the last one ended;
+ * the iterates are bit-identical to trsgd_run from the same t.  Enqueued on
+ * the handle's stream; does not synchronise.  TRSGD_EUNSUPPORTED for the
+ * optimal distribution (its tables are built for a mode drawn on the host).
+ * trsgd_set_counter enqueues c = t (also capturable). */
+trsgd_status trsgd_step_counter(trsgd_handle *h, int64_t T);
+trsgd_status trsgd_set_counter(trsgd_handle *h, int64_t t);
 
 /* RSE = ||TR(G) - X_ref||_F / ||X_ref||_F (Sec. 4) of problem `problem`,
  * reduced in FP64.  Xref_dev: NULL for the X given to init, else a tensor of

@@ -52,6 +52,8 @@ _SIGNATURES = {
                                   ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p,
                                   ctypes.POINTER(ctypes.c_void_p)]),
     "trsgd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "trsgd_step_counter": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "trsgd_set_counter": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "trsgd_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                  ctypes.c_double, ctypes.c_double, ctypes.c_void_p,
                                  ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]),

@@ -97,6 +97,14 @@ class Solver:
     def step(self, t: int):
         check(_abi.lib().trsgd_step(self._h, int(t)), "trsgd_step")
 
+    def step_counter(self, T: int):
+        """T iterations from the device-resident counter, which then advances by
+        T; recordable in a CUDA graph on ``self.stream``."""
+        check(_abi.lib().trsgd_step_counter(self._h, int(T)), "trsgd_step_counter")
+
+    def set_counter(self, t: int):
+        check(_abi.lib().trsgd_set_counter(self._h, int(t)), "trsgd_set_counter")
+
     def run(self, t0: int, T: int, chunk: int = 0, tol: float = 0.0, max_seconds: float = 0.0, Xref=None):
         done = ctypes.c_int64()
         rse = ctypes.c_double()

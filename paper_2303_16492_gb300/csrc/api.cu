@@ -57,6 +57,7 @@ struct trsgd_handle {
   int threads = 512;
   int *d_status = nullptr;
   double *d_sums = nullptr;
+  long long *d_t = nullptr;   // device-resident iteration counter (trsgd_step_counter)
   std::vector<const void *> X;
   int64_t t_next = 0;
   int64_t launches = 0;
@@ -314,7 +315,9 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
   cudaError_t e;
   if ((e = h->buf.alloc((void **)&h->d_status, 16)) != cudaSuccess) return fail(from_cuda(e));
   if ((e = h->buf.alloc((void **)&h->d_sums, 16)) != cudaSuccess) return fail(from_cuda(e));
+  if ((e = h->buf.alloc((void **)&h->d_t, 16)) != cudaSuccess) return fail(from_cuda(e));
   cudaMemsetAsync(h->d_status, 0, 16, h->stream);
+  cudaMemsetAsync(h->d_t, 0, 16, h->stream);
   const size_t sxc = dtype_size(h->xc_dtype);
   const size_t score = h->core_dtype == 0 ? 8 : 4;
   h->hdesc.resize(nproblems);
@@ -464,7 +467,8 @@ static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
                                               (const void *const *)D.cores, D.xmode[n], D.ldx[n], D.seed, t, D.J,
                                               h->opt, h->stream);
       if (e == cudaSuccess)
-        e = launch_step(h->core_dtype, h->xc_dtype, h->rmax, h->ddesc, h->nprob, h->lay, h->threads, t, 1, h->stream);
+        e = launch_step(h->core_dtype, h->xc_dtype, h->rmax, h->ddesc, h->nprob, h->lay, h->threads, t, 1, nullptr,
+                        h->stream);
       if (e != cudaSuccess) return from_cuda(e);
       ++h->launches;
     }
@@ -473,7 +477,7 @@ static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
   while (nsteps > 0) {
     const int n = (int)std::min<int64_t>(nsteps, 1 << 20);
     cudaError_t e = launch_step(h->core_dtype, h->xc_dtype, h->rmax, h->ddesc, h->nprob, h->lay, h->threads, t0,
-                                n, h->stream);
+                                n, nullptr, h->stream);
     if (e != cudaSuccess) return from_cuda(e);
     ++h->launches;
     t0 += n;
@@ -487,6 +491,24 @@ trsgd_status trsgd_step(trsgd_handle *h, int64_t t) {
   trsgd_status s = launch_steps(h, t, 1);
   if (s == TRSGD_OK) h->t_next = t + 1;
   return s;
+}
+
+trsgd_status trsgd_step_counter(trsgd_handle *h, int64_t T) {
+  if (!h || T < 0 || T > (1 << 20)) return TRSGD_EINVAL;
+  if (h->optimal) return TRSGD_EUNSUPPORTED;   // its per-step tables are drawn with the mode known on the host
+  if (T == 0) return TRSGD_OK;
+  cudaError_t e = launch_step(h->core_dtype, h->xc_dtype, h->rmax, h->ddesc, h->nprob, h->lay, h->threads, 0,
+                              (int)T, h->d_t, h->stream);
+  if (e == cudaSuccess) e = launch_advance_counter(h->d_t, T, 0, h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  ++h->launches;
+  return TRSGD_OK;
+}
+
+trsgd_status trsgd_set_counter(trsgd_handle *h, int64_t t) {
+  if (!h || t < 0) return TRSGD_EINVAL;
+  cudaError_t e = launch_advance_counter(h->d_t, t, 1, h->stream);
+  return e == cudaSuccess ? TRSGD_OK : from_cuda(e);
 }
 
 trsgd_status trsgd_rel_error(trsgd_handle *h, int32_t problem, const void *Xref_dev, double *out) {

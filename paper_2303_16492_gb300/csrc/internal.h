@@ -67,7 +67,8 @@ cudaError_t launch_optimal_sampling(int core_dtype, int x_dtype, int N, int n, c
                                     unsigned long long seed, long long t, int J, OptBuffers &b, cudaStream_t s);
 cudaError_t launch_step(int core_dtype, int x_dtype, int rmax, const ProbDesc *descs, int nprob,
                         const StepLayout &lay, int threads, long long t0, int nsteps,
-                        cudaStream_t s);
+                        const long long *t_dev, cudaStream_t s);
+cudaError_t launch_advance_counter(long long *t, long long T, int set, cudaStream_t s);
 cudaError_t step_kernel_prepare(int core_dtype, int x_dtype, int rmax, const StepLayout &lay);
 int step_max_smem();
 

@@ -164,7 +164,9 @@ __device__ __forceinline__ T step_delta(int rule, T alpha, T eta, T b, double ep
 
 template <typename T, typename XT, int RMAX>
 __global__ void __launch_bounds__(kMaxThreads)
-    step_cluster_kernel(const ProbDesc *__restrict__ descs, StepLayout lay, long long t0, int nsteps) {
+    step_cluster_kernel(const ProbDesc *__restrict__ descs, StepLayout lay, long long t0, int nsteps,
+                        const long long *__restrict__ t_dev) {
+  if (t_dev) t0 += __ldcg(t_dev);   // device-resident iteration counter (graph replays)
   cg::cluster_group cluster = cg::this_cluster();
   const int C = lay.C;
   const int c = (int)cluster.block_rank();
@@ -1121,7 +1123,7 @@ static cudaError_t prepare_one(const StepLayout &lay) {
 
 template <typename T, typename XT, int RMAX>
 static cudaError_t launch_one(const ProbDesc *descs, int nprob, const StepLayout &lay, int threads,
-                              long long t0, int nsteps, cudaStream_t s) {
+                              long long t0, int nsteps, const long long *t_dev, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(lay.C * nprob), 1, 1);
   cfg.blockDim = dim3((unsigned)threads, 1, 1);
@@ -1134,7 +1136,7 @@ static cudaError_t launch_one(const ProbDesc *descs, int nprob, const StepLayout
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, step_cluster_kernel<T, XT, RMAX>, descs, lay, t0, nsteps);
+  return cudaLaunchKernelEx(&cfg, step_cluster_kernel<T, XT, RMAX>, descs, lay, t0, nsteps, t_dev);
 }
 
 // RMAX: register length of one chain row; the smallest of 4, 8, 12, 16 that
@@ -1165,8 +1167,18 @@ cudaError_t step_kernel_prepare(int core_dtype, int x_dtype, int rmax, const Ste
 
 cudaError_t launch_step(int core_dtype, int x_dtype, int rmax, const ProbDesc *descs, int nprob,
                         const StepLayout &lay, int threads, long long t0, int nsteps,
-                        cudaStream_t s) {
-  TRSGD_DISPATCH(launch_one, descs, nprob, lay, threads, t0, nsteps, s);
+                        const long long *t_dev, cudaStream_t s) {
+  TRSGD_DISPATCH(launch_one, descs, nprob, lay, threads, t0, nsteps, t_dev, s);
+}
+
+// *t += T, after the step launch that read *t has finished (same stream)
+__global__ void advance_counter_kernel(long long *t, long long T, int set) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *t = set ? T : *t + T;
+}
+
+cudaError_t launch_advance_counter(long long *t, long long T, int set, cudaStream_t s) {
+  advance_counter_kernel<<<1, 32, 0, s>>>(t, T, set);
+  return cudaGetLastError();
 }
 
 int step_max_smem() { return 232448; }
