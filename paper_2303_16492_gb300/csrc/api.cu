@@ -134,7 +134,8 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   }
   L = {};
   L.C = C;
-  L.JB = (Jmax + C - 1) / C;
+  L.cw0 = (scaled && C > 1) ? 1 : 0;
+  L.JB = (Jmax + (C - L.cw0) - 1) / (C - L.cw0);
   const bool tc = h.xc_dtype == TRSGD_DTYPE_BF16;   // tensor-core path
   const size_t JB4 = rup((size_t)L.JB, 4);
   L.ldxs = (int)rup((size_t)Imax, tc ? 8 : 4);
@@ -186,7 +187,7 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   const size_t tail0 = rup(off, 128);
   if (tail0 >= limit) return false;
   const size_t avail = limit - tail0;
-  const size_t h64b = scaled ? (size_t)QH * QH * 8 : 0;
+  const size_t h64b = scaled ? (size_t)QH * (QH | 1) * 8 : 0;   // Gram, then the factor at an odd pitch
   const size_t hdb = scaled ? (size_t)QH * 8 : 0;
   auto own_rows_for = [&](int TI) { return scaled ? (Imax + C - 1) / C + 1 : (TI + C - 1) / C + 1; };
   auto reg_bytes = [&](int ti) {
@@ -336,6 +337,11 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
     for (int k = 0; k < c.N; ++k) {
       D.I[k] = (int)c.I[k];
       D.R[k] = (int)c.R[k];
+    }
+    if (c.variant == TRSGD_SCALED) {   // factor of h and reciprocal pivots, written by CTA 0 each step
+      size_t qm = 1;
+      for (int k = 0; k < c.N; ++k) qm = std::max<size_t>(qm, (size_t)(c.R[k] * c.R[(k + 1) % c.N]));
+      if ((e = h->buf.alloc(&D.lfac, (qm * qm + qm) * 8)) != cudaSuccess) return fail(from_cuda(e));
     }
     D.alpha = c.alpha;
     D.eta = c.eta;
@@ -665,6 +671,14 @@ trsgd_status trsgd_adagrad_state(trsgd_handle *h, int32_t problem, int32_t core,
   return from_cuda(e);
 }
 
+// The scaled variant's factorisation holds the 4 x 4 blocks of the Gram
+// matrix's lower triangle in registers, at most two blocks per thread.
+static bool threads_fit(const trsgd_handle &h, int T) {
+  if (h.lay.QH <= 0) return true;
+  const int Qb = (h.lay.QH + 3) / 4;
+  return Qb * (Qb + 1) / 2 <= 2 * T;
+}
+
 trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster, int32_t *threads) {
   if (!h || !cluster || !threads) return TRSGD_EINVAL;
   if (set == 0) {
@@ -676,6 +690,7 @@ trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster, 
   const int C = *cluster ? *cluster : h->lay.C;
   const int T = *threads ? *threads : h->threads;
   if (C < 1 || C > 16 || (C & (C - 1)) || (T != 128 && T != 256 && T != 512)) return TRSGD_EINVAL;
+  if (!threads_fit(*h, T)) return TRSGD_EUNSUPPORTED;
   StepLayout L;
   if (!make_layout(*h, C, L)) return TRSGD_EUNSUPPORTED;
   cudaError_t e = step_kernel_prepare(h->core_dtype, h->xc_dtype, h->rmax, L);
@@ -724,6 +739,7 @@ trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial) {
     if (!make_layout(*h, C, L)) continue;
     if (step_kernel_prepare(h->core_dtype, h->xc_dtype, h->rmax, L) != cudaSuccess) continue;
     for (int T : {256, 512}) {
+      if (!threads_fit(*h, T)) continue;
       h->lay = L;
       h->threads = T;
       if (launch_steps(h, 0, 1) != TRSGD_OK) { cudaGetLastError(); continue; }  // warm-up
@@ -756,6 +772,9 @@ trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial) {
       if (c.dist == TRSGD_DIST_EUCLIDEAN)
         launch_euclid_table(h->core_dtype, h->hdesc[p].cores[k], (int)c.I[k], (int)(c.R[k] * c.R[(k + 1) % c.N]),
                             h->hdesc[p].snorm[k], h->hdesc[p].prob[k], h->hdesc[p].cdf[k], h->stream);
+      if (c.dist == TRSGD_DIST_LEVERAGE)
+        launch_leverage_table(h->core_dtype, h->hdesc[p].cores[k], (int)c.I[k], (int)(c.R[k] * c.R[(k + 1) % c.N]),
+                              h->hdesc[p].prob[k], h->hdesc[p].cdf[k], h->d_status, h->stream);
     }
   }
   h->lay = best_lay;

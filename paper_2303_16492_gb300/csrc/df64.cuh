@@ -46,6 +46,26 @@ __device__ __forceinline__ df64 df_mul(df64 a, df64 b) {
 // c - a * b
 __device__ __forceinline__ df64 df_fnms(df64 a, df64 b, df64 c) { return df_add(c, df_neg(df_mul(a, b))); }
 
+// c - a * b with one renormalisation: the leading product a.hi b.hi is split
+// exactly (Dekker's two-product through an FMA), its difference with c.hi is
+// formed exactly (Knuth's two-sum), and the remaining small terms (the
+// product's error, the cross terms, c.lo) are added in float before a final
+// fast two-sum.  15 float operations instead of the 27 of df_fnms; the extra
+// rounding is a float rounding of terms of relative size 2^-24, so the
+// result keeps about 44 of the 48 bits.
+__device__ __forceinline__ df64 df_fnms_fast(df64 a, df64 b, df64 c) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);
+  const float s = c.hi - p;
+  const float bb = s - c.hi;
+  const float err = (c.hi - (s - bb)) + (-p - bb);
+  float lo = c.lo - e;
+  lo = fmaf(-a.hi, b.lo, lo);
+  lo = fmaf(-a.lo, b.hi, lo);
+  lo += err;
+  return df_fast_two_sum(s, lo);
+}
+
 __device__ __forceinline__ df64 df_div(df64 a, df64 b) {
   const float q1 = a.hi / b.hi;
   const df64 r = df_add(a, df_neg(df_mul(df64{q1, 0.f}, b)));

@@ -22,6 +22,8 @@ struct ProbDesc {
   unsigned long long *cdf[8];     // inclusive prefix sums of round(p_k * 2^52)
   double *snorm[8];               // Euclidean slice norms ||G_k(i)||_F^2
   int slice_tma;                  // bit k set: core k's slices can be bulk-copied (16-byte rows)
+  void *lfac;                     // scaled variant: Cholesky factor of h (column-major, Q x Q) then
+                                  // the Q reciprocal pivots, in the Gram-solve scalar (8 bytes each)
   const int *ext_idx;             // optimal distribution: this step's indices [J][N] and p_F [J]
   const double *ext_pf;
   // recording of intermediates (problem 0 only)
@@ -52,6 +54,8 @@ struct StepLayout {
       off_hdiag, off_gown, off_misc, off_const, off_sb, off_p0, off_p1, off_zh, off_zl, off_ew,
       off_hz, off_hidx, off_hw, total;
   int JBH;        // max Hessian-batch samples per CTA
+  int cw0;        // first CTA that takes samples: 1 for the scaled variant with C > 1 (CTA 0
+                  // factorises the Gram matrix meanwhile), else 0
 };
 
 // Device buffers of the optimal distribution (sized for the largest J_n).

@@ -12,15 +12,17 @@
 //   A4 sampled subchain rows Z(j, r + r' R_n) = P_j(r', r), one thread per
 //      row of P_j = G_{n+1}(i_{n+1}) ... G_{n-1}(i_{n-1});
 //   S  (scaled variant) partial Gram Z^T D Z, reduced over the cluster into
-//      CTA 0, which factors h + eta^t I in FP64 (Cholesky, damping grown on
-//      failure);
+//      CTA 0, which factors h + eta^t I (Cholesky in the Gram-solve scalar:
+//      FP64, or double-float for float cores; damping grown on failure) and
+//      writes the factor to global memory.  In the scaled variant CTA 0 takes
+//      no samples, so the factorisation overlaps the other CTAs' B and C;
 //   B  per chunk of G_n rows: residual E = G_n Z^T - X_S (Eq. S_gradient),
 //      weighted in place over the fibers;
 //   C  partial gradient (E D) Z of this CTA's samples;
 //   R  reduction of the partials over the cluster through distributed shared
 //      memory in fixed CTA order (deterministic), then the step rule (fixed
 //      alpha or AdaGrad) on the rows this CTA owns, written to G_n in HBM;
-//   scaled: p = -g h^{-1} on the owned rows by two FP64 triangular solves
+//   scaled: p = -g h^{-1} on the owned rows by two triangular solves
 //      against CTA 0's factor (Eq. scaledsg_direction, damped form);
 //   Euclidean distribution: slice norms of the updated rows and CTA 0's
 //      integer CDF of core n for the next iteration (Lemma euc_est).
@@ -34,6 +36,7 @@
 #include "internal.h"
 #include "tables.cuh"
 #include "df64.cuh"
+#include "gramsolve.cuh"
 
 #include <type_traits>
 
@@ -47,30 +50,6 @@ static constexpr uint32_t kTmaFiberBytes = 1024;   // fibers at least this long 
 
 __host__ __device__ inline size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// In-place lower Cholesky of the Q x Q matrix A (leading dim ld) by one CTA;
-// the strict upper triangle is left untouched.  Returns false at the first
-// non-positive or non-finite pivot (the same decision in every thread).
-__device__ __noinline__ bool cholesky_cta(double *A, int Q, int ld) {
-  const int tid = threadIdx.x, NT = blockDim.x;
-  for (int k = 0; k < Q; ++k) {
-    __syncthreads();
-    const double d = A[k * ld + k];
-    if (!(d > 0.0) || !isfinite(d)) return false;
-    const double l = sqrt(d);
-    __syncthreads();
-    if (tid == 0) A[k * ld + k] = l;
-    for (int i = k + 1 + tid; i < Q; i += NT) A[i * ld + k] = A[i * ld + k] / l;
-    __syncthreads();
-    const int m = Q - k - 1;
-    for (int e = tid; e < m * m; e += NT) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) A[i * ld + j] = fma(-A[i * ld + k], A[j * ld + k], A[i * ld + j]);
-    }
-  }
-  __syncthreads();
-  return true;
-}
-
 // sum_{a < LEN} p[a * PS] * s[a] with compile-time length and stride
 template <int LEN, int PS, typename T>
 __device__ __forceinline__ T dotk(const T *p, const T *s) {
@@ -78,34 +57,6 @@ __device__ __forceinline__ T dotk(const T *p, const T *s) {
 #pragma unroll
   for (int a = 0; a < LEN; ++a) acc = fma(p[a * PS], s[a], acc);
   return acc;
-}
-
-// In-place lower Cholesky in double-float arithmetic by one CTA; the strict
-// upper triangle is left untouched and the reciprocals of the pivots go to
-// inv[k].  Returns false at the first non-positive or non-finite pivot.
-__device__ __noinline__ bool cholesky_cta_df(df64 *A, int Q, int ld, df64 *inv) {
-  const int tid = threadIdx.x, NT = blockDim.x;
-  for (int k = 0; k < Q; ++k) {
-    __syncthreads();
-    const df64 d = A[k * ld + k];
-    if (!(d.hi > 0.f) || !isfinite(d.hi)) return false;
-    const df64 l = df_sqrt(d);
-    const df64 il = df_div(df64{1.f, 0.f}, l);
-    __syncthreads();
-    if (tid == 0) {
-      A[k * ld + k] = l;
-      inv[k] = il;
-    }
-    for (int i = k + 1 + tid; i < Q; i += NT) A[i * ld + k] = df_mul(A[i * ld + k], il);
-    __syncthreads();
-    const int m = Q - k - 1;
-    for (int e = tid; e < m * m; e += NT) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      if (j <= i) A[i * ld + j] = df_fnms(A[i * ld + k], A[j * ld + k], A[i * ld + j]);
-    }
-  }
-  __syncthreads();
-  return true;
 }
 
 // One factor of the batched slice chain for a uniform rank RU: P_{q+1} =
@@ -376,7 +327,10 @@ __global__ void __launch_bounds__(kMaxThreads)
     const int In = I[n], Rn = R[n], Rn1 = R[(n + 1) % N], Q = Rn * Rn1;
     const int Q4 = (Q + 3) & ~3;
     const int L = N - 1;
-    const int j0 = (int)((long long)J * c / C), j1 = (int)((long long)J * (c + 1) / C);
+    // samples of this CTA: CTAs cw0..C-1 share the J samples (with cw0 = 1 CTA 0
+    // factorises the scaled variant's Gram matrix while the others work on them)
+    const int cr = c - lay.cw0, CWk = C - lay.cw0;
+    const int j0 = cr < 0 ? 0 : (int)((long long)J * cr / CWk), j1 = cr < 0 ? 0 : (int)((long long)J * (cr + 1) / CWk);
     const int jb = j1 - j0, jb4 = (jb + 3) & ~3;
     cur_n = n;
     cur_Q = Q;
@@ -741,65 +695,39 @@ __global__ void __launch_bounds__(kMaxThreads)
       }
       cluster.sync();
       if (c == 0) {
-        // factor, growing the damping on failure (1e-12 tr(h)/Q * 10^m, m = 0..6)
-        if constexpr (kDF) {
-          df64 *A = reinterpret_cast<df64 *>(h64);
-          df64 *hd = reinterpret_cast<df64 *>(hdiag);
-          df64 *inv = reinterpret_cast<df64 *>(smem + lay.off_reg);   // reciprocal pivots (reg is free here)
-          if (tid == 0) {
-            double tr = 0.0;
-            for (int q = 0; q < Q; ++q) tr += df_to_double(hd[q]) - D.damping;
-            misc[2] = tr;
-          }
+        // factor, growing the damping on failure (1e-12 tr(h)/Q * 10^m, m = 0..6);
+        // the factor and reciprocal pivots go to D.lfac for every CTA's solves
+        using V = typename GramScalar<T>::type;
+        const V *A = reinterpret_cast<const V *>(h64);
+        const V *hd = reinterpret_cast<const V *>(hdiag);
+        V *colbuf = reinterpret_cast<V *>(smem + lay.off_reg);   // reg is free here
+        V *pinv = colbuf + 2 * Q;
+        V *lout = static_cast<V *>(D.lfac);
+        if (tid == 0) {
+          double tr = 0.0;
+          for (int q = 0; q < Q; ++q) tr += gs_to_double(hd[q]) - D.damping;
+          misc[2] = tr;
+        }
+        __syncthreads();
+        const double tr = misc[2];
+        const int Qb = (Q + 3) >> 2;
+        const bool one_block = Qb * (Qb + 1) / 2 <= NT;   // else two blocks per thread
+        auto attempt = [&](double extra) {
+          return one_block ? gram_factor_reg<V, 1>(A, Q, QH, extra, colbuf, pinv, lout)
+                           : gram_factor_reg<V, 2>(A, Q, QH, extra, colbuf, pinv, lout);
+        };
+        bool ok = attempt(0.0);
+        double extra = 0.0;
+        for (int m = 0; m < 7 && !ok; ++m) {
+          extra = 1e-12 * tr / Q * pow(10.0, (double)m);
           __syncthreads();
-          const double tr = misc[2];
-          bool ok = cholesky_cta_df(A, Q, QH, inv);
-          double extra = 0.0;
-          for (int m = 0; m < 7 && !ok; ++m) {
-            extra = 1e-12 * tr / Q * pow(10.0, (double)m);
-            const df64 ex = df_from_double(extra);
-            __syncthreads();
-            for (int e = tid; e < Q * Q; e += NT) {
-              const int a = e / Q, b = e % Q;
-              if (a == b) A[a * QH + a] = df_add(hd[a], ex);
-              else if (a > b) A[a * QH + b] = A[b * QH + a];
-            }
-            ok = cholesky_cta_df(A, Q, QH, inv);
-          }
-          if (rec && ok && extra > 0.0)
-            for (int q = tid; q < Q; q += NT) D.dbg_h[q * Q + q] = df_to_double(hd[q]) + extra;
-          __syncthreads();
-          for (int q = tid; q < Q; q += NT) hd[q] = inv[q];   // the diagonal copy is no longer needed
-          if (tid == 0) {
-            misc[0] = ok ? 1.0 : 0.0;
-            if (!ok) latch_status(D.status, kStatusNumeric);
-          }
-        } else {
-          if (tid == 0) {
-            double tr = 0.0;
-            for (int q = 0; q < Q; ++q) tr += hdiag[q] - D.damping;
-            misc[2] = tr;
-          }
-          __syncthreads();
-          const double tr = misc[2];
-          bool ok = cholesky_cta(h64, Q, QH);
-          double extra = 0.0;
-          for (int m = 0; m < 7 && !ok; ++m) {
-            extra = 1e-12 * tr / Q * pow(10.0, (double)m);
-            __syncthreads();
-            for (int e = tid; e < Q * Q; e += NT) {
-              const int a = e / Q, b = e % Q;
-              if (a == b) h64[a * QH + a] = hdiag[a] + extra;
-              else if (a > b) h64[a * QH + b] = h64[b * QH + a];
-            }
-            ok = cholesky_cta(h64, Q, QH);
-          }
-          if (tid == 0) {
-            misc[0] = ok ? 1.0 : 0.0;
-            if (!ok) latch_status(D.status, kStatusNumeric);
-          }
-          if (rec && ok && extra > 0.0)
-            for (int q = tid; q < Q; q += NT) D.dbg_h[q * Q + q] = hdiag[q] + extra;
+          ok = attempt(extra);
+        }
+        if (rec && ok && extra > 0.0)
+          for (int q = tid; q < Q; q += NT) D.dbg_h[q * Q + q] = gs_to_double(hd[q]) + extra;
+        if (tid == 0) {
+          misc[0] = ok ? 1.0 : 0.0;
+          if (!ok) latch_status(D.status, kStatusNumeric);
         }
       }
     }
@@ -810,44 +738,48 @@ __global__ void __launch_bounds__(kMaxThreads)
     const int ldg = lay.ldg;
     for (int i0 = 0; i0 < In; i0 += lay.TI) {
       const int ti = min(lay.TI, In - i0);
-      if constexpr (kTC) {
-        tc_chunk(ti, i0);
+      if (c < lay.cw0) {   // no samples on this CTA: a zero partial gradient
+        for (int e = tid; e < ti * Q; e += NT) reg[(size_t)(e / Q) * ldq + e % Q] = T(0);
       } else {
-        if ((Q * (int)sizeof(T)) % 16 == 0 && ((D.slice_tma >> n) & 1)) {
-          const int nch = Q * (int)sizeof(T) / 16;
-          for (int e = tid; e < ti * nch; e += NT) {
-            const int ii = e / nch, ch = e - ii * nch;
-            cp_async16(reinterpret_cast<char *>(gs + (size_t)ii * ldg) + 16 * ch,
-                       reinterpret_cast<const char *>(Gn + (size_t)(i0 + ii) * Q) + 16 * ch);
-          }
+        if constexpr (kTC) {
+          tc_chunk(ti, i0);
         } else {
-  #pragma unroll 4
-          for (int e = tid; e < ti * Q; e += NT) {
-            const int ii = e / Q, q = e - ii * Q;
-            gs[(size_t)ii * ldg + q] = ld_l2(Gn + (size_t)(i0 + ii) * Q + q);
+          if ((Q * (int)sizeof(T)) % 16 == 0 && ((D.slice_tma >> n) & 1)) {
+            const int nch = Q * (int)sizeof(T) / 16;
+            for (int e = tid; e < ti * nch; e += NT) {
+              const int ii = e / nch, ch = e - ii * nch;
+              cp_async16(reinterpret_cast<char *>(gs + (size_t)ii * ldg) + 16 * ch,
+                         reinterpret_cast<const char *>(Gn + (size_t)(i0 + ii) * Q) + 16 * ch);
+            }
+          } else {
+    #pragma unroll 4
+            for (int e = tid; e < ti * Q; e += NT) {
+              const int ii = e / Q, q = e - ii * Q;
+              gs[(size_t)ii * ldg + q] = ld_l2(Gn + (size_t)(i0 + ii) * Q + q);
+            }
           }
+          if (Q4 > Q)
+            for (int e = tid; e < ti * (Q4 - Q); e += NT) gs[(size_t)(e / (Q4 - Q)) * ldg + Q + e % (Q4 - Q)] = T(0);
+          cp_async_wait_all();
+          __syncthreads();
+          // residual, weighted in place: X_s(jl, i) <- w_j (G Z^T - X_S)(i, jl)
+          {
+            XT *xsp = xs;
+            const int ldxs = lay.ldxs;
+            T *dbg_e = rec ? static_cast<T *>(D.dbg_e) : nullptr;
+            const T *wt = wt_s;
+            gemm_s<2, false, false, T>(ti, jb, Q, gs, ldg, zs, ldq, nullptr, [=](int ii, int jl, T v) {
+              T *xp = reinterpret_cast<T *>(xsp) + (size_t)jl * ldxs + i0 + ii;
+              const T e = v - *xp;
+              if (dbg_e) dbg_e[(size_t)(j0 + jl) * In + i0 + ii] = e;
+              *xp = e * wt[jl];
+            });
+          }
+          __syncthreads();
+          // partial gradient of this CTA's samples: Gp(i, q) = sum_jl Ew(jl, i) Z(jl, q)
+          gemm_s<4, true, true, T>(ti, Q, jb, reinterpret_cast<T *>(xs) + i0, lay.ldxs, zs, ldq, nullptr,
+                                   [=](int ii, int q, T v) { reg[(size_t)ii * ldq + q] = v; });
         }
-        if (Q4 > Q)
-          for (int e = tid; e < ti * (Q4 - Q); e += NT) gs[(size_t)(e / (Q4 - Q)) * ldg + Q + e % (Q4 - Q)] = T(0);
-        cp_async_wait_all();
-        __syncthreads();
-        // residual, weighted in place: X_s(jl, i) <- w_j (G Z^T - X_S)(i, jl)
-        {
-          XT *xsp = xs;
-          const int ldxs = lay.ldxs;
-          T *dbg_e = rec ? static_cast<T *>(D.dbg_e) : nullptr;
-          const T *wt = wt_s;
-          gemm_s<2, false, false, T>(ti, jb, Q, gs, ldg, zs, ldq, nullptr, [=](int ii, int jl, T v) {
-            T *xp = reinterpret_cast<T *>(xsp) + (size_t)jl * ldxs + i0 + ii;
-            const T e = v - *xp;
-            if (dbg_e) dbg_e[(size_t)(j0 + jl) * In + i0 + ii] = e;
-            *xp = e * wt[jl];
-          });
-        }
-        __syncthreads();
-        // partial gradient of this CTA's samples: Gp(i, q) = sum_jl Ew(jl, i) Z(jl, q)
-        gemm_s<4, true, true, T>(ti, Q, jb, reinterpret_cast<T *>(xs) + i0, lay.ldxs, zs, ldq, nullptr,
-                                 [=](int ii, int q, T v) { reg[(size_t)ii * ldq + q] = v; });
       }
       cluster.sync();
       const int r0 = ti * c / C, r1 = ti * (c + 1) / C;
@@ -920,120 +852,81 @@ __global__ void __launch_bounds__(kMaxThreads)
 
     // ---- scaled direction p = -g h^{-1} on the owned rows, then the update --
     if (scaled) {
-      const int QH = lay.QH;
-      const double *L0 = cluster.map_shared_rank(h64, 0);
+      // every CTA copies the factor (written by CTA 0 before the chunk loop's
+      // barriers) into its own shared memory at an odd pitch, so that both a
+      // column (forward solve) and a row (backward solve) of L are read
+      // without bank conflicts; then one warp per owned row solves
+      // L y = -g^T and L^T x = y in the Gram-solve scalar.
+      using V = typename GramScalar<T>::type;
+      const int ldl = Q | 1;
+      V *Lc = reinterpret_cast<V *>(h64);
+      V *ivc = reinterpret_cast<V *>(hdiag);
       const bool ok = *cluster.map_shared_rank(misc, 0) != 0.0;
       const int warp = tid >> 5, lane = tid & 31, nw = NT >> 5;
       const int r0 = In * c / C;   // single chunk: owned rows [r0, r0 + own_rows)
       constexpr int QM = 4;        // Q <= 128 = 32 * QM
-      if constexpr (kDF) {
-        // local copy of the factor (lower triangle) and the reciprocal pivots
-        df64 *Lc = reinterpret_cast<df64 *>(h64);
-        df64 *ivc = reinterpret_cast<df64 *>(hdiag);
-        if (c != 0 && ok) {
-          const df64 *Lr = reinterpret_cast<const df64 *>(L0);
-          const df64 *ivr = reinterpret_cast<const df64 *>(cluster.map_shared_rank(hdiag, 0));
-          for (int e = tid; e < Q * Q; e += NT) {
-            const int a = e / Q, b = e - a * Q;
-            if (b <= a) Lc[a * QH + b] = Lr[a * QH + b];
-          }
-          for (int q = tid; q < Q; q += NT) ivc[q] = ivr[q];
+      if (ok) {
+        const V *Lg = static_cast<const V *>(D.lfac);
+        for (int e = tid; e < Q * Q; e += NT) {
+          const int k = e / Q, q = e - k * Q;
+          if (q >= k) Lc[k * ldl + q] = gs_ldcg(Lg + e);
         }
-        __syncthreads();
-        for (int rr = warp; rr < own_rows; rr += nw) {
-          const int i = r0 + rr;
-          df64 y[QM];
-#pragma unroll
-          for (int m = 0; m < QM; ++m) {
-            const int q = lane + 32 * m;
-            y[m] = df64{(q < Q) ? -(float)gown[(size_t)rr * ldq + q] : 0.f, 0.f};
-          }
-          if (ok) {
-            for (int k = 0; k < Q; ++k) {        // L y = -g^T
-              df64 yk = df64{0.f, 0.f};
-#pragma unroll
-              for (int m = 0; m < QM; ++m)
-                if ((k >> 5) == m && lane == (k & 31)) yk = df_mul(y[m], ivc[k]);
-              yk.hi = __shfl_sync(0xffffffffu, yk.hi, k & 31);
-              yk.lo = __shfl_sync(0xffffffffu, yk.lo, k & 31);
-#pragma unroll
-              for (int m = 0; m < QM; ++m) {
-                const int q = lane + 32 * m;
-                if (q == k) y[m] = yk;
-                else if (q > k && q < Q) y[m] = df_fnms(Lc[q * QH + k], yk, y[m]);
-              }
-            }
-            for (int k = Q - 1; k >= 0; --k) {   // L^T x = y
-              df64 xk = df64{0.f, 0.f};
-#pragma unroll
-              for (int m = 0; m < QM; ++m)
-                if ((k >> 5) == m && lane == (k & 31)) xk = df_mul(y[m], ivc[k]);
-              xk.hi = __shfl_sync(0xffffffffu, xk.hi, k & 31);
-              xk.lo = __shfl_sync(0xffffffffu, xk.lo, k & 31);
-#pragma unroll
-              for (int m = 0; m < QM; ++m) {
-                const int q = lane + 32 * m;
-                if (q == k) y[m] = xk;
-                else if (q < k) y[m] = df_fnms(Lc[k * QH + q], xk, y[m]);
-              }
-            }
-          } else {
-#pragma unroll
-            for (int m = 0; m < QM; ++m) y[m] = df64{0.f, 0.f};
-          }
-          __syncwarp();
-#pragma unroll
-          for (int m = 0; m < QM; ++m) {
-            const int q = lane + 32 * m;
-            if (q >= Q) continue;
-            const size_t gi = (size_t)i * Q + q;
-            const T p = (T)(y[m].hi + y[m].lo);
-            const T nv = ld_l2(Gn + gi) + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
-            if (!isfinite(nv)) latch_status(D.status, kStatusNumeric);
-            Gn[gi] = nv;
-            gown[(size_t)rr * ldq + q] = nv;
-            if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
-          }
-        }
-      } else {
+        for (int q = tid; q < Q; q += NT) ivc[q] = gs_ldcg(Lg + (size_t)Q * Q + q);
+      }
+      __syncthreads();
       for (int rr = warp; rr < own_rows; rr += nw) {
         const int i = r0 + rr;
-        double y[QM];
+        V y[QM];
 #pragma unroll
         for (int m = 0; m < QM; ++m) {
           const int q = lane + 32 * m;
-          y[m] = (q < Q) ? -(double)gown[(size_t)rr * ldq + q] : 0.0;
+          gs_from_double((q < Q) ? -(double)gown[(size_t)rr * ldq + q] : 0.0, y[m]);
         }
         if (ok) {
-          for (int k = 0; k < Q; ++k) {        // L y = -g^T
-            double yk = 0.0;
+          // branch-free sweeps: every lane of a live 32-block updates (clamped
+          // addresses, results selected); blocks the sweep has left are skipped
+          // with warp-uniform branches
+          int qc[QM];
 #pragma unroll
-            for (int m = 0; m < QM; ++m)
-              if ((k >> 5) == m && lane == (k & 31)) yk = y[m] / L0[k * QH + k];
-            yk = __shfl_sync(0xffffffffu, yk, k & 31);
+          for (int m = 0; m < QM; ++m) qc[m] = min(lane + 32 * m, Q - 1);
+          for (int k = 0; k < Q; ++k) {        // L y = -g^T (column sweep)
+            const int mk = k >> 5;
+            V yk = gs_shfl(y[0], k & 31);
+#pragma unroll
+            for (int m = 1; m < QM; ++m) {
+              const V sm = gs_shfl(y[m], k & 31);
+              if (mk == m) yk = sm;
+            }
+            yk = gs_mul(yk, ivc[k]);
+            const V *col = Lc + k * ldl;
 #pragma unroll
             for (int m = 0; m < QM; ++m) {
+              if (m < mk || 32 * m >= Q) continue;
               const int q = lane + 32 * m;
-              if (q == k) y[m] = yk;
-              else if (q > k && q < Q) y[m] = fma(-L0[q * QH + k], yk, y[m]);
+              const V nv = gs_fnms(col[qc[m]], yk, y[m]);
+              y[m] = (q > k) ? nv : ((q == k) ? yk : y[m]);
             }
           }
-          for (int k = Q - 1; k >= 0; --k) {   // L^T x = y
-            double xk = 0.0;
+          for (int k = Q - 1; k >= 0; --k) {   // L^T x = y (row sweep)
+            const int mk = k >> 5;
+            V xk = gs_shfl(y[0], k & 31);
 #pragma unroll
-            for (int m = 0; m < QM; ++m)
-              if ((k >> 5) == m && lane == (k & 31)) xk = y[m] / L0[k * QH + k];
-            xk = __shfl_sync(0xffffffffu, xk, k & 31);
+            for (int m = 1; m < QM; ++m) {
+              const V sm = gs_shfl(y[m], k & 31);
+              if (mk == m) xk = sm;
+            }
+            xk = gs_mul(xk, ivc[k]);
 #pragma unroll
             for (int m = 0; m < QM; ++m) {
+              if (m > mk) continue;
               const int q = lane + 32 * m;
-              if (q == k) y[m] = xk;
-              else if (q < k) y[m] = fma(-L0[k * QH + q], xk, y[m]);
+              const V nv = gs_fnms(Lc[qc[m] * ldl + k], xk, y[m]);
+              y[m] = (q < k) ? nv : ((q == k) ? xk : y[m]);
             }
           }
         } else {
 #pragma unroll
-          for (int m = 0; m < QM; ++m) y[m] = 0.0;
+          for (int m = 0; m < QM; ++m) gs_from_double(0.0, y[m]);
         }
         __syncwarp();
 #pragma unroll
@@ -1041,14 +934,13 @@ __global__ void __launch_bounds__(kMaxThreads)
           const int q = lane + 32 * m;
           if (q >= Q) continue;
           const size_t gi = (size_t)i * Q + q;
-          const T p = (T)y[m];
+          const T p = (T)gs_to_double(y[m]);
           const T nv = ld_l2(Gn + gi) + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
           if (!isfinite(nv)) latch_status(D.status, kStatusNumeric);
           Gn[gi] = nv;
           gown[(size_t)rr * ldq + q] = nv;
           if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
         }
-      }
       }
       if (D.dist == 2) {
         __syncthreads();
