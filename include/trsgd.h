@@ -79,6 +79,18 @@ typedef enum { TRSGD_FP64 = 0, TRSGD_FP32 = 1, TRSGD_BF16_MIXED = 2 } trsgd_prec
 
 typedef enum { TRSGD_DTYPE_F64 = 0, TRSGD_DTYPE_F32 = 1, TRSGD_DTYPE_BF16 = 2 } trsgd_dtype;
 
+/* Execution path of an iteration.
+ * CLUSTER: one fused persistent kernel, one thread-block cluster (<= 16 SMs)
+ *   per problem, everything on chip (R_n <= 16, R_n R_{n+1} <= 256, scaled
+ *   variant R_n R_{n+1} <= 128); batched problems, every distribution.
+ * GRID: a short sequence of kernels over the whole GPU per iteration, the
+ *   residual and gradient contractions on the tensor cores (tcgen05, BF16
+ *   operands; FP32 as three BF16 pieces per operand); one problem, uniform
+ *   sampling, plain variant, FP32 / BF16-mixed, R_n <= 32,
+ *   R_n R_{n+1} <= 512.
+ * AUTO: CLUSTER when the problem fits it, else GRID. */
+typedef enum { TRSGD_PATH_AUTO = 0, TRSGD_PATH_CLUSTER = 1, TRSGD_PATH_GRID = 2 } trsgd_path;
+
 /* One TR problem (Algorithm 3's arguments plus the stopping-free part of the
  * configuration). */
 typedef struct {
@@ -96,6 +108,8 @@ typedef struct {
   double eta, b, eps;              /* AdaGrad eta, b, epsilon                */
   double damping;                  /* eta^t of the damped preconditioner     */
   uint64_t seed;                   /* Philox key of this problem             */
+  int32_t path;                    /* trsgd_path                             */
+  int32_t reserved;                /* must be 0                              */
 } trsgd_config;
 
 typedef struct trsgd_handle trsgd_handle;
@@ -147,7 +161,8 @@ trsgd_status trsgd_run(trsgd_handle *h, int64_t t0, int64_t T, int64_t chunk,
  * the iterates are bit-identical to trsgd_run from the same t.  Enqueued on
  * the handle's stream; does not synchronise.  TRSGD_EUNSUPPORTED for the
  * optimal distribution (its tables are built for a mode drawn on the host).
- * trsgd_set_counter enqueues c = t (also capturable). */
+ * trsgd_set_counter enqueues c = t (also capturable).  The whole-GPU path
+ * (TRSGD_PATH_GRID) draws the mode on the host and returns EUNSUPPORTED. */
 trsgd_status trsgd_step_counter(trsgd_handle *h, int64_t T);
 trsgd_status trsgd_set_counter(trsgd_handle *h, int64_t t);
 
@@ -241,12 +256,16 @@ trsgd_status trsgd_adagrad_state(trsgd_handle *h, int32_t problem, int32_t core,
  * and threads per CTA.  set: 0 = query into *cluster / *threads, 1 = force
  * these values (validated; 0 keeps the current one).  trsgd_autotune times
  * the candidate shapes on scratch copies of the cores and keeps the fastest
- * (synchronising; the cores are left unchanged). */
+ * (synchronising; the cores are left unchanged).  On the whole-GPU path the
+ * query returns cluster 0 and threads 128, setting returns EUNSUPPORTED and
+ * trsgd_autotune does nothing. */
 trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster,
                                 int32_t *threads);
 trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial);
 
-/* Number of step-kernel launches enqueued by this handle so far. */
+/* Number of iteration kernels enqueued by this handle so far (the fused
+ * kernel counts once per launch of any number of iterations; the whole-GPU
+ * path launches five kernels per iteration). */
 int64_t trsgd_launch_count(const trsgd_handle *h);
 
 void trsgd_destroy(trsgd_handle *h);

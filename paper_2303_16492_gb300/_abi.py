@@ -15,6 +15,7 @@ PLAIN, SCALED = 0, 1
 STEP_FIXED, STEP_ADAGRAD = 0, 1
 FP64, FP32, BF16_MIXED = 0, 1, 2
 DTYPE_F64, DTYPE_F32, DTYPE_BF16 = 0, 1, 2
+PATH_AUTO, PATH_CLUSTER, PATH_GRID = 0, 1, 2
 DBG_MODE, DBG_IDX, DBG_PF, DBG_Z, DBG_E, DBG_G, DBG_P, DBG_H = range(8)
 
 
@@ -36,6 +37,8 @@ class Config(ctypes.Structure):
         ("eps", ctypes.c_double),
         ("damping", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("path", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -34,6 +34,7 @@ class ProblemConfig:
     J_H: int = 0
     seed: int = 0
     x_dtype: int | None = None
+    path: int = _abi.PATH_AUTO
 
     def to_c(self) -> _abi.Config:
         c = _abi.Config()
@@ -55,6 +56,7 @@ class ProblemConfig:
         c.eps = self.eps
         c.damping = self.damping
         c.seed = int(self.seed)
+        c.path = int(self.path)
         return c
 
 

@@ -63,10 +63,41 @@ struct trsgd_handle {
   int64_t launches = 0;
   bool dbg = false;
   bool optimal = false;   // problem 0 samples from the optimal distribution
+  bool grid = false;      // whole-GPU path (grid.cu) instead of the fused cluster kernel
+  GridPath gp = {};
   OptBuffers opt = {};
   size_t dbg_bytes[8] = {};
   void *dbg_ptr[8] = {};
 };
+
+// Limits of the fused cluster kernel (ranks held in registers, one problem
+// per cluster in shared memory).
+static bool cluster_fits(const trsgd_config *cfg, int32_t np) {
+  for (int p = 0; p < np; ++p) {
+    const trsgd_config &c = cfg[p];
+    if (c.dist == TRSGD_DIST_OPTIMAL && np > 1) return false;
+    for (int k = 0; k < c.N; ++k) {
+      if (c.R[k] > kMaxRank) return false;
+      const int64_t Q = c.R[k] * c.R[(k + 1) % c.N];
+      if (Q > kMaxQPlain) return false;
+      if (c.variant == TRSGD_SCALED && Q > kMaxQScaled) return false;
+    }
+  }
+  return true;
+}
+
+// Limits of the whole-GPU path (grid.cu).
+static bool grid_fits(const trsgd_config *cfg, int32_t np) {
+  if (np != 1) return false;
+  const trsgd_config &c = cfg[0];
+  if (c.dist != TRSGD_DIST_UNIFORM || c.variant != TRSGD_PLAIN || c.prec == TRSGD_FP64) return false;
+  if (c.J > (1LL << 24)) return false;
+  for (int k = 0; k < c.N; ++k) {
+    if (c.R[k] > 32 || c.R[k] * c.R[(k + 1) % c.N] > 512) return false;
+    if (c.I[k] > (1LL << 24)) return false;
+  }
+  return true;
+}
 
 static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
   if (!cfg || np < 1) return TRSGD_EINVAL;
@@ -92,15 +123,14 @@ static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
     if (c.prec == TRSGD_FP64 && c.x_dtype != TRSGD_DTYPE_F64) return TRSGD_EINVAL;
     if (c.prec == TRSGD_FP32 && c.x_dtype != TRSGD_DTYPE_F32) return TRSGD_EINVAL;
     if (c.prec == TRSGD_BF16_MIXED && c.x_dtype == TRSGD_DTYPE_F64) return TRSGD_EINVAL;
-    // this build
-    if (c.dist == TRSGD_DIST_OPTIMAL && np > 1) return TRSGD_EUNSUPPORTED;
-    for (int k = 0; k < c.N; ++k) {
-      if (c.R[k] > kMaxRank) return TRSGD_EUNSUPPORTED;
-      const int64_t Q = c.R[k] * c.R[(k + 1) % c.N];
-      if (Q > kMaxQPlain) return TRSGD_EUNSUPPORTED;
-      if (c.variant == TRSGD_SCALED && Q > kMaxQScaled) return TRSGD_EUNSUPPORTED;
-    }
+    if (c.path < TRSGD_PATH_AUTO || c.path > TRSGD_PATH_GRID || c.path != cfg[0].path || c.reserved != 0)
+      return TRSGD_EINVAL;
   }
+  // this build
+  const bool cf = cluster_fits(cfg, np), gf = grid_fits(cfg, np);
+  if (cfg[0].path == TRSGD_PATH_CLUSTER && !cf) return TRSGD_EUNSUPPORTED;
+  if (cfg[0].path == TRSGD_PATH_GRID && !gf) return TRSGD_EUNSUPPORTED;
+  if (!cf && !gf) return TRSGD_EUNSUPPORTED;
   return TRSGD_OK;
 }
 
@@ -440,8 +470,40 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
   }
   if ((e = cudaMalloc((void **)&h->ddesc, sizeof(ProbDesc) * nproblems)) != cudaSuccess) return fail(from_cuda(e));
   h->buf.ptrs.push_back(h->ddesc);
-  st = choose_layout(*h, default_cluster(*h));
-  if (st != TRSGD_OK) return fail(st);
+  h->grid = cfg[0].path == TRSGD_PATH_GRID || !cluster_fits(cfg, nproblems);
+  if (!h->grid) {
+    st = choose_layout(*h, default_cluster(*h));
+    if (st == TRSGD_EUNSUPPORTED && cfg[0].path == TRSGD_PATH_AUTO && grid_fits(cfg, nproblems)) h->grid = true;
+    else if (st != TRSGD_OK) return fail(st);
+  }
+  if (h->grid) {
+    const trsgd_config &c = cfg[0];
+    GridPath &g = h->gp;
+    int Ii[kMaxOrder] = {}, Ri[kMaxOrder] = {};
+    for (int k = 0; k < c.N; ++k) {
+      Ii[k] = (int)c.I[k];
+      Ri[k] = (int)c.R[k];
+    }
+    const int np = c.prec == TRSGD_BF16_MIXED ? 1 : 3;
+    grid_layout(Ii, Ri, c.N, (int)c.J, np, g);
+    g.x_bf16 = h->xc_dtype == TRSGD_DTYPE_BF16 ? 1 : 0;
+    g.w = (float)(1.0 / (double)c.J);
+    const size_t bf = 2;
+    for (int p = 0; p < np && e == cudaSuccess; ++p) {
+      if ((e = h->buf.alloc((void **)&g.Gp[p], (size_t)g.Ip * g.ldg * bf)) != cudaSuccess ||
+          (e = h->buf.alloc((void **)&g.Zp[p], (size_t)g.Jp * g.ldz * bf)) != cudaSuccess ||
+          (e = h->buf.alloc((void **)&g.ZTp[p], (size_t)g.QTp * g.ldzt * bf)) != cudaSuccess ||
+          (e = h->buf.alloc((void **)&g.Ep[p], (size_t)g.Ip * g.lde * bf)) != cudaSuccess)
+        break;
+      cudaMemsetAsync(g.Zp[p], 0, (size_t)g.Jp * g.ldz * bf, h->stream);
+      cudaMemsetAsync(g.ZTp[p], 0, (size_t)g.QTp * g.ldzt * bf, h->stream);
+    }
+    for (int p = np; p < 3; ++p) g.Gp[p] = g.Zp[p] = g.ZTp[p] = g.Ep[p] = nullptr;
+    if (e == cudaSuccess) e = h->buf.alloc((void **)&g.gpart, g.gpart_elems * 4);
+    if (e == cudaSuccess) e = h->buf.alloc((void **)&g.col, (size_t)c.J * 8);
+    if (e == cudaSuccess) e = grid_prepare_gemm();
+    if (e != cudaSuccess) return fail(from_cuda(e));
+  }
   h->threads = 512;
   if ((e = cudaMemcpyAsync(h->ddesc, h->hdesc.data(), sizeof(ProbDesc) * nproblems, cudaMemcpyHostToDevice,
                            h->stream)) != cudaSuccess)
@@ -465,6 +527,16 @@ static trsgd_status read_status(trsgd_handle *h) {
 }
 
 static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
+  if (h->grid) {   // the mode is drawn on the host; five kernels per iteration
+    const ProbDesc &D = h->hdesc[0];
+    for (int64_t t = t0; t < t0 + nsteps; ++t) {
+      const int n = draw_mode(D.seed, t, D.N);
+      cudaError_t e = launch_grid_step(h->gp, D, n, t, h->dbg ? 1 : 0, h->stream);
+      if (e != cudaSuccess) return from_cuda(e);
+      h->launches += 5;
+    }
+    return TRSGD_OK;
+  }
   if (h->optimal) {   // per step: the optimal distribution of this step's mode, its draws, then the step
     const ProbDesc &D = h->hdesc[0];
     for (int64_t t = t0; t < t0 + nsteps; ++t) {
@@ -501,7 +573,8 @@ trsgd_status trsgd_step(trsgd_handle *h, int64_t t) {
 
 trsgd_status trsgd_step_counter(trsgd_handle *h, int64_t T) {
   if (!h || T < 0 || T > (1 << 20)) return TRSGD_EINVAL;
-  if (h->optimal) return TRSGD_EUNSUPPORTED;   // its per-step tables are drawn with the mode known on the host
+  // the optimal distribution and the whole-GPU path draw the mode on the host
+  if (h->optimal || h->grid) return TRSGD_EUNSUPPORTED;
   if (T == 0) return TRSGD_OK;
   cudaError_t e = launch_step(h->core_dtype, h->xc_dtype, h->rmax, h->ddesc, h->nprob, h->lay, h->threads, 0,
                               (int)T, h->d_t, h->stream);
@@ -681,6 +754,12 @@ static bool threads_fit(const trsgd_handle &h, int T) {
 
 trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster, int32_t *threads) {
   if (!h || !cluster || !threads) return TRSGD_EINVAL;
+  if (h->grid) {   // whole-GPU path: no cluster; 128-thread GEMM CTAs
+    if (set != 0) return TRSGD_EUNSUPPORTED;
+    *cluster = 0;
+    *threads = 128;
+    return TRSGD_OK;
+  }
   if (set == 0) {
     *cluster = h->lay.C;
     *threads = h->threads;
@@ -702,6 +781,7 @@ trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster, 
 
 trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial) {
   if (!h || steps_per_trial < 1) return TRSGD_EINVAL;
+  if (h->grid) return TRSGD_OK;   // tile shapes follow from the problem sizes
   // scratch copies of every core so that the trial steps leave the cores unchanged
   std::vector<std::vector<void *>> saved(h->nprob);
   std::vector<std::vector<size_t>> sizes(h->nprob);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cuda_bf16.h>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -65,7 +66,29 @@ struct OptBuffers {
   int *idx, *dims;
 };
 
+// Buffers and layout of the whole-GPU path (grid.cu) for one problem.
+// Operand pieces are BF16, K-major, zero-padded: G_n [Ip][ldg], Z [Jp][ldz],
+// Z^T [QTp][ldzt], weighted residual E [Ip][lde]; gpart holds the FP32
+// partial gradients of the split samples.
+struct GridPath {
+  int np;                  // BF16 pieces per operand (1 or 3)
+  int nt_res;              // N tile of the residual GEMM
+  int Jp, Ip, Qp, QTp;     // padded J (256), I (128), Q (64 for K, 256 for the Z^T rows)
+  long long ldg, ldz, ldzt, lde;
+  int max_splits;
+  size_t gpart_elems;
+  int x_bf16;              // mode-major copies of X in BF16 (else FP32)
+  float w;                 // uniform sampling: every weight 1/|F|
+  __nv_bfloat16 *Gp[3], *Zp[3], *ZTp[3], *Ep[3];
+  float *gpart;
+  long long *col;
+};
+
 // kernel launchers (defined in the .cu files)
+void grid_layout(const int *I, const int *R, int N, int J, int np, GridPath &g);
+int grid_nt_max(int np);
+cudaError_t grid_prepare_gemm();
+cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long long t, int rec, cudaStream_t s);
 cudaError_t launch_optimal_sampling(int core_dtype, int x_dtype, int N, int n, const int *I, const int *R,
                                     const void *const *cores, const void *xmode, long long ldx,
                                     unsigned long long seed, long long t, int J, OptBuffers &b, cudaStream_t s);

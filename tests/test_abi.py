@@ -30,8 +30,8 @@ def test_status_strings(lib):
 
 
 def test_config_struct_layout():
-    assert ctypes.sizeof(_abi.Config) == 216
-    assert _abi.Config.I.offset == 8 and _abi.Config.seed.offset == 208
+    assert ctypes.sizeof(_abi.Config) == 224
+    assert _abi.Config.I.offset == 8 and _abi.Config.seed.offset == 208 and _abi.Config.path.offset == 216
 
 
 def _cfg(**kw):
@@ -90,13 +90,26 @@ def test_null_pointers(lib):
 
 
 def test_unsupported_shapes_reported(lib):
+    c = _cfg(path=_abi.PATH_CLUSTER)
+    c.R[0] = 17                          # rank beyond the fused kernel's registers
+    assert _init(lib, c)[0] == _abi.EUNSUPPORTED
     c = _cfg()
-    c.R[0] = 17
+    c.R[0] = 33                          # beyond both paths
+    assert _init(lib, c)[0] == _abi.EUNSUPPORTED
+    c = _cfg(dist=_abi.DIST_EUCLIDEAN)
+    c.R[0] = 17                          # the whole-GPU path samples uniformly only
     assert _init(lib, c)[0] == _abi.EUNSUPPORTED
     c = _cfg(variant=_abi.SCALED)
     for k in range(3):
-        c.R[k] = 12                      # Q = 144 > scaled limit
+        c.R[k] = 12                      # Q = 144 > scaled limit of the fused kernel
     assert _init(lib, c)[0] == _abi.EUNSUPPORTED
+    c = _cfg(path=_abi.PATH_GRID, prec=_abi.FP64, x_dtype=_abi.DTYPE_F64)
+    assert _init(lib, c)[0] == _abi.EUNSUPPORTED
+
+
+def test_path_field_validated(lib):
+    assert _init(lib, _cfg(path=3))[0] == _abi.EINVAL
+    assert _init(lib, _cfg(reserved=1))[0] == _abi.EINVAL
 
 
 def test_null_handle_calls(lib):
