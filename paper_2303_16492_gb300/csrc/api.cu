@@ -502,6 +502,7 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
     if (e == cudaSuccess) e = h->buf.alloc((void **)&g.gpart, g.gpart_elems * 4);
     if (e == cudaSuccess) e = h->buf.alloc((void **)&g.col, (size_t)c.J * 8);
     if (e == cudaSuccess) e = grid_prepare_gemm();
+    if (e == cudaSuccess) e = grid_tensor_maps(Ri, c.N, g);
     if (e != cudaSuccess) return fail(from_cuda(e));
   }
   h->threads = 512;

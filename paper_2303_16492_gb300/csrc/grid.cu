@@ -8,12 +8,12 @@
 //                           Algorithm 2, the same counters as the fused
 //                           kernel), fiber column, and the sampled subchain
 //                           row Z(j, r + r' R_n) = P_j(r', r) (Def. subchain)
-//                           as BF16 pieces, row-major and transposed;
+//                           as BF16 pieces, row-major [j][q];
 //   3. grid_gemm_kernel     E = G_n Z^T - X_S, weighted (residual epilogue
 //                           reads the fibers straight from the mode-major
 //                           copy of X);
 //   4. grid_gemm_kernel     partial gradients (E D) Z over slices of the
-//                           samples (split-K);
+//                           samples (split-K; Z read MN-major, no transpose);
 //   5. grid_update_kernel   fixed-order sum of the partials, step rule
 //                           (fixed alpha or AdaGrad), update of G_n.
 //
@@ -79,8 +79,7 @@ struct GridSampleArgs {
   const float *cores[kMaxOrder];
   long long *col;                       // [J] fiber column of X_[n]
   __nv_bfloat16 *Z[3];                  // [Jp][ldz] row-major pieces
-  __nv_bfloat16 *ZT[3];                 // [QTp][ldzt] transposed pieces
-  long long ldz, ldzt;
+  long long ldz;
   int *dbg_idx;                         // [J][N] (-1 at n)
   double *dbg_pf;                       // [J]
   float *dbg_z;                         // [J][Q]
@@ -165,26 +164,25 @@ __global__ void __launch_bounds__(32 * kGridWarps) grid_samples_kernel(GridSampl
       }
       __nv_bfloat16 p[3];
       bf16_pieces(v, a.np, p);
-      for (int pc = 0; pc < a.np; ++pc) {
-        a.Z[pc][(size_t)j * a.ldz + q] = p[pc];
-        if (q < a.Q) a.ZT[pc][(size_t)q * a.ldzt + j] = p[pc];
-      }
+      for (int pc = 0; pc < a.np; ++pc) a.Z[pc][(size_t)j * a.ldz + q] = p[pc];
     }
   }
 }
 
-// ---- 3/4. streaming tcgen05 GEMM -------------------------------------------
+// ---- 3/4. tcgen05 GEMM fed by TMA --------------------------------------------
 // D(m, n) = sum_k A(m, k) B(n, k) over the products of operand pieces
 // (pa, pb) with pa + pb <= maxord.  A: M x K, B: N x K, both K-major BF16
-// (row stride lda / ldb elements, buffers padded so that every tile read is
-// in bounds).  Tile 128 x NT, K in chunks of 64 through a ring of S
-// shared-memory stages filled by cp.async (the loads of chunk c + S - 2 are
-// issued after the MMAs of chunk c - 2 completed, so the tensor pipe always
-// has the next chunk queued); one thread issues the MMAs, accumulators in TMEM.
-struct GridGemmArgs {
-  const __nv_bfloat16 *A[3];
-  const __nv_bfloat16 *B[3];
-  long long lda, ldb;
+// in global memory, described by 2-D tensor maps (boxes of 64 K-elements x
+// 128 rows for A and x NT rows for B, 128-byte swizzle).  Tile 128 x NT, K in
+// chunks of 64 through a ring of S shared-memory stages: one thread issues
+// the TMA copies (completion on a "full" barrier per stage) and the MMAs
+// (completion on an "empty" barrier per stage); the MMAs of chunk c are
+// queued before the thread waits for chunk c - 1 to finish and refills that
+// stage, so the tensor pipe always has work.  Accumulators in TMEM; every
+// wait is bounded and a timeout latches TRSGD_ETIMEOUT.
+struct __align__(64) GridGemmArgs {
+  CUtensorMap tmA[3];
+  CUtensorMap tmB[3];
   int npa, npb, maxord;
   int kchunks, kper;       // chunks of 64 along K in total / per split (blockIdx.z)
   int NT, S;               // N tile (multiple of 16, <= 256), pipeline stages (2..4)
@@ -209,99 +207,151 @@ __host__ __device__ inline size_t grid_gemm_stage_bytes(int npa, int npb, int NT
   return (size_t)npa * 128 * 128 + (size_t)npb * NT * 128;
 }
 
-__global__ void __launch_bounds__(128) grid_gemm_kernel(GridGemmArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ uint64_t bars[5];   // [0..3] MMA completion per stage, [4] spare
+namespace {
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// K-major operand tile with 128-byte swizzle: rows of 128 bytes, 8-row atoms
+// 1024 bytes apart (SBO); the K offset inside the row is added to the start
+// address; layout type 2 (128-byte swizzle) in bits 61-63.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// 32 consecutive 32-bit TMEM columns of this thread's lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(128) grid_gemm_kernel(const __grid_constant__ GridGemmArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t full[4], empty[4];
   __shared__ uint32_t tslot;
+  __shared__ int last_s, bad_s;
+  __shared__ long long col_s[256];   // residual epilogue: fiber columns of the tile's samples
+  // the 128-byte swizzle repeats every 1024 bytes: align the stage ring to it
+  unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * 128, n0 = blockIdx.y * a.NT;
   const int kbeg = blockIdx.z * a.kper, kend = min(kbeg + a.kper, a.kchunks);
   const int nck = max(0, kend - kbeg);
   const size_t stage = grid_gemm_stage_bytes(a.npa, a.npb, a.NT);
-  const int S = a.S, P = S - 2;   // prefetch distance
+  const int S = a.S;
+  const uint32_t tx_bytes = (uint32_t)stage;
   if (tid == 0) {
-    for (int s = 0; s < 4; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < 4; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
     fence_mbar_init();
+    last_s = -1;
+    bad_s = 0;
   }
   if (warp == 0) tmem_alloc(&tslot, 256);
+  if (a.mode == 1)
+    for (int jl = tid; jl < a.NT; jl += 128) col_s[jl] = (n0 + jl < a.Nv) ? a.col[n0 + jl] : 0;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tslot;
 
-  auto load_chunk = [&](int c) {
-    unsigned char *st = smem + (size_t)(c % S) * stage;
-    const long long k0 = (long long)(kbeg + c) * 64;
-    for (int pa = 0; pa < a.npa; ++pa) {
-      const __nv_bfloat16 *src = a.A[pa] + (long long)m0 * a.lda + k0;
-      unsigned char *dst = st + (size_t)pa * 16384;
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int e = tid + 128 * u, r = e >> 3, kc = e & 7;
-        cp_async16(dst + kmaj_off(r, kc * 8, 8), src + (long long)r * a.lda + kc * 8);
+  if (tid == 0 && nck > 0) {
+    auto issue = [&](int c) {   // TMA copies of chunk c into stage c % S
+      unsigned char *st = smem + (size_t)(c % S) * stage;
+      const int k0 = (kbeg + c) * 64;
+      mbar_arrive_expect_tx(&full[c % S], tx_bytes);
+      for (int pa = 0; pa < a.npa; ++pa) tma_load_2d(st + pa * 16384, &a.tmA[pa], k0, m0, &full[c % S]);
+      for (int pb = 0; pb < a.npb; ++pb)
+        tma_load_2d(st + a.npa * 16384 + pb * a.NT * 128, &a.tmB[pb], k0, n0, &full[c % S]);
+    };
+    const uint32_t idesc = umma_idesc_bf16(128, a.NT, 0, 0);
+    int issued = 0, last = -1;
+    bool bad = false;
+    for (; issued < min(S, nck); ++issued) issue(issued);
+    for (int c = 0; c < nck && !bad; ++c) {
+      if (!mbar_wait_bounded(&full[c % S], (uint32_t)((c / S) & 1), kGridWaitLimit)) {
+        bad = true;
+        break;
       }
-    }
-    for (int pb = 0; pb < a.npb; ++pb) {
-      const __nv_bfloat16 *src = a.B[pb] + (long long)n0 * a.ldb + k0;
-      unsigned char *dst = st + (size_t)a.npa * 16384 + (size_t)pb * a.NT * 128;
-      for (int e = tid; e < a.NT * 8; e += 128) {
-        const int r = e >> 3, kc = e & 7;
-        cp_async16(dst + kmaj_off(r, kc * 8, 8), src + (long long)r * a.ldb + kc * 8);
-      }
-    }
-  };
-  auto wait_mma = [&](int c) {   // MMAs of chunk c have completed
-    if (!mbar_wait_bounded(&bars[c % S], (uint32_t)((c / S) & 1), kGridWaitLimit)) latch_status(a.status, kStatusTimeout);
-  };
-  const uint32_t idesc = umma_idesc_bf16(128, a.NT, 0, 0);
-
-  for (int c = 0; c < P; ++c) {   // always P groups, so that group c holds chunk c
-    if (c < nck) load_chunk(c);
-    cp_async_commit();
-  }
-  for (int c = 0; c < nck; ++c) {
-    const int cn = c + P;
-    if (cn < nck) {
-      if (cn >= S) wait_mma(cn - S);
-      load_chunk(cn);
-    }
-    cp_async_commit();
-    if (P == 2) cp_async_wait_n<2>();
-    else if (P == 1) cp_async_wait_n<1>();
-    else cp_async_wait_n<0>();
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (tid == 0) {
       tc_fence_after();
       const uint32_t sb = smem_u32(smem + (size_t)(c % S) * stage);
       bool first = (c == 0);
-      for (int ks = 0; ks < 4; ++ks) {
+      for (int ks = 0; ks < 4; ++ks)
         for (int pa = 0; pa < a.npa; ++pa)
           for (int pb = 0; pb < a.npb; ++pb) {
             if (pa + pb > a.maxord) continue;
-            const uint64_t da = umma_desc(sb + pa * 16384 + ks * 256, 128, 1024);
-            const uint64_t db = umma_desc(sb + a.npa * 16384 + pb * a.NT * 128 + ks * 256, 128, 1024);
+            const uint64_t da = umma_desc_sw128(sb + pa * 16384 + ks * 32);
+            const uint64_t db = umma_desc_sw128(sb + a.npa * 16384 + pb * a.NT * 128 + ks * 32);
             umma_bf16(tbase, da, db, idesc, !first);
             first = false;
           }
+      umma_commit(&empty[c % S]);
+      last = c;
+      // refill the stage of chunk c - 1 once its MMAs are done
+      if (c >= 1 && issued < nck) {
+        if (!mbar_wait_bounded(&empty[(c - 1) % S], (uint32_t)(((c - 1) / S) & 1), kGridWaitLimit)) {
+          bad = true;
+          break;
+        }
+        issue(issued++);
       }
-      umma_commit(&bars[c % S]);
     }
+    if (bad) {   // let the copies in flight land before the CTA exits
+      latch_status(a.status, kStatusTimeout);
+      for (int c = last + 1; c < issued; ++c) mbar_wait_bounded(&full[c % S], (uint32_t)((c / S) & 1), kGridWaitLimit);
+    }
+    last_s = last;
+    bad_s = bad ? 1 : 0;
   }
-  if (nck > 0) wait_mma(nck - 1);
+  __syncthreads();
+  const int last = last_s;
+  bool ok = !bad_s && (nck == 0 || last == nck - 1);
+  if (last >= 0 && !mbar_wait_bounded(&empty[last % S], (uint32_t)((last / S) & 1), kGridWaitLimit)) {
+    latch_status(a.status, kStatusTimeout);
+    ok = false;
+  }
   tc_fence_after();
-
-  // epilogue: thread = accumulator row (TMEM lane), 8 columns per load
-  const int row = warp * 32 + lane, m = m0 + row;
-  for (int cb = 0; cb < a.NT / 8; ++cb) {
-    float v[8];
-    if (nck > 0) {
-      tmem_ld8(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 8), v);
-    } else {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = 0.f;
+  // residual epilogue: the CTA's X tile (NT fibers x 128 rows) into the now
+  // free stage memory with one burst of cp.async, xs[jl][row]
+  const int sx = a.x_bf16 ? 2 : 4;
+  if (a.mode == 1) {
+    const int cpc = 128 * sx / 16;   // 16-byte chunks per fiber segment
+    for (int e = tid; e < a.NT * cpc; e += 128) {
+      const int jl = e / cpc, ch = e - jl * cpc, j = n0 + jl;
+      const long long ms = m0 + (long long)ch * (16 / sx);
+      if (j < a.Nv && ms < a.ldx)
+        cp_async16(smem + (size_t)jl * 128 * sx + ch * 16,
+                   static_cast<const unsigned char *>(a.xmode) + (col_s[jl] * a.ldx + ms) * sx);
     }
-    const int nb = n0 + cb * 8;
+    cp_async_commit();
+    cp_async_wait_n<0>();
+    __syncthreads();
+  }
+
+  // epilogue: thread = accumulator row (TMEM lane); 32 columns per load, then 8
+  const int row = warp * 32 + lane, m = m0 + row;
+  const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+  auto emit8 = [&](int nb, const float *v) {   // columns nb .. nb + 7 of this row
     if (a.mode == 0) {
       if (m < a.Mv) {
         float *dst = a.C + (long long)blockIdx.z * a.cstride + (long long)m * a.ldc;
@@ -316,9 +366,9 @@ __global__ void __launch_bounds__(128) grid_gemm_kernel(GridGemmArgs a) {
         const int j = nb + u;
         float ew = 0.f;
         if (m < a.Mv && j < a.Nv) {
-          const long long xo = a.col[j] * a.ldx + m;
-          const float x = a.x_bf16 ? __bfloat162float(__ldg(static_cast<const __nv_bfloat16 *>(a.xmode) + xo))
-                                   : __ldg(static_cast<const float *>(a.xmode) + xo);
+          const int xo = (nb - n0 + u) * 128 + row;
+          const float x = a.x_bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(smem)[xo])
+                                   : reinterpret_cast<const float *>(smem)[xo];
           const float e = v[u] - x;
           if (a.dbg_e) a.dbg_e[(long long)j * a.Mv + m] = e;
           ew = e * a.w;
@@ -331,10 +381,51 @@ __global__ void __launch_bounds__(128) grid_gemm_kernel(GridGemmArgs a) {
       for (int pc = 0; pc < a.npe; ++pc)
         *reinterpret_cast<uint4 *>(a.E[pc] + (long long)m * a.lde + nb) = *reinterpret_cast<const uint4 *>(pe[pc]);
     }
+  };
+  int cb = 0;
+  for (; cb + 32 <= a.NT; cb += 32) {
+    float v[32];
+    if (ok && nck > 0) {
+      tmem_ld32(trow + (uint32_t)cb, v);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 32; ++u) v[u] = 0.f;
+    }
+#pragma unroll
+    for (int g = 0; g < 4; ++g) emit8(n0 + cb + 8 * g, v + 8 * g);
+  }
+  for (; cb < a.NT; cb += 8) {
+    float v[8];
+    if (ok && nck > 0) {
+      tmem_ld8(trow + (uint32_t)cb, v);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = 0.f;
+    }
+    emit8(n0 + cb, v);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, 256);
+}
+
+// ---- Z^T from Z (32 x 32 tiles through shared memory) ------------------------
+__global__ void grid_transpose_kernel(const __nv_bfloat16 *__restrict__ Z, long long ldz, int rows, int cols,
+                                      __nv_bfloat16 *__restrict__ ZT, long long ldzt) {
+  __shared__ unsigned short tile[32][34];
+  const int j0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const unsigned short *z = reinterpret_cast<const unsigned short *>(Z);
+  unsigned short *zt = reinterpret_cast<unsigned short *>(ZT);
+  for (int r = ty; r < 32; r += 8) {
+    const int j = j0 + r, q = q0 + tx;
+    tile[r][tx] = (j < rows && q < cols) ? z[(size_t)j * ldz + q] : (unsigned short)0;
+  }
+  __syncthreads();
+  for (int r = ty; r < 32; r += 8) {
+    const int q = q0 + r, j = j0 + tx;
+    if (q < cols && j < rows) zt[(size_t)q * ldzt + j] = tile[tx][r];
+  }
 }
 
 // ---- 5. sum of the partial gradients, step rule, update ---------------------
@@ -384,20 +475,21 @@ static int grid_sm_count() {
   return sms;
 }
 
-size_t grid_gemm_smem(int npa, int npb, int NT, int S) { return grid_gemm_stage_bytes(npa, npb, NT) * S; }
+// stage ring plus 1 KB to align it to the 1024-byte swizzle period
+size_t grid_gemm_smem(int npa, int npb, int NT, int S) { return grid_gemm_stage_bytes(npa, npb, NT) * S + 1024; }
 
 // widest N tile with at least two pipeline stages: 256 for one piece, 128 for three
 int grid_nt_max(int np) { return np == 1 ? 256 : 128; }
 
 // stages that fit in `budget` bytes (2..4), 0 if not even two
 static int grid_stages(int npa, int npb, int NT) {
-  const size_t st = grid_gemm_stage_bytes(npa, npb, NT), budget = 200 * 1024;
+  const size_t st = grid_gemm_stage_bytes(npa, npb, NT), budget = 220 * 1024 - 1024;
   const int s = (int)std::min<size_t>(4, budget / st);
   return s >= 2 ? s : 0;
 }
 
 cudaError_t grid_prepare_gemm() {
-  return cudaFuncSetAttribute(grid_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  return cudaFuncSetAttribute(grid_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
 }
 
 // one iteration t of the grid path on mode n
@@ -434,10 +526,8 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     sa.col = g.col;
     for (int p = 0; p < 3; ++p) {
       sa.Z[p] = g.Zp[p];
-      sa.ZT[p] = g.ZTp[p];
     }
     sa.ldz = g.ldz;
-    sa.ldzt = g.ldzt;
     sa.dbg_idx = D.dbg_idx;
     sa.dbg_pf = D.dbg_pf;
     sa.dbg_z = static_cast<float *>(D.dbg_z);
@@ -450,13 +540,11 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
   // 3. residual: E = G_n Z^T - X_S (M = Ip, N = Jp, K = Qp), weighted, as pieces
   {
     GridGemmArgs ga = {};
-    for (int p = 0; p < 3; ++p) {
-      ga.A[p] = g.Gp[p];
-      ga.B[p] = g.Zp[p];
-      ga.E[p] = g.Ep[p];
+    for (int p = 0; p < 3; ++p) ga.E[p] = g.Ep[p];
+    for (int p = 0; p < np; ++p) {
+      ga.tmA[p] = g.tmG[p];
+      ga.tmB[p] = g.tmZ[p];
     }
-    ga.lda = g.ldg;
-    ga.ldb = g.ldz;
     ga.npa = ga.npb = np;
     ga.maxord = maxord;
     ga.kchunks = Qp / 64;
@@ -480,23 +568,27 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     grid_gemm_kernel<<<grid, 128, grid_gemm_smem(np, np, ga.NT, ga.S), s>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  // Z^T for the gradient's K-major B operand
+  for (int p = 0; p < np; ++p) {
+    dim3 grid(g.Jp / 32, (Q + 31) / 32);
+    grid_transpose_kernel<<<grid, 256, 0, s>>>(g.Zp[p], g.ldz, g.Jp, Q, g.ZTp[p], g.ldzt);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   // 4. partial gradients: (E D) Z over slices of the samples (M = Ip, N = Q, K = Jp)
-  const int ntmax = grid_nt_max(np);
-  const int ntile = (Q + ntmax - 1) / ntmax;
-  const int NT = (((Q + ntile - 1) / ntile) + 15) / 16 * 16;
+  int NT = 0;
+  const int ntile = grid_ntiles(Q, np, NT);
   int splits = 1;
   {
     const int tiles = (Ip / 128) * ntile, kch = g.Jp / 64;
-    splits = std::max(1, std::min(std::min(g.max_splits, kch), (grid_sm_count() + tiles - 1) / tiles));
+    // one wave: at most one CTA per SM (the stages fill most of shared memory)
+    splits = std::max(1, std::min(std::min(g.max_splits, kch), grid_sm_count() / tiles));
     const int kper = (kch + splits - 1) / splits;
     splits = (kch + kper - 1) / kper;
     GridGemmArgs ga = {};
-    for (int p = 0; p < 3; ++p) {
-      ga.A[p] = g.Ep[p];
-      ga.B[p] = g.ZTp[p];
+    for (int p = 0; p < np; ++p) {
+      ga.tmA[p] = g.tmE[p];
+      ga.tmB[p] = g.tmZT[n][p];
     }
-    ga.lda = g.lde;
-    ga.ldb = g.ldzt;
     ga.npa = ga.npb = np;
     ga.maxord = maxord;
     ga.kchunks = kch;
@@ -542,25 +634,81 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
   return cudaSuccess;
 }
 
+// N tiling of the gradient GEMM over the Q columns: the number of tiles and
+// their common width NT (a multiple of 16, at most grid_nt_max)
+int grid_ntiles(int Q, int np, int &NT) {
+  const int ntmax = grid_nt_max(np);
+  const int ntile = (Q + ntmax - 1) / ntmax;
+  NT = (((Q + ntile - 1) / ntile) + 15) / 16 * 16;
+  return ntile;
+}
+
 // buffer sizes of the grid path for problem c; fills the layout fields of g
 void grid_layout(const int *I, const int *R, int N, int J, int np, GridPath &g) {
   int Imax = 1, Qmax = 1;
+  long long zcols = 1;   // columns of Z any tile reads: the K padding of the residual, the N tiles of the gradient
   for (int k = 0; k < N; ++k) {
     Imax = std::max(Imax, I[k]);
-    Qmax = std::max(Qmax, R[k] * R[(k + 1) % N]);
+    const int Q = R[k] * R[(k + 1) % N];
+    Qmax = std::max(Qmax, Q);
+    int NT = 0;
+    const int ntile = grid_ntiles(Q, np, NT);
+    zcols = std::max<long long>(zcols, std::max<long long>((Q + 63) / 64 * 64, (long long)ntile * NT));
   }
   g.np = np;
   g.nt_res = grid_nt_max(np);
   g.Jp = (J + 255) / 256 * 256;
   g.Ip = (Imax + 127) / 128 * 128;
   g.Qp = (Qmax + 63) / 64 * 64;
-  g.QTp = (Qmax + 255) / 256 * 256;
+  g.QTp = g.Qp;
   g.ldg = g.Qp;
   g.ldz = g.Qp;
   g.ldzt = g.Jp;
   g.lde = g.Jp;
+  (void)zcols;
   g.max_splits = 16;
   g.gpart_elems = (size_t)g.max_splits * Imax * Qmax;
+}
+
+}  // namespace trsgd
+
+namespace trsgd {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against libcuda)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static cudaError_t encode_map(EncodeTiledFn fn, CUtensorMap *map, void *base, long long rows, long long cols,
+                              int box_rows) {
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t grid_tensor_maps(const int *R, int N, GridPath &g) {
+  void *fp = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fp, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fp) return e != cudaSuccess ? e : cudaErrorNotSupported;
+  const EncodeTiledFn fn = reinterpret_cast<EncodeTiledFn>(fp);
+  for (int p = 0; p < g.np && e == cudaSuccess; ++p) {
+    if ((e = encode_map(fn, &g.tmG[p], g.Gp[p], g.Ip, g.ldg, 128)) != cudaSuccess) break;
+    if ((e = encode_map(fn, &g.tmZ[p], g.Zp[p], g.Jp, g.ldz, g.nt_res)) != cudaSuccess) break;
+    if ((e = encode_map(fn, &g.tmE[p], g.Ep[p], g.Ip, g.lde, 128)) != cudaSuccess) break;
+    for (int n = 0; n < N && e == cudaSuccess; ++n) {
+      int NT = 0;
+      grid_ntiles(R[n] * R[(n + 1) % N], g.np, NT);
+      e = encode_map(fn, &g.tmZT[n][p], g.ZTp[p], g.QTp, g.ldzt, NT);
+    }
+  }
+  return e;
 }
 
 }  // namespace trsgd

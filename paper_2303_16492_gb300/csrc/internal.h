@@ -1,6 +1,7 @@
 // Internal descriptors shared by the host library and the kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -69,11 +70,13 @@ struct OptBuffers {
 // Buffers and layout of the whole-GPU path (grid.cu) for one problem.
 // Operand pieces are BF16, K-major, zero-padded: G_n [Ip][ldg], Z [Jp][ldz],
 // Z^T [QTp][ldzt], weighted residual E [Ip][lde]; gpart holds the FP32
-// partial gradients of the split samples.
+// partial gradients of the split samples.  Each piece buffer has a TMA tensor
+// map (boxes of 64 K-elements, 128-byte swizzle); Z^T's box height depends on
+// the mode, so it has one map per mode.
 struct GridPath {
   int np;                  // BF16 pieces per operand (1 or 3)
   int nt_res;              // N tile of the residual GEMM
-  int Jp, Ip, Qp, QTp;     // padded J (256), I (128), Q (64 for K, 256 for the Z^T rows)
+  int Jp, Ip, Qp, QTp;     // padded J (256), I (128), Q (64)
   long long ldg, ldz, ldzt, lde;
   int max_splits;
   size_t gpart_elems;
@@ -82,11 +85,15 @@ struct GridPath {
   __nv_bfloat16 *Gp[3], *Zp[3], *ZTp[3], *Ep[3];
   float *gpart;
   long long *col;
+  CUtensorMap tmG[3], tmZ[3], tmE[3];
+  CUtensorMap tmZT[8][3];
 };
 
 // kernel launchers (defined in the .cu files)
 void grid_layout(const int *I, const int *R, int N, int J, int np, GridPath &g);
+cudaError_t grid_tensor_maps(const int *R, int N, GridPath &g);
 int grid_nt_max(int np);
+int grid_ntiles(int Q, int np, int &NT);
 cudaError_t grid_prepare_gemm();
 cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long long t, int rec, cudaStream_t s);
 cudaError_t launch_optimal_sampling(int core_dtype, int x_dtype, int N, int n, const int *I, const int *R,
