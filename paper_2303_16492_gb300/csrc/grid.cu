@@ -186,6 +186,7 @@ struct __align__(64) GridGemmArgs {
   int npa, npb, maxord;
   int kchunks, kper;       // chunks of 64 along K in total / per split (blockIdx.z)
   int NT, S;               // N tile (multiple of 16, <= 256), pipeline stages (2..4)
+  int xpre;                // residual: gather the X tile at kernel start into its own region after the stages
   int mode;                // 0: FP32 partials C[z][m][n]; 1: residual epilogue
   float *C;
   long long ldc, cstride;
@@ -243,7 +244,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(128) grid_gemm_kernel(const __grid_constant__ GridGemmArgs a) {
+constexpr int kGemmThreads = 256;   // 2 warps per TMEM lane quarter in the epilogue
+
+__global__ void __launch_bounds__(kGemmThreads) grid_gemm_kernel(const __grid_constant__ GridGemmArgs a) {
+  // scalar arguments in registers: inside the lambdas below a reference to the
+  // parameter struct would turn every field access into a generic load
+  const int npa = a.npa, npb = a.npb, maxord = a.maxord, NT = a.NT, mode = a.mode, Mv = a.Mv, Nv = a.Nv;
+  const int x_bf16 = a.x_bf16, npe = a.npe;
+  const float w = a.w;
+  float *const dbg_e = a.dbg_e;
+  float *const Cout = a.C;
+  const long long ldx = a.ldx, lde = a.lde, ldc = a.ldc, cstride = a.cstride;
+  const unsigned char *const xmode = static_cast<const unsigned char *>(a.xmode);
+  __nv_bfloat16 *const Eo[3] = {a.E[0], a.E[1], a.E[2]};
+  const CUtensorMap *const tmA = a.tmA, *const tmB = a.tmB;
+  int *const status = a.status;
   extern __shared__ unsigned char smem_raw[];
   __shared__ uint64_t full[4], empty[4];
   __shared__ uint32_t tslot;
@@ -252,10 +267,10 @@ __global__ void __launch_bounds__(128) grid_gemm_kernel(const __grid_constant__ 
   // the 128-byte swizzle repeats every 1024 bytes: align the stage ring to it
   unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * 128, n0 = blockIdx.y * a.NT;
+  const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
   const int kbeg = blockIdx.z * a.kper, kend = min(kbeg + a.kper, a.kchunks);
   const int nck = max(0, kend - kbeg);
-  const size_t stage = grid_gemm_stage_bytes(a.npa, a.npb, a.NT);
+  const size_t stage = grid_gemm_stage_bytes(npa, npb, NT);
   const int S = a.S;
   const uint32_t tx_bytes = (uint32_t)stage;
   if (tid == 0) {
@@ -268,23 +283,39 @@ __global__ void __launch_bounds__(128) grid_gemm_kernel(const __grid_constant__ 
     bad_s = 0;
   }
   if (warp == 0) tmem_alloc(&tslot, 256);
-  if (a.mode == 1)
-    for (int jl = tid; jl < a.NT; jl += 128) col_s[jl] = (n0 + jl < a.Nv) ? a.col[n0 + jl] : 0;
+  if (mode == 1)
+    for (int jl = tid; jl < NT; jl += kGemmThreads) col_s[jl] = (n0 + jl < Nv) ? a.col[n0 + jl] : 0;
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tbase = tslot;
+  // residual epilogue: the CTA's X tile (NT fibers x 128 rows, xs[jl][row]) by
+  // one burst of cp.async, either now into its own region (overlapping the
+  // main loop) or after the main loop into the freed stage memory
+  const int sx = x_bf16 ? 2 : 4;
+  unsigned char *xs = smem + (a.xpre ? (size_t)S * stage : 0);
+  auto gather_x = [&]() {
+    const int cpc = 128 * sx / 16;   // 16-byte chunks per fiber segment
+    for (int e = tid; e < NT * cpc; e += kGemmThreads) {
+      const int jl = e / cpc, ch = e - jl * cpc, j = n0 + jl;
+      const long long ms = m0 + (long long)ch * (16 / sx);
+      if (j < Nv && ms < ldx)
+        cp_async16(xs + (size_t)jl * 128 * sx + ch * 16, xmode + (col_s[jl] * ldx + ms) * sx);
+    }
+    cp_async_commit();
+  };
+  if (mode == 1 && a.xpre) gather_x();
 
   if (tid == 0 && nck > 0) {
     auto issue = [&](int c) {   // TMA copies of chunk c into stage c % S
       unsigned char *st = smem + (size_t)(c % S) * stage;
       const int k0 = (kbeg + c) * 64;
       mbar_arrive_expect_tx(&full[c % S], tx_bytes);
-      for (int pa = 0; pa < a.npa; ++pa) tma_load_2d(st + pa * 16384, &a.tmA[pa], k0, m0, &full[c % S]);
-      for (int pb = 0; pb < a.npb; ++pb)
-        tma_load_2d(st + a.npa * 16384 + pb * a.NT * 128, &a.tmB[pb], k0, n0, &full[c % S]);
+      for (int pa = 0; pa < npa; ++pa) tma_load_2d(st + pa * 16384, &tmA[pa], k0, m0, &full[c % S]);
+      for (int pb = 0; pb < npb; ++pb)
+        tma_load_2d(st + npa * 16384 + pb * NT * 128, &tmB[pb], k0, n0, &full[c % S]);
     };
-    const uint32_t idesc = umma_idesc_bf16(128, a.NT, 0, 0);
+    const uint32_t idesc = umma_idesc_bf16(128, NT, 0, 0);
     int issued = 0, last = -1;
     bool bad = false;
     for (; issued < min(S, nck); ++issued) issue(issued);
@@ -297,11 +328,11 @@ __global__ void __launch_bounds__(128) grid_gemm_kernel(const __grid_constant__ 
       const uint32_t sb = smem_u32(smem + (size_t)(c % S) * stage);
       bool first = (c == 0);
       for (int ks = 0; ks < 4; ++ks)
-        for (int pa = 0; pa < a.npa; ++pa)
-          for (int pb = 0; pb < a.npb; ++pb) {
-            if (pa + pb > a.maxord) continue;
+        for (int pa = 0; pa < npa; ++pa)
+          for (int pb = 0; pb < npb; ++pb) {
+            if (pa + pb > maxord) continue;
             const uint64_t da = umma_desc_sw128(sb + pa * 16384 + ks * 32);
-            const uint64_t db = umma_desc_sw128(sb + a.npa * 16384 + pb * a.NT * 128 + ks * 32);
+            const uint64_t db = umma_desc_sw128(sb + npa * 16384 + pb * NT * 128 + ks * 32);
             umma_bf16(tbase, da, db, idesc, !first);
             first = false;
           }
@@ -317,7 +348,7 @@ __global__ void __launch_bounds__(128) grid_gemm_kernel(const __grid_constant__ 
       }
     }
     if (bad) {   // let the copies in flight land before the CTA exits
-      latch_status(a.status, kStatusTimeout);
+      latch_status(status, kStatusTimeout);
       for (int c = last + 1; c < issued; ++c) mbar_wait_bounded(&full[c % S], (uint32_t)((c / S) & 1), kGridWaitLimit);
     }
     last_s = last;
@@ -327,63 +358,67 @@ __global__ void __launch_bounds__(128) grid_gemm_kernel(const __grid_constant__ 
   const int last = last_s;
   bool ok = !bad_s && (nck == 0 || last == nck - 1);
   if (last >= 0 && !mbar_wait_bounded(&empty[last % S], (uint32_t)((last / S) & 1), kGridWaitLimit)) {
-    latch_status(a.status, kStatusTimeout);
+    latch_status(status, kStatusTimeout);
     ok = false;
   }
   tc_fence_after();
-  // residual epilogue: the CTA's X tile (NT fibers x 128 rows) into the now
-  // free stage memory with one burst of cp.async, xs[jl][row]
-  const int sx = a.x_bf16 ? 2 : 4;
-  if (a.mode == 1) {
-    const int cpc = 128 * sx / 16;   // 16-byte chunks per fiber segment
-    for (int e = tid; e < a.NT * cpc; e += 128) {
-      const int jl = e / cpc, ch = e - jl * cpc, j = n0 + jl;
-      const long long ms = m0 + (long long)ch * (16 / sx);
-      if (j < a.Nv && ms < a.ldx)
-        cp_async16(smem + (size_t)jl * 128 * sx + ch * 16,
-                   static_cast<const unsigned char *>(a.xmode) + (col_s[jl] * a.ldx + ms) * sx);
-    }
-    cp_async_commit();
+  if (mode == 1) {
+    if (!a.xpre) gather_x();
     cp_async_wait_n<0>();
     __syncthreads();
   }
 
-  // epilogue: thread = accumulator row (TMEM lane); 32 columns per load, then 8
-  const int row = warp * 32 + lane, m = m0 + row;
-  const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
-  auto emit8 = [&](int nb, const float *v) {   // columns nb .. nb + 7 of this row
-    if (a.mode == 0) {
-      if (m < a.Mv) {
-        float *dst = a.C + (long long)blockIdx.z * a.cstride + (long long)m * a.ldc;
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (nb + u < a.Nv) dst[nb + u] = v[u];
-      }
+  // epilogue: thread = accumulator row (TMEM lane) of its lane quarter; the
+  // two warps of a quarter take alternate 32-column blocks (32 columns per
+  // TMEM load, then 8); results go to a row-major tile in shared memory (rows
+  // padded by 16 bytes: conflict-free), which whole warps then copy out row by
+  // row, so the global stores are coalesced.
+  const int quarter = warp & 3, half = warp >> 2;
+  const int row = quarter * 32 + lane, m = m0 + row;
+  const uint32_t trow = tbase + ((uint32_t)(quarter * 32) << 16);
+  const size_t xbytes = (mode == 1 && !a.xpre) ? (size_t)NT * 128 * sx : 0;   // the X tile stays below
+  unsigned char *otile = smem + (xbytes + 1023) / 1024 * 1024;
+  const int ldo_b = mode == 0 ? (NT * 4 + 16) : (NT * 2 + 16);   // bytes per staged row
+  auto emit8 = [&](int cl, const float *v) {   // tile columns cl .. cl + 7 of this row
+    if (mode == 0) {
+      float4 *dst = reinterpret_cast<float4 *>(otile + (size_t)row * ldo_b + cl * 4);
+      dst[0] = make_float4(v[0], v[1], v[2], v[3]);
+      dst[1] = make_float4(v[4], v[5], v[6], v[7]);
     } else {
+      float xv[8], ew[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {   // all loads first
+        const int xo = (cl + u) * 128 + row;
+        xv[u] = x_bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(xs)[xo])
+                       : reinterpret_cast<const float *>(xs)[xo];
+      }
+      const bool rv = m < Mv;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool valid = rv && (n0 + cl + u < Nv);
+        const float e = v[u] - xv[u];
+        ew[u] = valid ? e * w : 0.f;
+        xv[u] = e;
+      }
+      if (dbg_e)
+        for (int u = 0; u < 8; ++u)
+          if (rv && n0 + cl + u < Nv) dbg_e[(long long)(n0 + cl + u) * Mv + m] = xv[u];
       __nv_bfloat16 pe[3][8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const int j = nb + u;
-        float ew = 0.f;
-        if (m < a.Mv && j < a.Nv) {
-          const int xo = (nb - n0 + u) * 128 + row;
-          const float x = a.x_bf16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(smem)[xo])
-                                   : reinterpret_cast<const float *>(smem)[xo];
-          const float e = v[u] - x;
-          if (a.dbg_e) a.dbg_e[(long long)j * a.Mv + m] = e;
-          ew = e * a.w;
-        }
         __nv_bfloat16 p[3];
-        bf16_pieces(ew, a.npe, p);
+        bf16_pieces(ew[u], npe, p);
 #pragma unroll
         for (int pc = 0; pc < 3; ++pc) pe[pc][u] = p[pc];
       }
-      for (int pc = 0; pc < a.npe; ++pc)
-        *reinterpret_cast<uint4 *>(a.E[pc] + (long long)m * a.lde + nb) = *reinterpret_cast<const uint4 *>(pe[pc]);
+      for (int pc = 0; pc < npe; ++pc)
+        *reinterpret_cast<uint4 *>(otile + ((size_t)pc * 128 + row) * ldo_b + cl * 2) =
+            *reinterpret_cast<const uint4 *>(pe[pc]);
     }
   };
-  int cb = 0;
-  for (; cb + 32 <= a.NT; cb += 32) {
+  const int nfull = NT / 32;
+  for (int b = half; b < nfull; b += 2) {
+    const int cb = 32 * b;
     float v[32];
     if (ok && nck > 0) {
       tmem_ld32(trow + (uint32_t)cb, v);
@@ -392,9 +427,9 @@ __global__ void __launch_bounds__(128) grid_gemm_kernel(const __grid_constant__ 
       for (int u = 0; u < 32; ++u) v[u] = 0.f;
     }
 #pragma unroll
-    for (int g = 0; g < 4; ++g) emit8(n0 + cb + 8 * g, v + 8 * g);
+    for (int g = 0; g < 4; ++g) emit8(cb + 8 * g, v + 8 * g);
   }
-  for (; cb < a.NT; cb += 8) {
+  for (int cb = 32 * nfull + 8 * half; cb < NT; cb += 16) {
     float v[8];
     if (ok && nck > 0) {
       tmem_ld8(trow + (uint32_t)cb, v);
@@ -402,7 +437,26 @@ __global__ void __launch_bounds__(128) grid_gemm_kernel(const __grid_constant__ 
 #pragma unroll
       for (int u = 0; u < 8; ++u) v[u] = 0.f;
     }
-    emit8(n0 + cb, v);
+    emit8(cb, v);
+  }
+  __syncthreads();
+  if (mode == 0) {   // FP32 partials: valid rows, valid columns, one warp per row
+    const int ncols = min(NT, Nv - n0);
+    for (int r = warp; r < 128; r += kGemmThreads / 32) {
+      if (m0 + r >= Mv) break;
+      const float *src = reinterpret_cast<const float *>(otile + (size_t)r * ldo_b);
+      float *dst = Cout + (long long)blockIdx.z * cstride + (long long)(m0 + r) * ldc + n0;
+      for (int c = lane; c < ncols; c += 32) dst[c] = src[c];
+    }
+  } else {             // E pieces: whole tile rows (zeros outside the valid block), 16 bytes per lane
+    const int chunks = NT / 8;
+    for (int pc = 0; pc < npe; ++pc)
+      for (int r = warp; r < 128; r += kGemmThreads / 32) {
+        const unsigned char *src = otile + ((size_t)pc * 128 + r) * ldo_b;
+        __nv_bfloat16 *dst = Eo[pc] + (long long)(m0 + r) * lde + n0;
+        for (int c = lane; c < chunks; c += 32)
+          reinterpret_cast<uint4 *>(dst)[c] = *reinterpret_cast<const uint4 *>(src + c * 16);
+      }
   }
   tc_fence_before();
   __syncthreads();
@@ -481,6 +535,13 @@ size_t grid_gemm_smem(int npa, int npb, int NT, int S) { return grid_gemm_stage_
 // widest N tile with at least two pipeline stages: 256 for one piece, 128 for three
 int grid_nt_max(int np) { return np == 1 ? 256 : 128; }
 
+// stages (2..4) that fit beside `extra` bytes in the shared-memory budget, 0 if not even two
+static int grid_stages_budget(int npa, int npb, int NT, size_t extra) {
+  const size_t st = grid_gemm_stage_bytes(npa, npb, NT), budget = 220 * 1024 - 1024;
+  if (extra + 2 * st > budget) return 0;
+  return (int)std::min<size_t>(4, (budget - extra) / st);
+}
+
 // stages that fit in `budget` bytes (2..4), 0 if not even two
 static int grid_stages(int npa, int npb, int NT) {
   const size_t st = grid_gemm_stage_bytes(npa, npb, NT), budget = 220 * 1024 - 1024;
@@ -550,7 +611,12 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     ga.kchunks = Qp / 64;
     ga.kper = ga.kchunks;
     ga.NT = g.nt_res;
-    ga.S = grid_stages(np, np, ga.NT);
+    {   // X tile in its own region when at least three stages still fit beside it
+      const size_t xb = (size_t)ga.NT * 128 * (g.x_bf16 ? 2 : 4);
+      const int sx3 = grid_stages_budget(np, np, ga.NT, xb);
+      ga.xpre = sx3 >= 3 ? 1 : 0;
+      ga.S = ga.xpre ? sx3 : grid_stages(np, np, ga.NT);
+    }
     if (ga.S < 2) return cudaErrorInvalidConfiguration;
     ga.mode = 1;
     ga.Mv = In;
@@ -565,7 +631,7 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     ga.dbg_e = rec ? static_cast<float *>(D.dbg_e) : nullptr;
     ga.status = D.status;
     dim3 grid(Ip / 128, g.Jp / ga.NT, 1);
-    grid_gemm_kernel<<<grid, 128, grid_gemm_smem(np, np, ga.NT, ga.S), s>>>(ga);
+    grid_gemm_kernel<<<grid, kGemmThreads, grid_gemm_smem(np, np, ga.NT, ga.S) + (ga.xpre ? (size_t)ga.NT * 128 * (g.x_bf16 ? 2 : 4) : 0), s>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // Z^T for the gradient's K-major B operand
@@ -604,7 +670,7 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     ga.Nv = Q;
     ga.status = D.status;
     dim3 grid(Ip / 128, ntile, splits);
-    grid_gemm_kernel<<<grid, 128, grid_gemm_smem(np, np, NT, ga.S), s>>>(ga);
+    grid_gemm_kernel<<<grid, kGemmThreads, grid_gemm_smem(np, np, NT, ga.S), s>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // 5. update
