@@ -87,11 +87,11 @@ struct GridSampleArgs {
 };
 
 constexpr int kGridRmax = 32;
-constexpr int kGridWarps = 2;
+constexpr int kGridWarps = 4;
+constexpr int kPld = kGridRmax + 4;   // row stride of P (multiple of 4: float4 row reads)
 
 __global__ void __launch_bounds__(32 * kGridWarps) grid_samples_kernel(GridSampleArgs a) {
-  __shared__ float Pbuf[kGridWarps][2][kGridRmax][kGridRmax + 1];
-  __shared__ float Sbuf[kGridWarps][kGridRmax][kGridRmax + 1];
+  __shared__ __align__(16) float Pbuf[kGridWarps][2][kGridRmax][kPld];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = a.N, n = a.n, L = N - 1;
   int order[kMaxOrder];
@@ -112,24 +112,22 @@ __global__ void __launch_bounds__(32 * kGridWarps) grid_samples_kernel(GridSampl
     for (int s = 0; s < kMaxOrder; ++s) idx[s] = __shfl_sync(0xffffffffu, myi, s);
     if (lane == 0) {
       long long col = 0, st = 1;
-      double pf = 1.0;
       for (int s = 0; s < L; ++s) {
-        const int k = order[s];
         col += (long long)idx[s] * st;
-        st *= a.I[k];
-        pf = __dmul_rn(pf, __ddiv_rn(1.0, (double)a.I[k]));
+        st *= a.I[order[s]];
       }
       a.col[j] = col;
-      if (a.rec) {
+      if (a.rec) {   // p_F in ring order (FP64), only for the record
+        double pf = 1.0;
+        for (int s = 0; s < L; ++s) pf = __dmul_rn(pf, __ddiv_rn(1.0, (double)a.I[order[s]]));
         a.dbg_pf[j] = pf;
         for (int k = 0; k < N; ++k) a.dbg_idx[(size_t)j * N + k] = -1;
         for (int s = 0; s < L; ++s) a.dbg_idx[(size_t)j * N + order[s]] = idx[s];
       }
     }
-    // P = G_{n+1}(i) ... G_{n-1}(i): R_{n+1} x R_n, one lane per column
-    float(*P)[kGridRmax + 1] = Pbuf[warp][0];
-    float(*Pn)[kGridRmax + 1] = Pbuf[warp][1];
-    float(*S)[kGridRmax + 1] = Sbuf[warp];
+    // P = G_{n+1}(i) ... G_{n-1}(i) (R_{n+1} x R_n) in shared memory, row-major
+    float(*P)[kPld] = Pbuf[warp][0];
+    float(*Pn)[kPld] = Pbuf[warp][1];
     {
       const int k = order[0], Ra = a.R[k], Rb = a.R[(k + 1) % N];
       const float *g = a.cores[k] + (size_t)idx[0] * Ra * Rb;
@@ -138,33 +136,56 @@ __global__ void __launch_bounds__(32 * kGridWarps) grid_samples_kernel(GridSampl
     for (int s = 1; s < L; ++s) {
       const int k = order[s], Ra = a.R[k], Rb = a.R[(k + 1) % N];
       const float *g = a.cores[k] + (size_t)idx[s] * Ra * Rb;
+      // lane b keeps column b of G_k(i) in registers; rows of P are read as
+      // broadcast float4 (padded with zeros past Ra)
+      float col[kGridRmax];
+#pragma unroll
+      for (int c = 0; c < kGridRmax; ++c) col[c] = (lane < Rb && c < Ra) ? __ldcg(g + c + lane * Ra) : 0.f;
       __syncwarp();
-      for (int e = lane; e < Ra * Rb; e += 32) S[e / Ra][e % Ra] = __ldcg(g + e);   // S[b][a] = G_k(a, b)
+      for (int r = lane; r < Rn1; r += 32)
+        for (int c = Ra; c < ((Ra + 3) & ~3); ++c) P[r][c] = 0.f;
       __syncwarp();
-      if (lane < Rb) {
-        for (int r = 0; r < Rn1; ++r) {
-          float acc = 0.f;
-          for (int c = 0; c < Ra; ++c) acc = fmaf(P[r][c], S[lane][c], acc);
-          Pn[r][lane] = acc;
+      const int Ra4 = (Ra + 3) >> 2;
+      for (int r = 0; r < Rn1; ++r) {
+        const float4 *pr = reinterpret_cast<const float4 *>(P[r]);
+        float acc = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < kGridRmax / 4; ++c4) {
+          if (c4 >= Ra4) break;
+          const float4 pv = pr[c4];
+          acc = fmaf(pv.x, col[4 * c4], acc);
+          acc = fmaf(pv.y, col[4 * c4 + 1], acc);
+          acc = fmaf(pv.z, col[4 * c4 + 2], acc);
+          acc = fmaf(pv.w, col[4 * c4 + 3], acc);
         }
+        if (lane < Rb) Pn[r][lane] = acc;
       }
       __syncwarp();
-      float(*tmp)[kGridRmax + 1] = P;
+      float(*tmp)[kPld] = P;
       P = Pn;
       Pn = tmp;
     }
     __syncwarp();
     // Z(j, r + r' R_n) = P(r', r); zero the padding columns [Q, Qp)
+    int rp = lane / Rn, r = lane - (lane / Rn) * Rn;
     for (int q = lane; q < a.Qp; q += 32) {
       float v = 0.f;
       if (q < a.Q) {
-        const int rp = q / Rn, r = q - rp * Rn;
         v = P[rp][r];
         if (a.rec) a.dbg_z[(size_t)j * a.Q + q] = v;
       }
-      __nv_bfloat16 p[3];
-      bf16_pieces(v, a.np, p);
-      for (int pc = 0; pc < a.np; ++pc) a.Z[pc][(size_t)j * a.ldz + q] = p[pc];
+      if (a.np == 1) {
+        a.Z[0][(size_t)j * a.ldz + q] = __float2bfloat16_rn(v);
+      } else {
+        __nv_bfloat16 p[3];
+        bf16_pieces(v, a.np, p);
+        for (int pc = 0; pc < a.np; ++pc) a.Z[pc][(size_t)j * a.ldz + q] = p[pc];
+      }
+      r += 32;
+      while (r >= Rn) {
+        r -= Rn;
+        ++rp;
+      }
     }
   }
 }
