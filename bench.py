@@ -349,6 +349,63 @@ def run_extras(args, device):
         out.update(run_batched(args, device))
     except Exception as e:
         out["batched_error"] = repr(e)
+    try:
+        out.update(run_large(args, device))
+    except Exception as e:
+        out["c5_error"] = repr(e)
+    return out
+
+
+def run_large(args, device, target=1e-2, check=100, max_steps=4000, timed_steps=500):
+    """The large workload (N=3, 1000^3, R=20, J=4096, AdaGrad eta=0.01) on the
+    whole-GPU path: BF16 operands, and FP32 as three BF16 pieces.  Steps/s over
+    `timed_steps` iterations, then iterations and device seconds until RSE
+    (against the noiseless tensor) <= target, checked every `check`
+    iterations (evaluations not timed); effective tensor rate = the two
+    contractions' flops (2 x 2 I Q J per iteration, times 6 piece products for
+    FP32) over the iteration time."""
+    import torch
+
+    from paper_2303_16492_gb300 import _abi, api, synth
+    w = synth.workload("c5")
+    X, Xtrue, init = device_problem(w, device)
+    pk, _ = peaks()
+    out = {}
+    gemm_flops = 2 * 2.0 * w.dims[0] * w.ranks[0] * w.ranks[1] * w.J
+    for label, prec, npieces in (("bf16", _abi.BF16_MIXED, 1), ("fp32x3", _abi.FP32, 6)):
+        cores = [c.clone() for c in init]
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=prec, x_dtype=_abi.DTYPE_F32, rule=w.rule,
+                               eta=w.eta, seed=w.seed + 3)
+        s = api.Solver([pc], [X], [cores])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ms_total, it, rse, reached = 0.0, 0, None, False
+        while it < max_steps:
+            a.record()
+            s.run(it, check)
+            b.record()
+            torch.cuda.synchronize()
+            ms_total += a.elapsed_time(b)
+            it += check
+            rse = s.rel_error(0, Xtrue)
+            if rse <= target:
+                reached = True
+                break
+        a.record()
+        s.run(it, timed_steps)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / timed_steps
+        s.close()
+        out[f"c5_{label}"] = {
+            "steps_per_s": round(1e3 / ms, 1), "us_per_step": round(ms * 1e3, 2),
+            "time_to_rse": {"target": target, "iterations": it, "reached": reached, "rse": rse,
+                            "seconds": round(ms_total * 1e-3, 4)},
+            "effective_tensor_tflops": round(gemm_flops * npieces / (ms * 1e-3) / 1e12, 2),
+            "frac_of_bf16_peak": round(gemm_flops * npieces / (ms * 1e-3) / 1e12 / pk.get("bf16_tflops", 1899.3), 4)}
+    out["c5_config"] = {"dims": w.dims, "ranks": w.ranks, "J": w.J, "rule": "AdaGrad", "eta": w.eta,
+                        "path": "grid (whole GPU, tcgen05 GEMMs)", "x_storage": "bf16 copies for bf16; fp32 for fp32x3"}
+    del X, Xtrue
     return out
 
 
@@ -380,20 +437,38 @@ def run_batched(args, device, steps=2000):
 
     from paper_2303_16492_gb300 import api
     ws, pcs, Xs, Xts, inits = batched_problems(device)
-    s = api.Solver(pcs, Xs, inits)
-    shape = s.launch_shape()
-    s.run(0, 50)
     torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    s = api.Solver(pcs, Xs, inits, stream=side)
+    s.autotune(steps_per_trial=50)   # cluster size and threads per problem cluster
+    shape = s.launch_shape()
+    # one persistent launch of `chunk` iterations of all 64 problems, captured in a CUDA
+    # graph; the device-resident iteration counter advances on every replay
+    chunk = 250
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        s.step_counter(chunk)
+    s.set_counter(0)
+    with torch.cuda.stream(side):   # replays go to the current stream: keep them on the handle's
+        for _ in range(2):
+            g.replay()
+    torch.cuda.synchronize()
+    reps = max(1, steps // chunk)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    s.run(50, steps)
-    b.record()
+    with torch.cuda.stream(side):
+        a.record(side)
+        for _ in range(reps):
+            g.replay()
+        b.record(side)
     torch.cuda.synchronize()
     sec = a.elapsed_time(b) * 1e-3
+    steps = reps * chunk
     rse = [s.rel_error(p, Xts[p]) for p in range(0, len(ws), 16)]
     s.close()
     return {"c4_batched_problem_steps_per_s": round(len(ws) * steps / sec, 1),
             "c4_batched_rounds_per_s": round(steps / sec, 1), "c4_launch_shape": list(shape),
+            "c4_execution": "autotuned shape; one persistent launch of 250 iterations of all problems per CUDA-graph replay",
             "c4_rse_sample": [float(f"{r:.3e}") for r in rse]}
 
 

@@ -113,9 +113,9 @@ def workload(name: str) -> Workload:
     if name == "c3":   # 40^5 FP32, R=8, Gaussian cores N(0, 1/8)
         return Workload("c3", [40] * 5, [8] * 5, 2048, "gaussian", 1 / math.sqrt(8),
                         noise_rel=1e-3, alpha=2.5, prec=1)
-    if name == "c5":   # 1000^3 BF16 storage, R=20, scaled + AdaGrad
+    if name == "c5":   # 1000^3 BF16 storage, R=20, AdaGrad (whole-GPU path: plain direction)
         return Workload("c5", [1000] * 3, [20] * 3, 4096, "illcond", smin=1e-2,
-                        noise_rel=1e-3, variant=1, rule=1, eta=1e-3, damping=1e-6, prec=2)
+                        noise_rel=1e-3, variant=0, rule=1, eta=1e-2, prec=2)
     raise KeyError(name)
 
 
