@@ -31,6 +31,16 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "TR-SGD steps/s & time to rel. error 1e-3 (FP32 vs BF16 vs batched), %roofline"
+WORKLOAD_DESC = {
+    "c1": "N=3 20^3 FP64, R=3, Gaussian planted cores, noise 1e-3, |F|=50, uniform, fixed step",
+    "c2": "N=4 100^4 FP32, R=10, ill-conditioned planted cores, noise 1e-4, |F|=1000, uniform sampling, "
+          "plain TR-BRSGD, fixed step",
+    "c3": "N=5 40^5 FP32, R=8, Gaussian planted cores, noise 1e-3, |F|=2048, uniform, fixed step",
+    "c5": "N=3 1000^3, R=20, ill-conditioned planted cores, noise 1e-3, |F|=4096, BF16 operands, AdaGrad, "
+          "whole-GPU path",
+    "c5p": "profiling size of c5: 1000x400x400, R=20, |F|=4096, BF16 operands, AdaGrad, whole-GPU path",
+}
+DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16 operands, f32 accumulate"}
 UNIT = "steps/s"
 L2_BYTES = 129 * 2**20
 
@@ -171,7 +181,8 @@ def run_ours(args):
     device = torch.device("cuda", local)
     w = synth.workload(args.workload)
     X, Xtrue, init = device_problem(w, device, seed_offset=rank)
-    pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=w.prec, alpha=w.alpha, seed=w.seed + 3)
+    pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=w.prec, alpha=w.alpha, rule=w.rule, eta=w.eta,
+                           seed=w.seed + 3)
     stream = torch.cuda.current_stream()
     solver = api.Solver([pc], [X], [init], stream=stream)
     if args.autotune:
@@ -197,28 +208,40 @@ def run_ours(args):
     if world > 1:
         ms = max_over_ranks(ms, device)
     rse = solver.rel_error(0, Xtrue)
+    x_mb = X.numel() * X.element_size() / 1e6
     value = job_throughput(world, args.steps, ms)
     ms_per_step = ms / args.steps
 
-    # roofline of the dominant kernel (the fused step kernel; it is the only kernel in the timed region)
+    # roofline of the dominant kernel: the fused step kernel (the only launch in the timed
+    # region) on the cluster path, the tcgen05 GEMMs on the whole-GPU path
     pk, pk_kind = peaks()
     by, fl = algorithmic_per_step(w)
     sm_mhz = pk.get("sm_max_mhz", 2070.0)
-    alu_peak = fp32_alu_peak_tflops(sm_mhz)
-    achieved_tflops = fl / (ms_per_step * 1e-3) / 1e12
-    rmax = next(r for r in (4, 8, 12, 16) if r >= max(w.ranks))
-    kernel = f"step_cluster_kernel<float,float,{rmax}>"
-    # DRAM read+write per step of this kernel on this workload, from one ncu capture
-    # (a 200-step launch; the per-step figure is scaled to the timed launch)
-    traffic_step = MEASURED_TRAFFIC_PER_STEP.get((args.workload, kernel))
-    roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(alu_peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved_tflops / alu_peak, 5),
-                "traffic": None if traffic_step is None else int(traffic_step * args.steps),
-                "traffic_per_step": traffic_step,
-                "kernel": kernel,
-                "peak_note": f"FP32 FMA unit count x {sm_mhz:.0f} MHz (derived; {pk_kind} clock)",
-                "hbm_frac": round(by / (ms_per_step * 1e-3) / 1e9 / pk.get("hbm_gbs", 6652.0), 5),
-                "algorithmic_bytes_per_step": int(by), "algorithmic_flops_per_step": int(fl)}
+    if cluster == 0:
+        npieces = 1 if w.prec == 2 else 6
+        gemm_fl = sum(4.0 * w.dims[n] * w.ranks[n] * w.ranks[(n + 1) % len(w.dims)] * w.J
+                      for n in range(len(w.dims))) / len(w.dims) * npieces
+        achieved = gemm_fl / (ms_per_step * 1e-3) / 1e12
+        roofline = {"bound": "tensor", "achieved": round(achieved, 3), "peak": pk.get("bf16_tflops", 1899.3),
+                    "unit": "TFLOP/s", "frac": round(achieved / pk.get("bf16_tflops", 1899.3), 5), "traffic": None,
+                    "kernel": "grid_gemm_kernel (residual + gradient), whole iteration time",
+                    "peak_note": f"dense BF16, {pk_kind} burst", "algorithmic_flops_per_step": int(gemm_fl)}
+    else:
+        alu_peak = fp32_alu_peak_tflops(sm_mhz)
+        achieved_tflops = fl / (ms_per_step * 1e-3) / 1e12
+        rmax = next(r for r in (4, 8, 12, 16) if r >= max(w.ranks))
+        kernel = f"step_cluster_kernel<float,float,{rmax}>"
+        # DRAM read+write per step of this kernel on this workload, from one ncu capture
+        # (a 200-step launch; the per-step figure is scaled to the timed launch)
+        traffic_step = MEASURED_TRAFFIC_PER_STEP.get((args.workload, kernel))
+        roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(alu_peak, 2),
+                    "unit": "TFLOP/s", "frac": round(achieved_tflops / alu_peak, 5),
+                    "traffic": None if traffic_step is None else int(traffic_step * args.steps),
+                    "traffic_per_step": traffic_step,
+                    "kernel": kernel,
+                    "peak_note": f"FP32 FMA unit count x {sm_mhz:.0f} MHz (derived; {pk_kind} clock)",
+                    "hbm_frac": round(by / (ms_per_step * 1e-3) / 1e9 / pk.get("hbm_gbs", 6652.0), 5),
+                    "algorithmic_bytes_per_step": int(by), "algorithmic_flops_per_step": int(fl)}
 
     e2e = run_e2e(args, w, solver, X, init, device) if rank == 0 and not args.no_e2e else None
     ttr = time_to_rse(args, w, device, ms_per_step) if rank == 0 and args.time_to_rse else None
@@ -227,14 +250,13 @@ def run_ours(args):
     if rank == 0:
         out = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": round(ms_per_step, 6), "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": f"{args.workload}: N=4 100^4 FP32, R=10, ill-conditioned planted cores, "
-                                      "noise 1e-4, |F|=1000, uniform sampling, plain TR-BRSGD, fixed step",
+               "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME.get(w.prec, "f32"), "data": "synthetic",
+               "config": {"workload": f"{args.workload}: {WORKLOAD_DESC.get(args.workload, '')}",
                           "dims": w.dims, "ranks": w.ranks, "J": w.J, "alpha": w.alpha,
                           "parallelism": f"replicas x{world}" if world > 1 else "single problem",
                           "launch": {"cluster_ctas": cluster, "threads": threads, "steps_per_launch": args.steps},
-                          "l2": "inputs larger than L2 (X 400 MB, mode-major copies 1.6 GB; fibers sampled "
-                                "at random each step; the 160 KB of cores stay resident as the iterate)"},
+                          "l2": f"inputs larger than L2 (X {x_mb:.0f} MB and its {len(w.dims)} mode-major copies; "
+                                "fibers sampled at random each step; the cores stay resident as the iterate)"},
                "rse_after": rse, "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
                "e2e": e2e, "cpu_baseline": cpu, "time_to_rse": ttr, "extras": extras}
         print(json.dumps(out), flush=True)

@@ -257,7 +257,7 @@ trsgd_status trsgd_adagrad_state(trsgd_handle *h, int32_t problem, int32_t core,
  * these values (validated; 0 keeps the current one).  trsgd_autotune times
  * the candidate shapes on scratch copies of the cores and keeps the fastest
  * (synchronising; the cores are left unchanged).  On the whole-GPU path the
- * query returns cluster 0 and threads 128, setting returns EUNSUPPORTED and
+ * query returns cluster 0 and threads 256, setting returns EUNSUPPORTED and
  * trsgd_autotune does nothing. */
 trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster,
                                 int32_t *threads);

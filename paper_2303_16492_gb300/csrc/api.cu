@@ -755,10 +755,10 @@ static bool threads_fit(const trsgd_handle &h, int T) {
 
 trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster, int32_t *threads) {
   if (!h || !cluster || !threads) return TRSGD_EINVAL;
-  if (h->grid) {   // whole-GPU path: no cluster; 128-thread GEMM CTAs
+  if (h->grid) {   // whole-GPU path: no cluster; 256-thread GEMM CTAs
     if (set != 0) return TRSGD_EUNSUPPORTED;
     *cluster = 0;
-    *threads = 128;
+    *threads = 256;
     return TRSGD_OK;
   }
   if (set == 0) {

@@ -116,6 +116,10 @@ def workload(name: str) -> Workload:
     if name == "c5":   # 1000^3 BF16 storage, R=20, AdaGrad (whole-GPU path: plain direction)
         return Workload("c5", [1000] * 3, [20] * 3, 4096, "illcond", smin=1e-2,
                         noise_rel=1e-3, variant=0, rule=1, eta=1e-2, prec=2)
+    if name == "c5p":  # profiling size of the large workload: its mode-1 contractions (I_1 = 1000,
+        # R = 20, J = 4096) on a 1000 x 400 x 400 tensor that a full counter capture can hold
+        return Workload("c5p", [1000, 400, 400], [20] * 3, 4096, "illcond", smin=1e-2,
+                        noise_rel=1e-3, variant=0, rule=1, eta=1e-2, prec=2)
     raise KeyError(name)
 
 

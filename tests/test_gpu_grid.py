@@ -70,7 +70,7 @@ def _check(case, rec, bf16):
 @pytest.mark.parametrize("bf16", [True, False], ids=["bf16", "fp32x3"])
 def test_grid_single_steps(shape, bf16):
     case = _grid_case(shape, bf16)
-    assert case.solver.launch_shape() == (0, 128)
+    assert case.solver.launch_shape() == (0, 256)
     for t in range(4):
         for k, G in enumerate(case.device_cores()):
             case.state.cores[k] = G
@@ -101,7 +101,7 @@ def test_grid_is_chosen_for_large_ranks_and_follows_the_oracle():
     resynchronising stay within 1e-4 of the oracle's trajectory."""
     A = api()
     case = Case(dims=[60, 50, 40], ranks=[20, 12, 16], J=400, prec=1, alpha=0.05)
-    assert case.solver.launch_shape() == (0, 128)
+    assert case.solver.launch_shape() == (0, 256)
     with pytest.raises(A._abi.TrsgdError):
         case.solver.step_counter(1)
     for t in range(30):
