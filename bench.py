@@ -372,9 +372,55 @@ def run_extras(args, device):
     except Exception as e:
         out["batched_error"] = repr(e)
     try:
+        out.update(run_c3(args, device))
+    except Exception as e:
+        out["c3_error"] = repr(e)
+    try:
         out.update(run_large(args, device))
     except Exception as e:
         out["c5_error"] = repr(e)
+    return out
+
+
+def run_c3(args, device):
+    """The c3 workload (N=5, 40^5, R=8, |F|=2048) with each of the four
+    distributions (steps/s and RSE after the timed iterations), and the
+    sampled-loss adjoint of all five cores (launches/s)."""
+    import torch
+
+    from paper_2303_16492_gb300 import api, synth
+    w = synth.workload("c3")
+    X, Xtrue, init = device_problem(w, device)
+    out = {}
+    for name, dist, steps in (("uniform", 0, 3000), ("leverage", 1, 1000), ("euclidean", 2, 1000),
+                              ("optimal", 3, 40)):
+        cores = [c.clone() for c in init]
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, dist=dist, seed=w.seed + 3)
+        s = api.Solver([pc], [X], [cores])
+        s.run(0, max(10, steps // 10))
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        s.run(10**5, steps)
+        b.record()
+        torch.cuda.synchronize()
+        out[f"c3_{name}_steps_per_s"] = round(steps / (a.elapsed_time(b) * 1e-3), 1)
+        s.close()
+    # adjoint of the sampled loss for all cores at |F| = 2048
+    n = 2
+    idx = torch.randint(0, w.dims[0], (w.J, 5), device=device, dtype=torch.int32)
+    XS = torch.randn(w.J, w.dims[n], device=device)
+    wt = torch.ones(w.J, device=device)
+    api.sampled_loss_grad(init, w.dims, w.ranks, n, idx, XS, wt)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(200):
+        api.sampled_loss_grad(init, w.dims, w.ranks, n, idx, XS, wt)
+    b.record()
+    torch.cuda.synchronize()
+    out["c3_adjoint_all_cores_per_s"] = round(200 / (a.elapsed_time(b) * 1e-3), 1)
+    del X, Xtrue
     return out
 
 

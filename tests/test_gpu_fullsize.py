@@ -146,3 +146,88 @@ def test_large_size_grid_path_steps(bf16):
             else:
                 assert rel(dev, ora) < tol_c
     s.close()
+
+
+def _c3_problem(A):
+    """The c3 workload (N=5, 40^5, R=8, |F|=2048, Gaussian cores N(0, 1/8),
+    noise 1e-3): device X by the library's reconstruction plus seeded device
+    noise; the oracle's X evaluated fiber by fiber from the planted cores."""
+    from paper_2303_16492_gb300 import synth
+    w = synth.workload("c3")
+    planted = synth.planted_cores(w)
+    P = to_oracle_cores(planted, w.ranks)
+    rng = np.random.default_rng(0)
+    ent = [tr.tr_entry(P, [int(rng.integers(0, d)) for d in w.dims]) for _ in range(2000)]
+    sigma = w.noise_rel * float(np.sqrt(np.mean(np.square(ent))))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w.seed + 1)
+    noise_d = torch.randn(int(np.prod(w.dims)), generator=gen, device="cuda", dtype=torch.float32)
+    Xo = LazyTensor(P, w.dims, lambda pos: noise_d[torch.from_numpy(pos).cuda()].double().cpu().numpy(), sigma)
+    Xd = A.reconstruct([torch.from_numpy(G).to("cuda", torch.float32) for G in planted], w.dims, w.ranks)
+    Xd.add_(noise_d, alpha=sigma)
+    init = [G.astype(np.float32) for G in synth.initial_cores(w, float(torch.linalg.vector_norm(Xd.double()) ** 2))]
+    return w, P, Xo, Xd, init
+
+
+@pytest.mark.parametrize("dist", [ob.DIST_UNIFORM, ob.DIST_LEVERAGE, ob.DIST_EUCLIDEAN],
+                         ids=["uniform", "leverage", "euclidean"])
+def test_c3_size_distributions(dist):
+    """N=5, 40^5, R=8, |F|=2048 with three of the four distributions, two
+    iterations each: indices bit-exact and p_F bit-exact for the uniform and
+    Euclidean tables (built from the same cores on both sides); at I_k = 40 <
+    R^2 = 64 leverage is exactly uniform, 1/I_k on the device and to 1e-15
+    from the oracle's SVD; every intermediate within the FP32 tolerance.  The
+    optimal distribution needs the full residual on the oracle side (10^8
+    entries per iteration) and is checked at the smaller sizes of
+    test_gpu_step."""
+    A = api()
+    w, P, Xo, Xd, init = _c3_problem(A)
+    cores_d = [torch.from_numpy(G).cuda() for G in init]
+    pc = A.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, dist=dist, seed=w.seed + 3)
+    s = A.Solver([pc], [Xd], [cores_d])
+    s.set_debug(True)
+    N, J, Q = 5, w.J, 64
+    st = ob.State.new(to_oracle_cores([G.astype(np.float64) for G in init], w.ranks))
+    cfg = ob.Config(J=w.J, alpha=w.alpha, dist=dist, seed=w.seed + 3)
+    for t in range(2):
+        for k in range(N):
+            st.cores[k] = tr.fold2(cores_d[k].double().cpu().numpy(), w.ranks[k], w.ranks[(k + 1) % N])
+        rec = ob.step(st, Xo, cfg, t)
+        s.step(t)
+        n, In = rec["n"], w.dims[rec["n"]]
+        np.testing.assert_array_equal(s.get_debug(A._abi.DBG_IDX, np.int32, J * N).reshape(J, N), rec["idx"])
+        pf = s.get_debug(A._abi.DBG_PF, np.float64, J)
+        if dist == ob.DIST_LEVERAGE:   # exactly 1/I_k on the device, 1/I_k to rounding from the oracle's SVD
+            np.testing.assert_allclose(pf, rec["pF"], rtol=1e-12)
+        else:
+            np.testing.assert_array_equal(pf, rec["pF"])
+        assert rel(s.get_debug(A._abi.DBG_Z, np.float32, J * Q).reshape(J, Q), rec["Z"]) < 2e-5
+        assert rel(s.get_debug(A._abi.DBG_E, np.float32, J * In).reshape(J, In).T, rec["E"]) < 2e-5
+        assert rel(s.get_debug(A._abi.DBG_G, np.float32, In * Q).reshape(In, Q), rec["g"]) < 2e-5
+        for k in range(N):
+            assert rel(cores_d[k].double().cpu().numpy(), tr.unfold2(st.cores[k])) < 2e-5
+    s.close()
+
+
+def test_c3_size_adjoint():
+    """The hand-written adjoint of the sampled loss for all five cores at the
+    c3 size (|F| = 2048 samples of mode n, 40^5, R = 8) against the oracle's
+    product-rule gradient (pinned by central differences at small sizes)."""
+    A = api()
+    from paper_2303_16492_gb300 import synth
+    w = synth.workload("c3")
+    cores = [G.astype(np.float32).astype(np.float64) for G in to_oracle_cores(synth.planted_cores(w), w.ranks)]
+    n = 2
+    idx = ob.draw_indices(11, 5, n, w.J, w.dims, None)
+    XS = np.random.default_rng(3).standard_normal((w.dims[n], w.J)).astype(np.float32).astype(np.float64)
+    wt = np.random.default_rng(4).uniform(0.5, 1.5, w.J).astype(np.float32).astype(np.float64)
+    loss = ob.sampled_loss(cores, n, idx, XS, wt)
+    grads = ob.sampled_loss_grads(cores, n, idx, XS, wt)
+    cd = [torch.from_numpy(tr.unfold2(G)).to("cuda", torch.float32) for G in cores]
+    idx_d = torch.from_numpy(np.where(idx < 0, 0, idx).astype(np.int32)).cuda()
+    XS_d = torch.from_numpy(np.ascontiguousarray(XS.T).astype(np.float32)).cuda()
+    w_d = torch.from_numpy(wt.astype(np.float32)).cuda()
+    lg, gg = A.sampled_loss_grad(cd, w.dims, w.ranks, n, idx_d, XS_d, w_d)
+    assert abs(float(lg.item()) - loss) < 1e-5 * abs(loss)
+    for k in range(5):
+        assert rel(gg[k].double().cpu().numpy(), tr.unfold2(grads[k])) < 3e-5
