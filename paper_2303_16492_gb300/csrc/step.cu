@@ -60,42 +60,44 @@ __device__ __forceinline__ T dotk(const T *p, const T *s) {
 }
 
 // One factor of the batched slice chain for a uniform rank RU: P_{q+1} =
-// P_q S_q for the samples jl = warp, warp + nwarps, ... of this CTA, lane l
-// computing entries l, l + 32, ... (row-major [r'][b]).  All of a lane's
-// dot products are issued together (independent FMA chains); rows past the
-// last entry are computed from clamped addresses and not stored.
+// P_q S_q (row-major [r'][b] per sample; the first P is the staged slice,
+// column-major).  32 / RU samples per warp, lane = (sample slot, output
+// column b): the column b of the sample's slice stays in registers and each
+// row of P is read once per group of RU lanes (a broadcast within the group).
 template <int RU, bool FIRST, typename T>
 __device__ __noinline__ void chain_factor_uniform(const T *src, int sstride, const T *sfac, int qpad, T *dst,
                                                   int dstride, int jb) {
-  constexpr int PER = RU * RU, NU = (PER + 31) / 32;
+  constexpr int G = 32 / RU;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  int po[NU], so[NU], dof[NU];
-  bool ok[NU];
+  const int g = lane / RU, b = lane - g * RU;
+  const bool lane_ok = g < G;
+  for (int j0 = warp * G; j0 < jb; j0 += nwarps * G) {
+    const int jl = j0 + g;
+    const bool ok = lane_ok && jl < jb;
+    const int jc = ok ? jl : 0;
+    const T *prow = src + (size_t)jc * sstride;
+    const T *S = sfac + (size_t)jc * qpad + (lane_ok ? b : 0) * RU;
+    T col[RU];
 #pragma unroll
-  for (int u = 0; u < NU; ++u) {
-    const int it0 = lane + 32 * u;
-    ok[u] = it0 < PER;
-    const int it = ok[u] ? it0 : PER - 1;
-    const int rp = it / RU, b = it - rp * RU;
-    po[u] = FIRST ? rp : rp * RU;
-    so[u] = b * RU;
-    dof[u] = it;
-  }
-  for (int jl = warp; jl < jb; jl += nwarps) {
-    const T *prow = src + (size_t)jl * sstride;
-    const T *S = sfac + (size_t)jl * qpad;
-    T acc[NU];
+    for (int a = 0; a < RU; ++a) col[a] = S[a];
+    T *drow = dst + (size_t)jc * dstride;
+#pragma unroll 2
+    for (int r = 0; r < RU; ++r) {
+      T acc = T(0);
+      if constexpr (!FIRST && (RU % 2 == 0) && sizeof(T) == 4) {
+        const float2 *pr = reinterpret_cast<const float2 *>(prow + r * RU);
 #pragma unroll
-    for (int u = 0; u < NU; ++u) acc[u] = T(0);
+        for (int a2 = 0; a2 < RU / 2; ++a2) {
+          const float2 v = pr[a2];
+          acc = fma(v.x, col[2 * a2], acc);
+          acc = fma(v.y, col[2 * a2 + 1], acc);
+        }
+      } else {
 #pragma unroll
-    for (int a = 0; a < RU; ++a) {
-#pragma unroll
-      for (int u = 0; u < NU; ++u) acc[u] = fma(prow[po[u] + a * (FIRST ? RU : 1)], S[so[u] + a], acc[u]);
+        for (int a = 0; a < RU; ++a) acc = fma(prow[FIRST ? r + a * RU : r * RU + a], col[a], acc);
+      }
+      if (ok) drow[r * RU + b] = acc;
     }
-    T *drow = dst + (size_t)jl * dstride;
-#pragma unroll
-    for (int u = 0; u < NU; ++u)
-      if (ok[u]) drow[dof[u]] = acc[u];
   }
 }
 
