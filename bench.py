@@ -130,7 +130,7 @@ def device_problem(w, device, seed_offset=0):
 
 # dram__bytes_read.sum + dram__bytes_write.sum per step, from the ncu capture
 # summarised in profiles/step_cluster_kernel_c2_fp32.md (101.80 MB over 200 steps)
-MEASURED_TRAFFIC_PER_STEP = {("c2", "step_cluster_kernel<float,float,12>"): 509019}
+MEASURED_TRAFFIC_PER_STEP = {}
 
 
 def algorithmic_per_step(w):
@@ -230,7 +230,8 @@ def run_ours(args):
         alu_peak = fp32_alu_peak_tflops(sm_mhz)
         achieved_tflops = fl / (ms_per_step * 1e-3) / 1e12
         rmax = next(r for r in (4, 8, 12, 16) if r >= max(w.ranks))
-        kernel = f"step_cluster_kernel<float,float,{rmax}>"
+        pieces = solver.tensor_pieces()
+        kernel = f"step_cluster_kernel<float,float,{rmax},{pieces}>"
         # DRAM read+write per step of this kernel on this workload, from one ncu capture
         # (a 200-step launch; the per-step figure is scaled to the timed launch)
         traffic_step = MEASURED_TRAFFIC_PER_STEP.get((args.workload, kernel))
@@ -239,7 +240,9 @@ def run_ours(args):
                     "traffic": None if traffic_step is None else int(traffic_step * args.steps),
                     "traffic_per_step": traffic_step,
                     "kernel": kernel,
-                    "peak_note": f"FP32 FMA unit count x {sm_mhz:.0f} MHz (derived; {pk_kind} clock)",
+                    "peak_note": f"FP32 FMA unit count x {sm_mhz:.0f} MHz (derived; {pk_kind} clock)"
+                                 + ("; the two contractions run on the tensor cores as three BF16 pieces per "
+                                    "operand, the rest of the step on the FP32 pipes" if pieces == 3 else ""),
                     "hbm_frac": round(by / (ms_per_step * 1e-3) / 1e9 / pk.get("hbm_gbs", 6652.0), 5),
                     "algorithmic_bytes_per_step": int(by), "algorithmic_flops_per_step": int(fl)}
 
@@ -353,6 +356,14 @@ def run_extras(args, device):
         s = api.Solver([pc], [X], [initb])
         out["c2_bf16_mixed_tensor_core_steps_per_s"] = round(timed(s, 20000), 1)
         out["c2_bf16_mixed_rse_after"] = s.rel_error(0, Xtrue)
+        s.close()
+        # FP32 contractions on the FMA units instead of three BF16 pieces on the tensor cores
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, seed=w.seed + 3,
+                               fp32_units=api._abi.FP32_FMA)
+        initf = [c.clone() for c in init]
+        s = api.Solver([pc], [X], [initf])
+        out["c2_fp32_fma_units_steps_per_s"] = round(timed(s, 20000), 1)
+        out["c2_fp32_fma_units_rse_after"] = s.rel_error(0, Xtrue)
         s.close()
         pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=0.5, variant=1, damping=1e-9,
                                seed=w.seed + 3)

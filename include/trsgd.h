@@ -69,7 +69,8 @@ typedef enum { TRSGD_PLAIN = 0, TRSGD_SCALED = 1 } trsgd_variant;
 typedef enum { TRSGD_STEP_FIXED = 0, TRSGD_STEP_ADAGRAD = 1 } trsgd_steprule;
 
 /* Arithmetic of the step.  FP64: cores, X and all arithmetic in double.
- * FP32: cores and X in float, FP32 arithmetic.  BF16_MIXED: cores in float,
+ * FP32: cores and X in float, FP32 arithmetic (the two contractions: see
+ * trsgd_fp32_units).  BF16_MIXED: cores in float,
  * the sampled fibers stored in bfloat16, tensor-core contractions with FP32
  * accumulation.  The scaled variant's Gram matrix is reduced, factorised and
  * applied in FP64 for FP64 cores and in double-float arithmetic (a float
@@ -91,6 +92,23 @@ typedef enum { TRSGD_DTYPE_F64 = 0, TRSGD_DTYPE_F32 = 1, TRSGD_DTYPE_BF16 = 2 } 
  * AUTO: CLUSTER when the problem fits it, else GRID. */
 typedef enum { TRSGD_PATH_AUTO = 0, TRSGD_PATH_CLUSTER = 1, TRSGD_PATH_GRID = 2 } trsgd_path;
 
+/* Units of the FP32 mode's two contractions, the residual G_n Z^T and the
+ * gradient (E D) Z of Eq. S_gradient.
+ * PIECES: the tensor cores (tcgen05, FP32 accumulation in tensor memory),
+ *   every operand held as three BF16 pieces that sum to its FP32 value (each
+ *   piece the rounding of what the previous ones left) and the six piece
+ *   products of total order <= 2 accumulated: a dropped product is below
+ *   2^-23 of the term, about one FP32 rounding.  The cluster path takes it
+ *   when its shared-memory layout holds the pieces (R_n R_{n+1} and the
+ *   samples per CTA <= 256, one chunk of 128 rows of G_n at a time), else
+ *   the FMA units.  The grid path always uses it.
+ * FMA: the FP32 FMA units only (cluster path; the grid path is then not
+ *   taken, TRSGD_EUNSUPPORTED if requested).
+ * The other modes ignore the field (FP64: FMA units; BF16_MIXED: two pieces
+ * for the residual, one for the gradient) but it must hold one of the two
+ * values. */
+typedef enum { TRSGD_FP32_PIECES = 0, TRSGD_FP32_FMA = 1 } trsgd_fp32_units;
+
 /* One TR problem (Algorithm 3's arguments plus the stopping-free part of the
  * configuration). */
 typedef struct {
@@ -109,7 +127,7 @@ typedef struct {
   double damping;                  /* eta^t of the damped preconditioner     */
   uint64_t seed;                   /* Philox key of this problem             */
   int32_t path;                    /* trsgd_path                             */
-  int32_t reserved;                /* must be 0                              */
+  int32_t fp32_units;              /* trsgd_fp32_units, FP32 mode            */
 } trsgd_config;
 
 typedef struct trsgd_handle trsgd_handle;
@@ -267,6 +285,14 @@ trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial);
  * kernel counts once per launch of any number of iterations; the whole-GPU
  * path launches five kernels per iteration). */
 int64_t trsgd_launch_count(const trsgd_handle *h);
+
+/* BF16 pieces per tensor-core operand of the residual and gradient
+ * contractions in the handle's current launch shape: 0 = the FMA units (FP64;
+ * FP32 with TRSGD_FP32_FMA or where the pieces do not fit the cluster's shared
+ * memory), 3 = FP32 on pieces (either path), 2 = the cluster path's
+ * BF16-mixed mode, 1 = the whole-GPU path's BF16-mixed mode.  -1 for a null
+ * handle.  Pure host query. */
+int32_t trsgd_tensor_pieces(const trsgd_handle *h);
 
 void trsgd_destroy(trsgd_handle *h);
 const char *trsgd_status_string(trsgd_status s);

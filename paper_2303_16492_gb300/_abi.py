@@ -16,6 +16,7 @@ STEP_FIXED, STEP_ADAGRAD = 0, 1
 FP64, FP32, BF16_MIXED = 0, 1, 2
 DTYPE_F64, DTYPE_F32, DTYPE_BF16 = 0, 1, 2
 PATH_AUTO, PATH_CLUSTER, PATH_GRID = 0, 1, 2
+FP32_PIECES, FP32_FMA = 0, 1
 DBG_MODE, DBG_IDX, DBG_PF, DBG_Z, DBG_E, DBG_G, DBG_P, DBG_H = range(8)
 
 
@@ -38,7 +39,7 @@ class Config(ctypes.Structure):
         ("damping", ctypes.c_double),
         ("seed", ctypes.c_uint64),
         ("path", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("fp32_units", ctypes.c_int32),
     ]
 
 
@@ -83,6 +84,7 @@ _SIGNATURES = {
                                           ctypes.POINTER(ctypes.c_int32)]),
     "trsgd_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "trsgd_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "trsgd_tensor_pieces": (ctypes.c_int32, [ctypes.c_void_p]),
     "trsgd_destroy": (None, [ctypes.c_void_p]),
     "trsgd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -35,6 +35,7 @@ class ProblemConfig:
     seed: int = 0
     x_dtype: int | None = None
     path: int = _abi.PATH_AUTO
+    fp32_units: int = _abi.FP32_PIECES
 
     def to_c(self) -> _abi.Config:
         c = _abi.Config()
@@ -57,6 +58,7 @@ class ProblemConfig:
         c.damping = self.damping
         c.seed = int(self.seed)
         c.path = int(self.path)
+        c.fp32_units = int(self.fp32_units)
         return c
 
 
@@ -150,6 +152,10 @@ class Solver:
 
     def launch_count(self) -> int:
         return int(_abi.lib().trsgd_launch_count(self._h))
+
+    def tensor_pieces(self) -> int:
+        """BF16 pieces per tensor-core operand of the two contractions (0: FMA units)."""
+        return int(_abi.lib().trsgd_tensor_pieces(self._h))
 
     def close(self):
         if getattr(self, "_h", None):

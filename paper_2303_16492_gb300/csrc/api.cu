@@ -50,6 +50,7 @@ struct trsgd_handle {
   std::vector<trsgd_config> cfg;
   cudaStream_t stream = nullptr;
   int core_dtype = 1, xc_dtype = 1, rmax = 4;
+  int fp32_pieces = 1;   // FP32 contractions on the tensor cores as three BF16 pieces when they fit
   std::vector<ProbDesc> hdesc;
   ProbDesc *ddesc = nullptr;
   Buffers buf;
@@ -91,6 +92,7 @@ static bool grid_fits(const trsgd_config *cfg, int32_t np) {
   if (np != 1) return false;
   const trsgd_config &c = cfg[0];
   if (c.dist != TRSGD_DIST_UNIFORM || c.variant != TRSGD_PLAIN || c.prec == TRSGD_FP64) return false;
+  if (c.prec == TRSGD_FP32 && c.fp32_units == TRSGD_FP32_FMA) return false;   // pieces only
   if (c.J > (1LL << 24)) return false;
   for (int k = 0; k < c.N; ++k) {
     if (c.R[k] > 32 || c.R[k] * c.R[(k + 1) % c.N] > 512) return false;
@@ -123,7 +125,9 @@ static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
     if (c.prec == TRSGD_FP64 && c.x_dtype != TRSGD_DTYPE_F64) return TRSGD_EINVAL;
     if (c.prec == TRSGD_FP32 && c.x_dtype != TRSGD_DTYPE_F32) return TRSGD_EINVAL;
     if (c.prec == TRSGD_BF16_MIXED && c.x_dtype == TRSGD_DTYPE_F64) return TRSGD_EINVAL;
-    if (c.path < TRSGD_PATH_AUTO || c.path > TRSGD_PATH_GRID || c.path != cfg[0].path || c.reserved != 0)
+    if (c.path < TRSGD_PATH_AUTO || c.path > TRSGD_PATH_GRID || c.path != cfg[0].path)
+      return TRSGD_EINVAL;
+    if ((c.fp32_units != TRSGD_FP32_PIECES && c.fp32_units != TRSGD_FP32_FMA) || c.fp32_units != cfg[0].fp32_units)
       return TRSGD_EINVAL;
   }
   // this build
@@ -139,7 +143,7 @@ static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
 // Z and Z^T.  Tail region [off_reg, total): G_n chunk / partial gradient
 // (reg), the FP64 Gram (scaled), the owned rows; the staged slices of the
 // chain and the CDF scratch alias the same tail.
-static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
+static bool make_layout_p(const trsgd_handle &h, int C, int tcp, StepLayout &L) {
   const size_t st = h.core_dtype == 0 ? 8 : 4;
   const size_t sx = dtype_size(h.xc_dtype);
   int Imax = 1, Qmax = 1, Jmax = 1, QH = 0;
@@ -166,7 +170,8 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   L.C = C;
   L.cw0 = (scaled && C > 1) ? 1 : 0;
   L.JB = (Jmax + (C - L.cw0) - 1) / (C - L.cw0);
-  const bool tc = h.xc_dtype == TRSGD_DTYPE_BF16;   // tensor-core path
+  const bool tc = tcp > 0;   // tensor-core path with tcp BF16 pieces per operand
+  L.tcp = tcp;
   const size_t JB4 = rup((size_t)L.JB, 4);
   L.ldxs = (int)rup((size_t)Imax, tc ? 8 : 4);
   {
@@ -209,10 +214,7 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
       L.off_hw = take(JBH4 * st, 16);
     }
   }
-  if (tc) {
-    L.off_zh = take((size_t)L.jbp * L.qp * 2, 128);
-    L.off_zl = take((size_t)L.jbp * L.qp * 2, 128);
-  }
+  for (int k = 0; k < tcp; ++k) L.off_zp[k] = take((size_t)L.jbp * L.qp * 2, 128);
   const size_t limit = (size_t)step_max_smem() - 1024;
   const size_t tail0 = rup(off, 128);
   if (tail0 >= limit) return false;
@@ -224,9 +226,12 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
     size_t reg = std::max((size_t)ti * L.ldg, (size_t)ti * L.ldq);
     if (scaled) reg = std::max(reg, (size_t)QH * L.ldq);
     size_t b = reg * st;
-    if (tc)   // split-BF16 G chunk (hi, lo) | partial gradient FP32 + Ew tile
+    if (tcp == 2)   // split-BF16 G chunk (hi, lo) | partial gradient FP32 + Ew tile
       b = std::max(std::max(b, (size_t)2 * 128 * L.qp * 2),
                    rup((size_t)128 * L.ldq * st, 128) + (size_t)128 * L.jbp * 2);
+    if (tcp == 3)   // G pieces, then the Ew pieces, then the FP32 partial, in turn (each dead
+                    // once the tensor cores have read it)
+      b = std::max(b, std::max((size_t)3 * 128 * L.qp * 2, (size_t)3 * 128 * L.jbp * 2));
     return b;
   };
   auto tail_bytes = [&](int ti) {
@@ -240,7 +245,7 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   L.rows_own = own_rows_for(TI);
   off = tail0;
   L.off_reg = take(reg_bytes(TI), 128);
-  L.off_ew = L.off_reg + rup((size_t)128 * L.ldq * st, 128);
+  L.off_ew = tcp == 3 ? L.off_reg : L.off_reg + rup((size_t)128 * L.ldq * st, 128);
   L.off_sb = L.off_reg;
   if (scaled) {
     L.off_h64 = take(h64b, 16);
@@ -266,6 +271,14 @@ static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
   if (tc) end = std::max(end, (size_t)120 * 1024);
   L.total = rup(end, 128);
   return L.total <= limit;
+}
+
+// BF16-mixed: two pieces; FP32: three pieces when they fit, else the FMA
+// units; FP64: the FMA units.
+static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
+  if (h.xc_dtype == TRSGD_DTYPE_BF16) return make_layout_p(h, C, 2, L);
+  if (h.core_dtype == 1 && h.fp32_pieces && make_layout_p(h, C, 3, L)) return true;
+  return make_layout_p(h, C, 0, L);
 }
 
 static int default_cluster(const trsgd_handle &h) {
@@ -329,6 +342,7 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
   h->stream = static_cast<cudaStream_t>(stream);
   h->core_dtype = cfg[0].prec == TRSGD_FP64 ? 0 : 1;
   h->xc_dtype = cfg[0].prec == TRSGD_BF16_MIXED ? TRSGD_DTYPE_BF16 : cfg[0].x_dtype;
+  h->fp32_pieces = cfg[0].fp32_units == TRSGD_FP32_PIECES ? 1 : 0;
   int rmax = 1;
   for (int p = 0; p < nproblems; ++p)
     for (int k = 0; k < cfg[p].N; ++k) rmax = std::max<int>(rmax, (int)cfg[p].R[k]);
@@ -867,6 +881,11 @@ trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial) {
 }
 
 int64_t trsgd_launch_count(const trsgd_handle *h) { return h ? h->launches : -1; }
+
+int32_t trsgd_tensor_pieces(const trsgd_handle *h) {
+  if (!h) return -1;
+  return h->grid ? h->gp.np : h->lay.tcp;
+}
 
 void trsgd_destroy(trsgd_handle *h) {
   if (!h) return;

@@ -50,10 +50,11 @@ struct StepLayout {
   int sb_ok;      // sampled slices staged in shared memory (else read through L2)
   int pstride;    // per-sample stride of the chain intermediates
   int qp, jbp;    // tensor-core path: Q and samples padded to 16 (tile extents)
+  int tcp;        // BF16 pieces per tensor-core operand: 2 (BF16-mixed), 3 (FP32), 0 (FMA units)
   // off_sb aliases the region [off_reg, total): the staged slices are dead
   // before the Gram / chunk buffers and the CDF scratch are written
   size_t off_desc, off_idx, off_col, off_w, off_wt, off_bar, off_x, off_z, off_reg, off_h64,
-      off_hdiag, off_gown, off_misc, off_const, off_sb, off_p0, off_p1, off_zh, off_zl, off_ew,
+      off_hdiag, off_gown, off_misc, off_const, off_sb, off_p0, off_p1, off_zp[3], off_ew,
       off_hz, off_hidx, off_hw, total;
   int JBH;        // max Hessian-batch samples per CTA
   int cw0;        // first CTA that takes samples: 1 for the scaled variant with C > 1 (CTA 0
@@ -105,6 +106,12 @@ cudaError_t launch_step(int core_dtype, int x_dtype, int rmax, const ProbDesc *d
 cudaError_t launch_advance_counter(long long *t, long long T, int set, cudaStream_t s);
 cudaError_t step_kernel_prepare(int core_dtype, int x_dtype, int rmax, const StepLayout &lay);
 int step_max_smem();
+// instantiated per (core type, fiber type, BF16 pieces) in step_<variant>.cu
+template <typename T, typename XT, int RMAX, int NPC>
+cudaError_t step_prepare_t(const StepLayout &lay);
+template <typename T, typename XT, int RMAX, int NPC>
+cudaError_t step_launch_t(const ProbDesc *descs, int nprob, const StepLayout &lay, int threads, long long t0,
+                          int nsteps, const long long *t_dev, cudaStream_t s);
 
 cudaError_t launch_mode_copy(int src_dtype, int dst_dtype, const void *X, void *out, long long A,
                              long long In, long long B, long long ld, cudaStream_t s);

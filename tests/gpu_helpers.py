@@ -56,7 +56,7 @@ class Case:
         self.cores_d = [torch.from_numpy(G.astype(self.dtype_np)).to(dev) for G in to_lib_cores(start)]
         pc = A.ProblemConfig(dims=self.dims, ranks=self.ranks, J=J, prec=prec, seed=self.ocfg.seed,
                              **{k: v for k, v in ocfg.items() if k in ("dist", "variant", "rule", "alpha", "eta",
-                                                                       "b", "eps", "damping", "J_H")})
+                                                                       "b", "eps", "damping", "J_H", "fp32_units")})
         self.pc = pc
         self.solver = A.Solver([pc], [self.Xd], [self.cores_d])
 

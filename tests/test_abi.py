@@ -109,7 +109,9 @@ def test_unsupported_shapes_reported(lib):
 
 def test_path_field_validated(lib):
     assert _init(lib, _cfg(path=3))[0] == _abi.EINVAL
-    assert _init(lib, _cfg(reserved=1))[0] == _abi.EINVAL
+    assert _init(lib, _cfg(fp32_units=2))[0] == _abi.EINVAL
+    # the whole-GPU path runs FP32 on tensor-core pieces only
+    assert _init(lib, _cfg(path=_abi.PATH_GRID, fp32_units=_abi.FP32_FMA))[0] == _abi.EUNSUPPORTED
 
 
 def test_null_handle_calls(lib):
@@ -119,6 +121,7 @@ def test_null_handle_calls(lib):
     assert lib.trsgd_rel_error(None, 0, None, ctypes.byref(out)) == _abi.EINVAL
     assert lib.trsgd_set_debug(None, 1) == _abi.EINVAL
     assert lib.trsgd_launch_count(None) == -1
+    assert lib.trsgd_tensor_pieces(None) == -1
     lib.trsgd_destroy(None)
 
 

@@ -40,9 +40,11 @@ class LazyTensor:
         return fiber + self.sigma * np.asarray(nz, dtype=np.float64)
 
 
-def test_headline_size_three_steps():
+@pytest.mark.parametrize("units", ["pieces", "fma"])
+def test_headline_size_three_steps(units):
     from paper_2303_16492_gb300 import synth
     A = api()
+    fu = A._abi.FP32_PIECES if units == "pieces" else A._abi.FP32_FMA
     w = synth.workload("c2")
     planted = synth.planted_cores(w)
     P = to_oracle_cores(planted, w.ranks)
@@ -59,8 +61,10 @@ def test_headline_size_three_steps():
     init = synth.initial_cores(w, float(torch.linalg.vector_norm(Xd.double()) ** 2))
     init = [G.astype(np.float32) for G in init]
     cores_d = [torch.from_numpy(G).cuda() for G in init]
-    pc = A.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, seed=w.seed + 3)
+    pc = A.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, seed=w.seed + 3, fp32_units=fu)
     s = A.Solver([pc], [Xd], [cores_d])
+    assert s.launch_shape() == (16, 512)   # the launch shape the benchmark times
+    assert s.tensor_pieces() == (3 if units == "pieces" else 0)
     s.set_debug(True)
     st = ob.State.new(to_oracle_cores([G.astype(np.float64) for G in init], w.ranks))
     cfg = ob.Config(J=w.J, alpha=w.alpha, seed=w.seed + 3)

@@ -6,7 +6,9 @@ Tolerances (derived from the arithmetic, stated per path):
   FP32 path: single steps within 2e-5 relative (sums of at most a few
     hundred FP32 products: sqrt(K) * 2^-24 ~ 1e-6 typical, K * 2^-24 ~ 1e-5
     worst case); indices and p_F bit-exact whenever both sides start from the
-    same cores.
+    same cores.  The same bound holds for the contractions on three BF16
+    pieces per operand: each operand is split exactly up to 2^-24 of its
+    value and the dropped piece products are below 2^-23 of each term.
 """
 import numpy as np
 import pytest
@@ -45,11 +47,18 @@ SHAPES_FP32 = [
 ]
 
 
+@pytest.mark.parametrize("units", ["pieces", "fma"])
 @pytest.mark.parametrize("shape", SHAPES_FP32, ids=lambda s: "x".join(map(str, s["dims"])) + f"_J{s['J']}")
 @pytest.mark.parametrize("cluster", [1, 4, 16])
-def test_fp32_single_steps(shape, cluster):
-    case = Case(prec=1, alpha=0.05, **shape)
+def test_fp32_single_steps(shape, cluster, units):
+    """FP32 on the FMA units and on the tensor cores as three BF16 pieces per
+    operand (the six products of order <= 2): both within the FP32 bound."""
+    A = api()
+    fu = A._abi.FP32_PIECES if units == "pieces" else A._abi.FP32_FMA
+    case = Case(prec=1, alpha=0.05, fp32_units=fu, **shape)
     case.solver.launch_shape(cluster=cluster, threads=256 if cluster == 4 else 512)
+    # these shapes are small enough for the pieces at every cluster size
+    assert case.solver.tensor_pieces() == (3 if units == "pieces" else 0)
     case.solver.set_debug(True)
     for t in range(4):
         # restart both sides from identical cores so each step is a single-step comparison
