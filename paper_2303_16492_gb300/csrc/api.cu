@@ -195,6 +195,7 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, StepLayout &L) 
   L.off_bar = take(16, 16);
   L.off_misc = take(64, 16);
   L.off_const = take(32 * 8, 16);
+  L.off_ord = take(3 * kMaxOrder * 4, 16);   // chain order, staged-slice offsets and pitches
   L.off_desc = take(rup(sizeof(ProbDesc), 16), 16);
   L.off_idx = take((size_t)L.JB * kMaxOrder * 4, 16);
   L.off_col = take((size_t)L.JB * 8, 16);

@@ -58,20 +58,21 @@ __device__ __forceinline__ void gemm_tn(int M, int N, int K, const T *__restrict
 // core of factor s, `idx[s]` its slice index.  Slice G_k(i) is column-major
 // R_k x R_{k+1} at cores[k] + i*R_k*R_{k+1}.  On return row[0..R_{k_{L-1}+1})
 // holds row rp of P (rp < R_{k_0}).  Core reads go through L2 only.
-template <int RMAX, typename T>
+// BYCORE: `idx` is indexed by core (idx[k]) instead of by factor.
+template <int RMAX, typename T, bool BYCORE = false>
 __device__ __forceinline__ void chain_row(const T *const *cores, const int *R, int N,
                                           const int *order, const int *idx, int L, int rp,
                                           T (&row)[RMAX]) {
   int k = order[0];
   int Ra = R[k], Rb = R[(k + 1) % N];
-  const T *S = cores[k] + (size_t)idx[0] * Ra * Rb;
+  const T *S = cores[k] + (size_t)idx[BYCORE ? k : 0] * Ra * Rb;
 #pragma unroll
   for (int b = 0; b < RMAX; ++b) row[b] = (b < Rb) ? ld_l2(S + rp + (size_t)b * Ra) : T(0);
   for (int s = 1; s < L; ++s) {
     k = order[s];
     Ra = R[k];
     Rb = R[(k + 1) % N];
-    S = cores[k] + (size_t)idx[s] * Ra * Rb;
+    S = cores[k] + (size_t)idx[BYCORE ? k : s] * Ra * Rb;
     T nrow[RMAX];
 #pragma unroll
     for (int b = 0; b < RMAX; ++b) {

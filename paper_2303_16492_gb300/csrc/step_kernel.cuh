@@ -168,6 +168,9 @@ __global__ void __launch_bounds__(kMaxThreads)
   double *misc = reinterpret_cast<double *>(smem + lay.off_misc);
   double *cst = reinterpret_cast<double *>(smem + lay.off_const);   // [0,8): 1/I_k, [8,16): |F| J_n
   T *sb = reinterpret_cast<T *>(smem + lay.off_sb);                 // staged slices (aliases the tail)
+  // per step: ring order of the chain factors, staged-slice offsets and pitches
+  int *order = reinterpret_cast<int *>(smem + lay.off_ord);
+  int *soff = order + kMaxOrder, *qpad = order + 2 * kMaxOrder;
 
   const int tid = threadIdx.x, NT = blockDim.x;
   {   // the problem descriptor, once per launch
@@ -200,9 +203,9 @@ __global__ void __launch_bounds__(kMaxThreads)
   uint32_t mphase = 0;
   const ProbDesc &D = *desc_s;
   const int N = D.N, J = D.J;
-  int I[kMaxOrder], R[kMaxOrder];
-#pragma unroll
-  for (int k = 0; k < kMaxOrder; ++k) { I[k] = D.I[k]; R[k] = D.R[k]; }
+  // dims and ranks read from the shared descriptor: small per-thread arrays
+  // indexed at run time would live in local memory (L2 round trips)
+  const int *I = D.I, *R = D.R;
   const bool scaled = D.variant == 1;
   const bool rec = D.dbg && pidx == 0;
   int ru = R[0];   // the common rank when all ranks are equal, else 0
@@ -256,13 +259,31 @@ __global__ void __launch_bounds__(kMaxThreads)
       }
 #pragma unroll
       for (int k = 0; k < EWP; ++k) ewp[k] = smem + lay.off_ew + (size_t)k * 128 * lay.jbp * 2;
+      const bool g16 = (D.slice_tma >> n) & 1;   // 16-byte rows of G_n: float4 reads
       for (int e = tid; e < 128 * QC; e += NT) {
-        const int ii = e / QC, qb = e - ii * QC;
+        // 8 consecutive threads: the 8 rows of one core matrix, so that each
+        // piece store of a warp covers 512 contiguous bytes (no bank conflicts)
+        const int rest = e >> 3, qb = rest % QC, ii = (rest / QC) * 8 + (e & 7);
+        const bool live = ii < ti;
+        const float *grow = reinterpret_cast<const float *>(Gn) + (size_t)(i0 + (live ? ii : 0)) * Q;
         float v[8];
+        if (g16) {
   #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int q = qb * 8 + j;
-          v[j] = (ii < ti && q < Q) ? (float)ld_l2(Gn + (size_t)(i0 + ii) * Q + q) : 0.f;
+          for (int h = 0; h < 2; ++h) {
+            const int q = qb * 8 + 4 * h;
+            const float4 f = (live && q < Q) ? __ldcg(reinterpret_cast<const float4 *>(grow + q))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[4 * h] = f.x;
+            v[4 * h + 1] = f.y;
+            v[4 * h + 2] = f.z;
+            v[4 * h + 3] = f.w;
+          }
+        } else {
+  #pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int q = qb * 8 + j;
+            v[j] = (live && q < Q) ? __ldcg(grow + q) : 0.f;
+          }
         }
         uint4 w[NPC > 0 ? NPC : 1];
         bf16_split8<NPC>(v, w);
@@ -373,26 +394,28 @@ __global__ void __launch_bounds__(kMaxThreads)
     cur_Q = Q;
     cur_jb = jb;
     cur_j0 = j0;
-    int order[kMaxOrder];
-#pragma unroll
-    for (int q = 0; q < kMaxOrder; ++q) order[q] = (q < L) ? (n + 1 + q) % N : 0;
-    // staged slice layout: factor s at sb + soff[s], sample jl at + jl * qpad[s]
-    int soff[kMaxOrder], qpad[kMaxOrder];
-    bool sl_async = true;
-    {
+    // core of chain factor q (ring order n+1, ..., n-1), computed where the
+    // shared copy is not yet written
+    auto ring = [&](int q) {
+      const int k = n + 1 + q;
+      return k >= N ? k - N : k;
+    };
+    // staged slice layout: factor s at sb + soff[s], sample jl at + jl * qpad[s];
+    // written by thread 0 here, read after the sampling barrier (the previous
+    // step's readers finished several barriers ago)
+    if (tid == 0) {
       int off = 0;
-#pragma unroll
       for (int q = 0; q < kMaxOrder; ++q) {
-        const int k = order[q];
+        const int k = q < L ? ring(q) : 0;
         const int qs = R[k] * R[(k + 1) % N];
+        order[q] = k;
         qpad[q] = (int)round_up((size_t)qs, 16 / sizeof(T));
         soff[q] = off;
-        if (q < L) {
-          off += jb * qpad[q];
-          if (!((D.slice_tma >> k) & 1)) sl_async = false;
-        }
+        if (q < L) off += jb * qpad[q];
       }
     }
+    const int all_k = (1 << N) - 1;
+    const bool sl_async = ((D.slice_tma | (1 << n)) & all_k) == all_k;   // every factor's slices 16-byte rows
     T *Gn = static_cast<T *>(D.cores[n]);
     T *accn = static_cast<T *>(D.acc[n]);
 
@@ -409,7 +432,7 @@ __global__ void __launch_bounds__(kMaxThreads)
       long long col = 0, st = 1;
       if (D.dist == 3) {   // optimal distribution: indices and p_F drawn by the sampling kernels
         for (int sp = 0; sp < L; ++sp) {
-          const int k = order[sp];
+          const int k = ring(sp);
           const int i = __ldcg(D.ext_idx + (size_t)(j0 + jl) * N + k);
           idx_s[jl * kMaxOrder + k] = i;
           col += (long long)i * st;
@@ -420,11 +443,11 @@ __global__ void __launch_bounds__(kMaxThreads)
       uint64_t us[kMaxOrder];
 #pragma unroll
       for (int sp = 0; sp < kMaxOrder; ++sp)
-        us[sp] = (sp < L) ? draw_u64(D.seed, t, kStreamF, order[sp], (uint32_t)(j0 + jl)) : 0ull;
+        us[sp] = (sp < L) ? draw_u64(D.seed, t, kStreamF, ring(sp), (uint32_t)(j0 + jl)) : 0ull;
 #pragma unroll
       for (int sp = 0; sp < kMaxOrder; ++sp) {
         if (sp >= L) break;
-        const int k = order[sp], Ik = I[k];
+        const int k = ring(sp), Ik = I[k];
         const uint64_t u = us[sp];
         int i;
         if (uni) {
@@ -515,15 +538,15 @@ __global__ void __launch_bounds__(kMaxThreads)
       // P_1 = G_{n+1}(i) (staged, column-major); P_{s+1} = P_s G_{k_s}(i_s), one
       // thread per entry (jl, r', b), row-major [r'][b] per sample; the last
       // product lands in Z.  Intermediates ping-pong between two buffers.
-      T *pbuf[2] = {reinterpret_cast<T *>(smem + lay.off_p0), reinterpret_cast<T *>(smem + lay.off_p1)};
+      T *const pb0 = reinterpret_cast<T *>(smem + lay.off_p0), *const pb1 = reinterpret_cast<T *>(smem + lay.off_p1);
       const int pst = lay.pstride;
       const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
       for (int q = 1; q < L; ++q) {
         const int k = order[q], Ra = R[k], Rb = R[(k + 1) % N];
         const bool last = q == L - 1;
-        T *dst = last ? zs : pbuf[q & 1];
+        T *dst = last ? zs : ((q & 1) ? pb1 : pb0);
         const int dstride = last ? ldq : pst;
-        const T *src = (q == 1) ? sb + soff[0] : pbuf[(q - 1) & 1];
+        const T *src = (q == 1) ? sb + soff[0] : (((q - 1) & 1) ? pb1 : pb0);
         const int sstride = (q == 1) ? qpad[0] : pst;
         const int per = Rn1 * Rb;              // entries of P_{q+1} per sample (<= 256)
         bool done = true;
@@ -584,13 +607,8 @@ __global__ void __launch_bounds__(kMaxThreads)
       for (int e = tid; e < jb * Rn1; e += NT) {
         const int jl = e / Rn1, rp = e - jl * Rn1;
         T row[RMAX];
-        int sidx[kMaxOrder];
-#pragma unroll
-        for (int q = 0; q < kMaxOrder; ++q) sidx[q] = (q < L) ? idx_s[jl * kMaxOrder + order[q]] : 0;
-        const T *cores_c[kMaxOrder];
-#pragma unroll
-        for (int q = 0; q < kMaxOrder; ++q) cores_c[q] = static_cast<const T *>(D.cores[q]);
-        chain_row<RMAX, T>(cores_c, R, N, order, sidx, L, rp, row);
+        chain_row<RMAX, T, true>(reinterpret_cast<const T *const *>(D.cores), R, N, order, idx_s + jl * kMaxOrder,
+                                 L, rp, row);
         T *zrow = zs + (size_t)jl * ldq + rp * Rn;
 #pragma unroll
         for (int r = 0; r < RMAX; ++r) {
@@ -610,12 +628,19 @@ __global__ void __launch_bounds__(kMaxThreads)
       // Z as NPC BF16 pieces in the no-swizzle K-major tiles [JBP rows jl][QP cols q]
       const int QC = lay.qp / 8;
       for (int e = tid; e < lay.jbp * QC; e += NT) {
-        const int jl = e / QC, qb = e - jl * QC;
+        // 8 consecutive threads: the 8 rows of one core matrix (conflict-free
+        // piece stores); 16-byte reads of Z, whose rows are zero-padded to Q4
+        const int rest = e >> 3, qb = rest % QC, jl = (rest / QC) * 8 + (e & 7);
         float v[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int q = qb * 8 + j;
-          v[j] = (jl < jb && q < Q) ? (float)zs[(size_t)jl * ldq + q] : 0.f;
+        for (int h = 0; h < 2; ++h) {
+          const int q = qb * 8 + 4 * h;
+          const float4 f = (jl < jb && q < Q) ? *reinterpret_cast<const float4 *>(zs + (size_t)jl * ldq + q)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+          v[4 * h] = f.x;
+          v[4 * h + 1] = f.y;
+          v[4 * h + 2] = f.z;
+          v[4 * h + 3] = f.w;
         }
         uint4 w[NPC > 0 ? NPC : 1];
         bf16_split8<NPC>(v, w);
@@ -666,16 +691,11 @@ __global__ void __launch_bounds__(kMaxThreads)
           hw[jl] = (T)__ddiv_rn(1.0, __dmul_rn(cst[24 + n], pH));
         }
         __syncthreads();
-        const T *cores_c[kMaxOrder];
-#pragma unroll
-        for (int q = 0; q < kMaxOrder; ++q) cores_c[q] = static_cast<const T *>(D.cores[q]);
         for (int e = tid; e < jbh * Rn1; e += NT) {
           const int jl = e / Rn1, rp = e - jl * Rn1;
-          int sidx[kMaxOrder];
-#pragma unroll
-          for (int q = 0; q < kMaxOrder; ++q) sidx[q] = (q < L) ? hidx[jl * kMaxOrder + order[q]] : 0;
           T row[RMAX];
-          chain_row<RMAX, T>(cores_c, R, N, order, sidx, L, rp, row);
+          chain_row<RMAX, T, true>(reinterpret_cast<const T *const *>(D.cores), R, N, order, hidx + jl * kMaxOrder,
+                                   L, rp, row);
           T *zrow = hz + (size_t)jl * ldq + rp * Rn;
 #pragma unroll
           for (int r = 0; r < RMAX; ++r)
