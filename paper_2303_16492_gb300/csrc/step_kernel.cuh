@@ -86,51 +86,99 @@ __device__ __forceinline__ T dotk(const T *p, const T *s) {
   return acc;
 }
 
-// One factor of the batched slice chain for a uniform rank RU: P_{q+1} =
-// P_q S_q (row-major [r'][b] per sample; the first P is the staged slice,
-// column-major).  32 / RU samples per warp, lane = (sample slot, output
-// column b): the column b of the sample's slice stays in registers and each
-// row of P is read once per group of RU lanes (a broadcast within the group).
-template <int RU, bool FIRST, typename T>
+// One factor of the batched slice chain for a uniform (even) rank RU:
+// P_{q+1} = P_q S_q per sample, written row-major [r'][b]; the first P is the
+// staged slice itself (column-major).  A group of RU / CB lanes per sample:
+// lane bb owns the CB output columns bb*CB .., whose entries of S_q stay in
+// registers, so every loaded value of P_q serves CB outputs and a warp covers
+// 32 / (RU / CB) samples.  Column-major P_q (FIRST) is accumulated as outer
+// products of its columns, row-major P_q as dot products with its rows; either
+// way each output sums a = 0 .. RU-1 in order with fused multiply-adds.
+template <int RU, int CB, bool FIRST, typename T>
 __device__ __noinline__ void chain_factor_uniform(const T *src, int sstride, const T *sfac, int qpad, T *dst,
                                                   int dstride, int jb) {
-  constexpr int G = 32 / RU;
+  static_assert(RU % 2 == 0 && RU % CB == 0, "even rank, whole lane groups");
+  constexpr int LPS = RU / CB, G = 32 / LPS;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int g = lane / RU, b = lane - g * RU;
+  const int g = lane / LPS, bb = lane - g * LPS;
   const bool lane_ok = g < G;
+  const int b0 = (lane_ok ? bb : 0) * CB;
   for (int j0 = warp * G; j0 < jb; j0 += nwarps * G) {
     const int jl = j0 + g;
     const bool ok = lane_ok && jl < jb;
     const int jc = ok ? jl : 0;
-    const T *prow = src + (size_t)jc * sstride;
-    const T *S = sfac + (size_t)jc * qpad + (lane_ok ? b : 0) * RU;
-    T col[RU];
+    const T *P = src + (size_t)jc * sstride;
+    const T *S = sfac + (size_t)jc * qpad;   // column-major RU x RU
+    T col[CB][RU];
 #pragma unroll
-    for (int a = 0; a < RU; ++a) col[a] = S[a];
-    T *drow = dst + (size_t)jc * dstride;
+    for (int c = 0; c < CB; ++c)
+#pragma unroll
+      for (int a = 0; a < RU; ++a) col[c][a] = S[(b0 + c) * RU + a];
+    T *Dp = dst + (size_t)jc * dstride + b0;
+    if constexpr (FIRST) {
+      T acc[RU][CB];
+#pragma unroll
+      for (int r = 0; r < RU; ++r)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) acc[r][c] = T(0);
 #pragma unroll 2
-    for (int r = 0; r < RU; ++r) {
-      T acc = T(0);
-      if constexpr (!FIRST && (RU % 2 == 0) && sizeof(T) == 4) {
-        const float2 *pr = reinterpret_cast<const float2 *>(prow + r * RU);
+      for (int a = 0; a < RU; ++a) {
+        T pc[RU];   // column a of P_q
+        if constexpr (sizeof(T) == 4) {
+          const float2 *p2 = reinterpret_cast<const float2 *>(P + a * RU);
 #pragma unroll
-        for (int a2 = 0; a2 < RU / 2; ++a2) {
-          const float2 v = pr[a2];
-          acc = fma(v.x, col[2 * a2], acc);
-          acc = fma(v.y, col[2 * a2 + 1], acc);
+          for (int r2 = 0; r2 < RU / 2; ++r2) {
+            const float2 v = p2[r2];
+            pc[2 * r2] = v.x;
+            pc[2 * r2 + 1] = v.y;
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < RU; ++r) pc[r] = P[a * RU + r];
         }
-      } else {
 #pragma unroll
-        for (int a = 0; a < RU; ++a) acc = fma(prow[FIRST ? r + a * RU : r * RU + a], col[a], acc);
+        for (int r = 0; r < RU; ++r)
+#pragma unroll
+          for (int c = 0; c < CB; ++c) acc[r][c] = fma(pc[r], col[c][a], acc[r][c]);
       }
-      if (ok) drow[r * RU + b] = acc;
+      if (ok) {
+#pragma unroll
+        for (int r = 0; r < RU; ++r)
+#pragma unroll
+          for (int c = 0; c < CB; ++c) Dp[r * RU + c] = acc[r][c];
+      }
+    } else {
+#pragma unroll 2
+      for (int r = 0; r < RU; ++r) {
+        T pr[RU];   // row r of P_q
+        if constexpr (sizeof(T) == 4) {
+          const float2 *p2 = reinterpret_cast<const float2 *>(P + r * RU);
+#pragma unroll
+          for (int a2 = 0; a2 < RU / 2; ++a2) {
+            const float2 v = p2[a2];
+            pr[2 * a2] = v.x;
+            pr[2 * a2 + 1] = v.y;
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < RU; ++a) pr[a] = P[r * RU + a];
+        }
+        T acc[CB];
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          acc[c] = T(0);
+#pragma unroll
+          for (int a = 0; a < RU; ++a) acc[c] = fma(pr[a], col[c][a], acc[c]);
+        }
+        if (ok) {
+#pragma unroll
+          for (int c = 0; c < CB; ++c) Dp[r * RU + c] = acc[c];
+        }
+      }
     }
   }
 }
 
-// Step rule on one entry of G_n: fixed alpha (Eq. update_brsgd) or AdaGrad
-// (Remark after Algorithm 3: A += p^2, step eta (b + A)^-(1/2 + eps) p, zero
-// where b + A = 0), in the core precision.
 template <typename T>
 __device__ __forceinline__ T step_delta(int rule, T alpha, T eta, T b, double eps, T *accn, size_t gi, T p) {
   if (rule == 0) return alpha * p;
@@ -478,6 +526,9 @@ __global__ void __launch_bounds__(kMaxThreads)
     __syncthreads();
 
     // ---- A3: gather fibers and sampled slices into shared memory -----------
+    // Long fibers by bulk copies (one per fiber, issued by warp 0, completing on
+    // an mbarrier); short fibers and the slices by 16-byte per-thread
+    // asynchronous copies, which issue faster than one small bulk copy each.
     const uint32_t fbytes = (uint32_t)round_up((size_t)In * sizeof(XT), 16);
     const bool fiber_tma = fbytes >= kTmaFiberBytes;
     {
@@ -551,14 +602,14 @@ __global__ void __launch_bounds__(kMaxThreads)
         const int per = Rn1 * Rb;              // entries of P_{q+1} per sample (<= 256)
         bool done = true;
         switch (ru) {
-          case 4: q == 1 ? chain_factor_uniform<4, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
-                         : chain_factor_uniform<4, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
-          case 8: q == 1 ? chain_factor_uniform<8, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
-                         : chain_factor_uniform<8, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
-          case 10: q == 1 ? chain_factor_uniform<10, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
-                          : chain_factor_uniform<10, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
-          case 16: q == 1 ? chain_factor_uniform<16, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
-                          : chain_factor_uniform<16, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
+          case 4: q == 1 ? chain_factor_uniform<4, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
+                         : chain_factor_uniform<4, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
+          case 8: q == 1 ? chain_factor_uniform<8, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
+                         : chain_factor_uniform<8, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
+          case 10: q == 1 ? chain_factor_uniform<10, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
+                          : chain_factor_uniform<10, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
+          case 16: q == 1 ? chain_factor_uniform<16, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
+                          : chain_factor_uniform<16, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
           default: done = false;
         }
         if (!done) {

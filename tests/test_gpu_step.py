@@ -69,6 +69,24 @@ def test_fp32_single_steps(shape, cluster, units):
         _compare_step(case, rec, 2e-5)
 
 
+@pytest.mark.parametrize("rank", [4, 8, 10, 16])
+@pytest.mark.parametrize("cluster", [1, 16])
+def test_fp32_uniform_rank_chain(rank, cluster):
+    """Equal ranks take the register-blocked chain (two output columns per
+    lane, one lane group per sample): N = 4 runs its first factor on the
+    column-major staged slice and the second on a row-major intermediate;
+    J = 77 leaves ragged lane groups at both cluster sizes."""
+    case = Case(dims=[9, 11, 10, 12], ranks=[rank] * 4, J=77, prec=1, alpha=0.02)
+    case.solver.launch_shape(cluster=cluster, threads=512)
+    case.solver.set_debug(True)
+    for t in range(4):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, 2e-5)
+
+
 def test_fp32_chunked_rows_ragged_tail():
     """I_n = 300 with Q = 256 does not fit one chunk: rows are processed in
     chunks with a ragged last chunk."""
