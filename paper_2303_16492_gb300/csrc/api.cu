@@ -256,12 +256,20 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, StepLayout &L) 
   size_t end = std::max(off, tail0 + (size_t)Imax * 16);
   // staged slices followed by the two chain buffers, all aliasing the tail
   L.pstride = pst;
-  const size_t sb_bytes = rup((size_t)L.JB * sbq * st, 128);
-  const size_t pb_bytes = rup((size_t)L.JB * pst * st, 128);
+  // for all JB samples if they fit, else for the largest group of 32k (or
+  // fewer) samples that does; the chain then runs group by group
+  auto sb_need = [&](int s) {
+    return rup((size_t)s * sbq * st, 128) + 2 * rup((size_t)s * pst * st, 128);
+  };
+  int sbj = L.JB;
+  while (sbj > 0 && tail0 + sb_need(sbj) > limit) sbj = sbj > 32 ? (sbj - 1) / 32 * 32 : sbj - 1;
+  const size_t sb_bytes = rup((size_t)sbj * sbq * st, 128);
+  const size_t pb_bytes = rup((size_t)sbj * pst * st, 128);
+  L.sbj = std::max(sbj, 1);
   L.off_p0 = tail0 + sb_bytes;
   L.off_p1 = L.off_p0 + pb_bytes;
-  L.sb_ok = (tail0 + sb_bytes + 2 * pb_bytes <= limit) ? 1 : 0;
-  if (L.sb_ok) end = std::max(end, tail0 + sb_bytes + 2 * pb_bytes);
+  L.sb_ok = sbj > 0 ? 1 : 0;
+  if (L.sb_ok) end = std::max(end, tail0 + sb_need(sbj));
   // the leverage table of the updated core is rebuilt in the tail by CTA 0
   for (const auto &c : h.cfg) {
     if (c.dist != TRSGD_DIST_LEVERAGE) continue;

@@ -48,6 +48,7 @@ struct StepLayout {
   int QH;         // max Q of the scaled variant (0: none)
   int rows_own;   // max rows of g owned by one CTA
   int sb_ok;      // sampled slices staged in shared memory (else read through L2)
+  int sbj;        // samples whose slices are staged at a time (the chain runs per group)
   int pstride;    // per-sample stride of the chain intermediates
   int qp, jbp;    // tensor-core path: Q and samples padded to 16 (tile extents)
   int tcp;        // BF16 pieces per tensor-core operand: 2 (BF16-mixed), 3 (FP32), 0 (FMA units)

@@ -451,6 +451,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     // staged slice layout: factor s at sb + soff[s], sample jl at + jl * qpad[s];
     // written by thread 0 here, read after the sampling barrier (the previous
     // step's readers finished several barriers ago)
+    const int jbs = min(jb, lay.sbj);   // samples whose slices are staged at a time
     if (tid == 0) {
       int off = 0;
       for (int q = 0; q < kMaxOrder; ++q) {
@@ -459,7 +460,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         order[q] = k;
         qpad[q] = (int)round_up((size_t)qs, 16 / sizeof(T));
         soff[q] = off;
-        if (q < L) off += jb * qpad[q];
+        if (q < L) off += jbs * qpad[q];
       }
     }
     const int all_k = (1 << N) - 1;
@@ -525,9 +526,9 @@ __global__ void __launch_bounds__(kMaxThreads)
     if (rec && c == 0 && tid == 0) *D.dbg_n = n;
     __syncthreads();
 
-    // ---- A3: gather fibers and sampled slices into shared memory -----------
+    // ---- A3: gather the fibers into shared memory (waited for after A4) -----
     // Long fibers by bulk copies (one per fiber, issued by warp 0, completing on
-    // an mbarrier); short fibers and the slices by 16-byte per-thread
+    // an mbarrier); short fibers (and the slices, in A4) by 16-byte per-thread
     // asynchronous copies, which issue faster than one small bulk copy each.
     const uint32_t fbytes = (uint32_t)round_up((size_t)In * sizeof(XT), 16);
     const bool fiber_tma = fbytes >= kTmaFiberBytes;
@@ -554,99 +555,96 @@ __global__ void __launch_bounds__(kMaxThreads)
       for (int e = tid; e < (jb4 - jb) * lay.ldxs; e += NT)
         xs[(size_t)(jb + e / lay.ldxs) * lay.ldxs + e % lay.ldxs] = XT(0);
     }
-    if (lay.sb_ok) {
-      for (int q = 0; q < L; ++q) {
-        const int k = order[q], qs = R[k] * R[(k + 1) % N];
-        const T *G = static_cast<const T *>(D.cores[k]);
-        if (sl_async) {
-          const int nch = qs * (int)sizeof(T) / 16;
-          for (int e = tid; e < jb * nch; e += NT) {
-            const int jl = e / nch, ch = e - jl * nch;
-            cp_async16(reinterpret_cast<char *>(sb + soff[q] + (size_t)jl * qpad[q]) + 16 * ch,
-                       reinterpret_cast<const char *>(G + (size_t)idx_s[jl * kMaxOrder + k] * qs) + 16 * ch);
-          }
-        } else {
-#pragma unroll 4
-          for (int e = tid; e < jb * qs; e += NT) {
-            const int jl = e / qs, off = e - jl * qs;
-            sb[soff[q] + (size_t)jl * qpad[q] + off] = ld_l2(G + (size_t)idx_s[jl * kMaxOrder + k] * qs + off);
-          }
-        }
-      }
-    }
-    cp_async_wait_all();
-    if (fiber_tma && jb > 0) {
-      if (!mbar_wait_bounded(bar, phase, kWaitLimit)) {
-        latch_status(D.status, kStatusTimeout);
-        mbar_wait_bounded(bar, phase, kWaitLimit);
-      }
-      phase ^= 1u;
-    }
-    __syncthreads();
 
     // ---- A4: sampled subchain rows, Z(j, r + r' R_n) = P_j(r', r) ----------
     if (lay.sb_ok) {
-      // P_1 = G_{n+1}(i) (staged, column-major); P_{s+1} = P_s G_{k_s}(i_s), one
-      // thread per entry (jl, r', b), row-major [r'][b] per sample; the last
-      // product lands in Z.  Intermediates ping-pong between two buffers.
+      // Per group of jbs samples: stage the sampled slices G_k(i_k), then
+      // P_1 = G_{n+1}(i) (staged, column-major); P_{s+1} = P_s G_{k_s}(i_s),
+      // row-major [r'][b] per sample; the last product lands in rows s0.. of Z.
+      // Intermediates ping-pong between two buffers.
       T *const pb0 = reinterpret_cast<T *>(smem + lay.off_p0), *const pb1 = reinterpret_cast<T *>(smem + lay.off_p1);
       const int pst = lay.pstride;
       const int warp = tid >> 5, lane = tid & 31, nwarps = NT >> 5;
-      for (int q = 1; q < L; ++q) {
-        const int k = order[q], Ra = R[k], Rb = R[(k + 1) % N];
-        const bool last = q == L - 1;
-        T *dst = last ? zs : ((q & 1) ? pb1 : pb0);
-        const int dstride = last ? ldq : pst;
-        const T *src = (q == 1) ? sb + soff[0] : (((q - 1) & 1) ? pb1 : pb0);
-        const int sstride = (q == 1) ? qpad[0] : pst;
-        const int per = Rn1 * Rb;              // entries of P_{q+1} per sample (<= 256)
-        bool done = true;
-        switch (ru) {
-          case 4: q == 1 ? chain_factor_uniform<4, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
-                         : chain_factor_uniform<4, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
-          case 8: q == 1 ? chain_factor_uniform<8, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
-                         : chain_factor_uniform<8, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
-          case 10: q == 1 ? chain_factor_uniform<10, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
-                          : chain_factor_uniform<10, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
-          case 16: q == 1 ? chain_factor_uniform<16, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb)
-                          : chain_factor_uniform<16, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jb); break;
-          default: done = false;
-        }
-        if (!done) {
-          // general ranks: this lane's entries it = lane + 32 u, row r' and column b
-          int pofs[8], pstep[8], sofs[8], dofs[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int it = lane + 32 * u;
-            const int rp = it / Rb, bb = it - rp * Rb;
-            pofs[u] = (q == 1) ? rp : rp * Ra;
-            pstep[u] = (q == 1) ? Rn1 : 1;
-            sofs[u] = bb * Ra;
-            dofs[u] = rp * Rb + bb;
-          }
-          for (int jl = warp; jl < jb; jl += nwarps) {
-            const T *prow = src + (size_t)jl * sstride;
-            const T *S = sb + soff[q] + (size_t)jl * qpad[q];
-            T *drow = dst + (size_t)jl * dstride;
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-              if (lane + 32 * u < per) {
-                const T *pp = prow + pofs[u];
-                const T *sc = S + sofs[u];
-                const int ps = pstep[u];
-                T acc = T(0);
-                for (int a = 0; a < Ra; ++a) acc = fma(pp[a * ps], sc[a], acc);
-                drow[dofs[u]] = acc;
-              }
+      for (int s0 = 0; s0 < jb; s0 += jbs) {
+        const int jbc = min(jbs, jb - s0);
+        const int *idg = idx_s + s0 * kMaxOrder;
+        for (int q = 0; q < L; ++q) {
+          const int k = order[q], qs = R[k] * R[(k + 1) % N];
+          const T *G = static_cast<const T *>(D.cores[k]);
+          if (sl_async) {
+            const int nch = qs * (int)sizeof(T) / 16;
+            for (int e = tid; e < jbc * nch; e += NT) {
+              const int jl = e / nch, ch = e - jl * nch;
+              cp_async16(reinterpret_cast<char *>(sb + soff[q] + (size_t)jl * qpad[q]) + 16 * ch,
+                         reinterpret_cast<const char *>(G + (size_t)idg[jl * kMaxOrder + k] * qs) + 16 * ch);
+            }
+          } else {
+  #pragma unroll 4
+            for (int e = tid; e < jbc * qs; e += NT) {
+              const int jl = e / qs, off = e - jl * qs;
+              sb[soff[q] + (size_t)jl * qpad[q] + off] = ld_l2(G + (size_t)idg[jl * kMaxOrder + k] * qs + off);
             }
           }
         }
+        cp_async_wait_all();
         __syncthreads();
-      }
-      if (L == 1) {   // N = 2: Z row is the single staged slice, transposed
-        for (int e = tid; e < jb * Q; e += NT) {
-          const int jl = e / Q, rem = e - jl * Q, rp = rem / Rn, r = rem - rp * Rn;
-          zs[(size_t)jl * ldq + rem] = sb[soff[0] + (size_t)jl * qpad[0] + rp + r * Rn1];
+        for (int q = 1; q < L; ++q) {
+          const int k = order[q], Ra = R[k], Rb = R[(k + 1) % N];
+          const bool last = q == L - 1;
+          T *dst = last ? zs + (size_t)s0 * ldq : ((q & 1) ? pb1 : pb0);
+          const int dstride = last ? ldq : pst;
+          const T *src = (q == 1) ? sb + soff[0] : (((q - 1) & 1) ? pb1 : pb0);
+          const int sstride = (q == 1) ? qpad[0] : pst;
+          const int per = Rn1 * Rb;              // entries of P_{q+1} per sample (<= 256)
+          bool done = true;
+          switch (ru) {
+            case 4: q == 1 ? chain_factor_uniform<4, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jbc)
+                           : chain_factor_uniform<4, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jbc); break;
+            case 8: q == 1 ? chain_factor_uniform<8, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jbc)
+                           : chain_factor_uniform<8, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jbc); break;
+            case 10: q == 1 ? chain_factor_uniform<10, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jbc)
+                            : chain_factor_uniform<10, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jbc); break;
+            case 16: q == 1 ? chain_factor_uniform<16, 2, true, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jbc)
+                            : chain_factor_uniform<16, 2, false, T>(src, sstride, sb + soff[q], qpad[q], dst, dstride, jbc); break;
+            default: done = false;
+          }
+          if (!done) {
+            // general ranks: this lane's entries it = lane + 32 u, row r' and column b
+            int pofs[8], pstep[8], sofs[8], dofs[8];
+  #pragma unroll
+            for (int u = 0; u < 8; ++u) {
+              const int it = lane + 32 * u;
+              const int rp = it / Rb, bb = it - rp * Rb;
+              pofs[u] = (q == 1) ? rp : rp * Ra;
+              pstep[u] = (q == 1) ? Rn1 : 1;
+              sofs[u] = bb * Ra;
+              dofs[u] = rp * Rb + bb;
+            }
+            for (int jl = warp; jl < jbc; jl += nwarps) {
+              const T *prow = src + (size_t)jl * sstride;
+              const T *S = sb + soff[q] + (size_t)jl * qpad[q];
+              T *drow = dst + (size_t)jl * dstride;
+  #pragma unroll
+              for (int u = 0; u < 8; ++u) {
+                if (lane + 32 * u < per) {
+                  const T *pp = prow + pofs[u];
+                  const T *sc = S + sofs[u];
+                  const int ps = pstep[u];
+                  T acc = T(0);
+                  for (int a = 0; a < Ra; ++a) acc = fma(pp[a * ps], sc[a], acc);
+                  drow[dofs[u]] = acc;
+                }
+              }
+            }
+          }
+          __syncthreads();
+        }
+        if (L == 1) {   // N = 2: Z row is the single staged slice, transposed
+          for (int e = tid; e < jbc * Q; e += NT) {
+            const int jl = e / Q, rem = e - jl * Q, rp = rem / Rn, r = rem - rp * Rn;
+            zs[(size_t)(s0 + jl) * ldq + rem] = sb[soff[0] + (size_t)jl * qpad[0] + rp + r * Rn1];
+          }
+          __syncthreads();   // the next group restages the slices
         }
       }
       if (rec) {
@@ -669,6 +667,15 @@ __global__ void __launch_bounds__(kMaxThreads)
           }
         }
       }
+    }
+    // the fibers (A3)
+    cp_async_wait_all();
+    if (fiber_tma && jb > 0) {
+      if (!mbar_wait_bounded(bar, phase, kWaitLimit)) {
+        latch_status(D.status, kStatusTimeout);
+        mbar_wait_bounded(bar, phase, kWaitLimit);
+      }
+      phase ^= 1u;
     }
     // zero padding of Z: columns [Q, Q4) of rows < jb, and rows [jb, jb4)
     if (Q4 > Q)

@@ -87,6 +87,22 @@ def test_fp32_uniform_rank_chain(rank, cluster):
         _compare_step(case, rec, 2e-5)
 
 
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_fp32_slices_staged_in_groups(cluster):
+    """N = 5 with equal ranks 8 and J = 300: on one CTA the sampled slices of
+    all 300 samples (1 KB each) do not fit shared memory at once, so they are
+    staged and chained in groups of samples with a ragged last group."""
+    case = Case(dims=[8, 7, 9, 6, 8], ranks=[8] * 5, J=300, prec=1, alpha=0.02)
+    case.solver.launch_shape(cluster=cluster, threads=512)
+    case.solver.set_debug(True)
+    for t in range(4):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, 2e-5)
+
+
 def test_fp32_chunked_rows_ragged_tail():
     """I_n = 300 with Q = 256 does not fit one chunk: rows are processed in
     chunks with a ragged last chunk."""
