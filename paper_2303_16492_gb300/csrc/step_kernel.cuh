@@ -308,6 +308,10 @@ __global__ void __launch_bounds__(kMaxThreads)
 #pragma unroll
       for (int k = 0; k < EWP; ++k) ewp[k] = smem + lay.off_ew + (size_t)k * 128 * lay.jbp * 2;
       const bool g16 = (D.slice_tma >> n) & 1;   // 16-byte rows of G_n: float4 reads
+      // plain variant: the rows [r0, r1) this CTA owns in the update are kept in
+      // gown, so that the update reads them from shared memory
+      const bool stash = !scaled;
+      const int r0 = ti * c / C, r1 = ti * (c + 1) / C;
       for (int e = tid; e < 128 * QC; e += NT) {
         // 8 consecutive threads: the 8 rows of one core matrix, so that each
         // piece store of a warp covers 512 contiguous bytes (no bank conflicts)
@@ -338,6 +342,11 @@ __global__ void __launch_bounds__(kMaxThreads)
         const uint32_t o = kmaj_off(ii, qb * 8, QC);
   #pragma unroll
         for (int k = 0; k < NPC; ++k) *reinterpret_cast<uint4 *>(gp[k] + o) = w[k];
+        if (stash && ii >= r0 && ii < r1) {   // FP32 values of the rows this CTA updates
+  #pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (qb * 8 + j < Q) gown[(size_t)(ii - r0) * ldq + qb * 8 + j] = v[j];
+        }
       }
       fence_proxy_async_smem();
       tc_fence_before();
@@ -898,31 +907,38 @@ __global__ void __launch_bounds__(kMaxThreads)
           gown[(size_t)(own_rows + ii - r0) * ldq + q] = g;
         } else {
           const T p = -g;
-          const T nv = ld_l2(Gn + gi) + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
+          T *own = gown + (size_t)(ii - r0) * ldq + q;
+          const T cur = kTC ? *own : ld_l2(Gn + gi);   // the tensor-core chunk kept the owned rows
+          const T nv = cur + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
           if (!isfinite(nv)) latch_status(D.status, kStatusNumeric);
           Gn[gi] = nv;
-          gown[(size_t)(ii - r0) * ldq + q] = nv;
+          *own = nv;
           if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
         }
       };
       if constexpr (sizeof(T) == 4) {
-        if ((Q & 3) == 0) {   // 16-byte remote loads, same fixed CTA order per entry
+        if ((Q & 3) == 0) {
+          // 16-byte remote loads; owner c pulls from CTAs c+1, c+2, ... (mod C) and
+          // sums in that fixed order (deterministic), so that the owners' requests
+          // spread over all CTAs instead of all hitting CTA 0 first
           const int Qv = Q >> 2;
           for (int e = tid; e < (r1 - r0) * Qv; e += NT) {
             const int ii = r0 + e / Qv, q0 = (e - (e / Qv) * Qv) * 4;
             float4 v[16];
 #pragma unroll
-            for (int cc = 0; cc < 16; ++cc)
-              v[cc] = (cc < C) ? *reinterpret_cast<const float4 *>(cluster.map_shared_rank(reg, cc) + (size_t)ii * ldq + q0)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int u = 0; u < 16; ++u) {
+              const int cc = c + 1 + u >= C ? c + 1 + u - C : c + 1 + u;
+              v[u] = (u < C) ? *reinterpret_cast<const float4 *>(cluster.map_shared_rank(reg, cc) + (size_t)ii * ldq + q0)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
             float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int cc = 0; cc < 16; ++cc)
-              if (cc < C) {
-                g.x += v[cc].x;
-                g.y += v[cc].y;
-                g.z += v[cc].z;
-                g.w += v[cc].w;
+            for (int u = 0; u < 16; ++u)
+              if (u < C) {
+                g.x += v[u].x;
+                g.y += v[u].y;
+                g.z += v[u].z;
+                g.w += v[u].w;
               }
             own_entry(ii, q0, g.x);
             own_entry(ii, q0 + 1, g.y);
