@@ -74,6 +74,21 @@ __device__ __forceinline__ void bf16_split8(const float (&v)[8], uint4 (&w)[PA])
   for (int k = 0; k < P; ++k) w[k] = make_uint4(u[k][0], u[k][1], u[k][2], u[k][3]);
 }
 
+// Commit this thread's outstanding cp.async copies as one group; wait until at
+// most n of its most recent groups are still in flight (n >= 6: 6).
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+  }
+}
+
 __device__ __forceinline__ float to_f32(float x) { return x; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
 
@@ -461,11 +476,11 @@ __global__ void __launch_bounds__(kMaxThreads)
     // written by thread 0 here, read after the sampling barrier (the previous
     // step's readers finished several barriers ago)
     const int jbs = min(jb, lay.sbj);   // samples whose slices are staged at a time
-    if (tid == 0) {
+    if (tid == NT - 1) {   // the last thread: the sampling below starts at thread 0
       int off = 0;
       for (int q = 0; q < kMaxOrder; ++q) {
         const int k = q < L ? ring(q) : 0;
-        const int qs = R[k] * R[(k + 1) % N];
+        const int qs = R[k] * R[k + 1 == N ? 0 : k + 1];
         order[q] = k;
         qpad[q] = (int)round_up((size_t)qs, 16 / sizeof(T));
         soff[q] = off;
@@ -479,6 +494,18 @@ __global__ void __launch_bounds__(kMaxThreads)
 
     // ---- A1/A2: per sample, slice indices (Algorithm 2), p_F (product in ring
     // order), weight 1/(|F| J_n p_F) and fiber column -------------------------
+    // Uniform sampling: first one thread per (sample, factor) draws the index,
+    // then one thread per sample combines them (the draws are independent).
+    const bool uni_split = D.dist == 0;
+    if (uni_split) {
+      for (int e = tid; e < L * jb; e += NT) {
+        const int sp = e / jb, jl = e - sp * jb;
+        const int k = ring(sp);
+        const uint64_t u = draw_u64(D.seed, t, kStreamF, k, (uint32_t)(j0 + jl));
+        idx_s[jl * kMaxOrder + k] = (int)mulhi64(u, (uint64_t)I[k]);
+      }
+      __syncthreads();
+    }
     for (int jl = tid; jl < jb4; jl += NT) {
       if (jl >= jb) {
         wt_s[jl] = T(0);
@@ -497,30 +524,30 @@ __global__ void __launch_bounds__(kMaxThreads)
           st *= I[k];
         }
         pF = __ldcg(D.ext_pf + j0 + jl);
-      } else {
-      uint64_t us[kMaxOrder];
-#pragma unroll
-      for (int sp = 0; sp < kMaxOrder; ++sp)
-        us[sp] = (sp < L) ? draw_u64(D.seed, t, kStreamF, ring(sp), (uint32_t)(j0 + jl)) : 0ull;
-#pragma unroll
-      for (int sp = 0; sp < kMaxOrder; ++sp) {
-        if (sp >= L) break;
-        const int k = ring(sp), Ik = I[k];
-        const uint64_t u = us[sp];
-        int i;
-        if (uni) {
-          i = (int)mulhi64(u, (uint64_t)Ik);
+      } else if (uni) {   // indices drawn above; p_F = prod 1/I_k (only when recorded)
+        for (int sp = 0; sp < L; ++sp) {
+          const int k = ring(sp);
           if (need_pf) pF = __dmul_rn(pF, cst[k]);
-        } else {
+          col += (long long)idx_s[jl * kMaxOrder + k] * st;
+          st *= I[k];
+        }
+      } else {   // leverage / Euclidean: inverse-CDF draws, p_F in ring order
+        uint64_t us[kMaxOrder];
+#pragma unroll
+        for (int sp = 0; sp < kMaxOrder; ++sp)
+          us[sp] = (sp < L) ? draw_u64(D.seed, t, kStreamF, ring(sp), (uint32_t)(j0 + jl)) : 0ull;
+#pragma unroll
+        for (int sp = 0; sp < kMaxOrder; ++sp) {
+          if (sp >= L) break;
+          const int k = ring(sp), Ik = I[k];
           const unsigned long long *cdf = D.cdf[k];
           const uint64_t W = __ldcg(cdf + Ik - 1);
-          i = cdf_search(cdf, Ik, mulhi64(u, W));
+          const int i = cdf_search(cdf, Ik, mulhi64(us[sp], W));
           pF = __dmul_rn(pF, __ldcg(D.prob[k] + i));
+          idx_s[jl * kMaxOrder + k] = i;
+          col += (long long)i * st;
+          st *= Ik;
         }
-        idx_s[jl * kMaxOrder + k] = i;
-        col += (long long)i * st;
-        st *= Ik;
-      }
       }
       const double w = need_pf ? __ddiv_rn(1.0, __dmul_rn(cst[8 + n], pF)) : cst[16];
       w_s[jl] = w;
@@ -594,10 +621,16 @@ __global__ void __launch_bounds__(kMaxThreads)
               sb[soff[q] + (size_t)jl * qpad[q] + off] = ld_l2(G + (size_t)idg[jl * kMaxOrder + k] * qs + off);
             }
           }
+          cp_async_commit_group();   // one group per factor (the first also holds the fibers)
         }
-        cp_async_wait_all();
+        // factor 1 needs the slices of factors 0 and 1; later ones arrive meanwhile
+        cp_async_wait_pending(L >= 2 ? L - 2 : 0);
         __syncthreads();
         for (int q = 1; q < L; ++q) {
+          if (q >= 2) {
+            cp_async_wait_pending(L - 1 - q);
+            __syncthreads();
+          }
           const int k = order[q], Ra = R[k], Rb = R[(k + 1) % N];
           const bool last = q == L - 1;
           T *dst = last ? zs + (size_t)s0 * ldq : ((q & 1) ? pb1 : pb0);
