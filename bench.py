@@ -390,6 +390,48 @@ def run_extras(args, device):
         out.update(run_large(args, device))
     except Exception as e:
         out["c5_error"] = repr(e)
+    try:
+        out["paper_experiment_shapes"] = run_paper_shapes(args, device)
+    except Exception as e:
+        out["paper_shapes_error"] = repr(e)
+    return out
+
+
+def run_paper_shapes(args, device):
+    """The shapes of the paper's experiments (Sec. 4): Experiment I (300^3,
+    R=10, |F|=200, plain and scaled with |H| = 200 / 400) run for the paper's
+    T = 4000 iterations, and same-shape stand-ins for the three hyperspectral
+    images (plain and scaled with |H| = 1000) for 2000 iterations.  Steps/s of
+    the timed run (device events) and the RSE it reached."""
+    import torch
+
+    from paper_2303_16492_gb300 import api, synth
+    out = {}
+    for name in synth.NEXT_WORKLOADS:
+        w = synth.workload(name)
+        X, Xtrue, init = device_problem(w, device)
+        steps = 4000 if name.startswith("e1") else 2000
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, variant=w.variant,
+                               J_H=w.JH, damping=w.damping, seed=w.seed + 3)
+        rec = {"dims": w.dims, "R": w.ranks[0], "J": w.J, "J_H": w.JH, "variant": "scaled" if w.variant else "plain",
+               "alpha": w.alpha, "iterations": steps}
+        s = api.Solver([pc], [X], [[c.clone() for c in init]])
+        try:
+            rec["rse_start"] = round(s.rel_error(0, Xtrue), 6)
+            shape = s.launch_shape()
+            rec["launch"] = {"cluster_ctas": shape[0], "threads": shape[1], "tensor_pieces": s.tensor_pieces()}
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            s.run(0, steps)
+            b.record()
+            torch.cuda.synchronize()
+            rec["steps_per_s"] = round(steps / (a.elapsed_time(b) * 1e-3), 1)
+            rec["rse_after"] = s.rel_error(0, Xtrue)
+        except Exception as e:   # a diverging step size is reported, not hidden
+            rec["error"] = repr(e)
+        s.close()
+        out[name] = rec
+        del X, Xtrue, init
     return out
 
 

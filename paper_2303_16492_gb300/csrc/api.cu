@@ -222,7 +222,11 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, StepLayout &L) 
   const size_t avail = limit - tail0;
   const size_t h64b = scaled ? (size_t)QH * (QH | 1) * 8 : 0;   // Gram, then the factor at an odd pitch
   const size_t hdb = scaled ? (size_t)QH * 8 : 0;
-  auto own_rows_for = [&](int TI) { return scaled ? (Imax + C - 1) / C + 1 : (TI + C - 1) / C + 1; };
+  // rows of g a CTA owns: per chunk of TI rows ceil(TI / C); the scaled
+  // variant keeps them for every chunk until the solve
+  auto own_rows_for = [&](int TI) {
+    return scaled ? (Imax + C - 1) / C + (Imax + TI - 1) / TI : (TI + C - 1) / C + 1;
+  };
   auto reg_bytes = [&](int ti) {
     size_t reg = std::max((size_t)ti * L.ldg, (size_t)ti * L.ldq);
     if (scaled) reg = std::max(reg, (size_t)QH * L.ldq);
@@ -241,7 +245,6 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, StepLayout &L) 
   int TI = tc ? 128 : (int)rup((size_t)Imax, 4);
   while (!tc && TI > 4 && tail_bytes(TI) > avail) TI = std::max(4, (TI * 7 / 8) & ~3);
   if (tail_bytes(TI) > avail) return false;
-  if (scaled && TI < Imax) return false;   // scaled: one chunk
   L.TI = TI;
   L.rows_own = own_rows_for(TI);
   off = tail0;

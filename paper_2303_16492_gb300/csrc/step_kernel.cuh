@@ -1019,7 +1019,16 @@ __global__ void __launch_bounds__(kMaxThreads)
       V *ivc = reinterpret_cast<V *>(hdiag);
       const bool ok = *cluster.map_shared_rank(misc, 0) != 0.0;
       const int warp = tid >> 5, lane = tid & 31, nw = NT >> 5;
-      const int r0 = In * c / C;   // single chunk: owned rows [r0, r0 + own_rows)
+      // owned row number rr -> row of G_n: chunk by chunk, this CTA owned rows
+      // [i0 + ti c / C, i0 + ti (c + 1) / C) of each chunk [i0, i0 + ti)
+      auto own_row = [&](int rr) {
+        for (int i0 = 0; i0 < In; i0 += lay.TI) {
+          const int ti = min(lay.TI, In - i0), a = ti * c / C, b = ti * (c + 1) / C;
+          if (rr < b - a) return i0 + a + rr;
+          rr -= b - a;
+        }
+        return In - 1;   // not reached: rr < own_rows
+      };
       constexpr int QM = 4;        // Q <= 128 = 32 * QM
       if (ok) {
         const V *Lg = static_cast<const V *>(D.lfac);
@@ -1031,7 +1040,7 @@ __global__ void __launch_bounds__(kMaxThreads)
       }
       __syncthreads();
       for (int rr = warp; rr < own_rows; rr += nw) {
-        const int i = r0 + rr;
+        const int i = own_row(rr);
         V y[QM];
 #pragma unroll
         for (int m = 0; m < QM; ++m) {
@@ -1107,7 +1116,7 @@ __global__ void __launch_bounds__(kMaxThreads)
             const double v = (double)row[q];
             sn = __dadd_rn(sn, __dmul_rn(v, v));
           }
-          D.snorm[n][r0 + rr] = sn;
+          D.snorm[n][own_row(rr)] = sn;
         }
       }
       cluster.sync();

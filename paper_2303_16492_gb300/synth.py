@@ -96,6 +96,7 @@ class Workload:
     rule: int = 0                    # 0 fixed, 1 AdaGrad
     eta: float = 0.0
     damping: float = 0.0
+    JH: int = 0                      # |H| of the scaled variant (0: H = F)
     dist: int = 0
     prec: int = 1                    # 0 FP64, 1 FP32, 2 BF16 storage / mixed
     seed: int = 0
@@ -103,7 +104,7 @@ class Workload:
 
 
 def workload(name: str) -> Workload:
-    """The five workload recipes (sizes of the synthetic test problems)."""
+    """The workload recipes (sizes of the synthetic test problems)."""
     if name == "c1":   # plain method, FP64 20^3, R=3
         return Workload("c1", [20, 20, 20], [3, 3, 3], 50, "gaussian", 1 / math.sqrt(3),
                         noise_rel=1e-3, init=0.1, alpha=0.01, prec=0)
@@ -120,7 +121,32 @@ def workload(name: str) -> Workload:
         # R = 20, J = 4096) on a 1000 x 400 x 400 tensor that a full counter capture can hold
         return Workload("c5p", [1000, 400, 400], [20] * 3, 4096, "illcond", smin=1e-2,
                         noise_rel=1e-3, variant=0, rule=1, eta=1e-2, prec=2)
+    # Experiment I (Sec. 4): 300^3, Gaussian N(0, 1) cores 10 x 300 x 10, |F| = 200,
+    # noiseless; the paper's step sizes (plain 6e-2; scaled 1e-1 with |H| = 200 or 400)
+    if name == "e1":
+        return Workload("e1", [300] * 3, [10] * 3, 200, "gaussian", 1.0, noise_rel=0.0, alpha=6e-2, prec=1)
+    if name in ("e1s", "e1s4"):
+        return Workload(name, [300] * 3, [10] * 3, 200, "gaussian", 1.0, noise_rel=0.0, alpha=1e-1, prec=1,
+                        variant=1, JH=200 if name == "e1s" else 400)
+    # Stand-ins shaped like the hyperspectral images of Sec. 4 (the images are not
+    # available): planted ill-conditioned rank-R TR (singular values 1 .. 1e-2) plus
+    # 5 % noise, |F| = 200; plain step 0.5 / lambda_max of the planted sampled-gradient
+    # curvature (rounded), scaled variant with the paper's alpha and |H| = 1000
+    hsi = {"hsi-salinas": ([83, 86, 224], 5, 8e3, 2e-2),
+           "hsi-indian": ([145, 145, 220], 10, 3.5e4, 4e-3),
+           "hsi-pavia": ([610, 340, 103], 10, 6e4, 4e-2)}
+    base = name[:-2] if name.endswith("-s") else name
+    if base in hsi:
+        dims, R, a_plain, a_scaled = hsi[base]
+        if name.endswith("-s"):
+            return Workload(name, dims, [R] * 3, 200, "illcond", smin=1e-2, noise_rel=0.05, alpha=a_scaled,
+                            prec=1, variant=1, JH=1000)
+        return Workload(name, dims, [R] * 3, 200, "illcond", smin=1e-2, noise_rel=0.05, alpha=a_plain, prec=1)
     raise KeyError(name)
+
+
+NEXT_WORKLOADS = ["e1", "e1s", "e1s4", "hsi-salinas", "hsi-salinas-s", "hsi-indian", "hsi-indian-s",
+                  "hsi-pavia", "hsi-pavia-s"]
 
 
 def batched_workloads(count: int = 64, seed: int = 0, J: int = 256):

@@ -152,25 +152,35 @@ def test_large_size_grid_path_steps(bf16):
     s.close()
 
 
-def _c3_problem(A):
-    """The c3 workload (N=5, 40^5, R=8, |F|=2048, Gaussian cores N(0, 1/8),
-    noise 1e-3): device X by the library's reconstruction plus seeded device
-    noise; the oracle's X evaluated fiber by fiber from the planted cores."""
+def _problem(A, name):
+    """A named workload from the synth module: device X by the library's
+    reconstruction plus seeded device noise (noise_rel of the rms of X_true,
+    estimated on 2000 oracle entries); the oracle's X evaluated fiber by fiber
+    from the planted cores and the same noise values."""
     from paper_2303_16492_gb300 import synth
-    w = synth.workload("c3")
+    w = synth.workload(name)
     planted = synth.planted_cores(w)
     P = to_oracle_cores(planted, w.ranks)
-    rng = np.random.default_rng(0)
-    ent = [tr.tr_entry(P, [int(rng.integers(0, d)) for d in w.dims]) for _ in range(2000)]
-    sigma = w.noise_rel * float(np.sqrt(np.mean(np.square(ent))))
-    gen = torch.Generator(device="cuda")
-    gen.manual_seed(w.seed + 1)
-    noise_d = torch.randn(int(np.prod(w.dims)), generator=gen, device="cuda", dtype=torch.float32)
-    Xo = LazyTensor(P, w.dims, lambda pos: noise_d[torch.from_numpy(pos).cuda()].double().cpu().numpy(), sigma)
     Xd = A.reconstruct([torch.from_numpy(G).to("cuda", torch.float32) for G in planted], w.dims, w.ranks)
-    Xd.add_(noise_d, alpha=sigma)
+    if w.noise_rel > 0:
+        rng = np.random.default_rng(0)
+        ent = [tr.tr_entry(P, [int(rng.integers(0, d)) for d in w.dims]) for _ in range(2000)]
+        sigma = w.noise_rel * float(np.sqrt(np.mean(np.square(ent))))
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(w.seed + 1)
+        noise_d = torch.randn(int(np.prod(w.dims)), generator=gen, device="cuda", dtype=torch.float32)
+        Xo = LazyTensor(P, w.dims, lambda pos: noise_d[torch.from_numpy(pos).cuda()].double().cpu().numpy(), sigma)
+        Xd.add_(noise_d, alpha=sigma)
+    else:
+        Xo = LazyTensor(P, w.dims, lambda pos: np.zeros(len(pos)), 0.0)
     init = [G.astype(np.float32) for G in synth.initial_cores(w, float(torch.linalg.vector_norm(Xd.double()) ** 2))]
     return w, P, Xo, Xd, init
+
+
+def _c3_problem(A):
+    """The c3 workload (N=5, 40^5, R=8, |F|=2048, Gaussian cores N(0, 1/8),
+    noise 1e-3)."""
+    return _problem(A, "c3")
 
 
 @pytest.mark.parametrize("dist", [ob.DIST_UNIFORM, ob.DIST_LEVERAGE, ob.DIST_EUCLIDEAN],
@@ -235,3 +245,44 @@ def test_c3_size_adjoint():
     assert abs(float(lg.item()) - loss) < 1e-5 * abs(loss)
     for k in range(5):
         assert rel(gg[k].double().cpu().numpy(), tr.unfold2(grads[k])) < 3e-5
+
+
+@pytest.mark.parametrize("name", ["e1", "e1s", "e1s4", "hsi-salinas", "hsi-salinas-s", "hsi-indian",
+                                  "hsi-indian-s", "hsi-pavia", "hsi-pavia-s"])
+def test_paper_experiment_shapes(name):
+    """The shapes of the paper's own experiments (Sec. 4): Experiment I (300^3,
+    R = 10, |F| = 200; plain, and scaled with |H| = 200 and 400) and stand-ins
+    for the three hyperspectral images (83x86x224 R=5, 145x145x220 R=10,
+    610x340x103 R=10, |F| = 200; plain, and scaled with |H| = 1000), in the
+    launch shape the library picks.  Two iterations from shared cores:
+    indices and p_F bit-exact, every intermediate (and h for the scaled
+    variant) within the FP32 tolerance."""
+    A = api()
+    w, P, Xo, Xd, init = _problem(A, name)
+    N, J = 3, w.J
+    cores_d = [torch.from_numpy(G).cuda() for G in init]
+    pc = A.ProblemConfig(dims=w.dims, ranks=w.ranks, J=J, prec=1, alpha=w.alpha, variant=w.variant, J_H=w.JH,
+                         damping=w.damping, seed=w.seed + 3)
+    s = A.Solver([pc], [Xd], [cores_d])
+    s.set_debug(True)
+    st = ob.State.new(to_oracle_cores([G.astype(np.float64) for G in init], w.ranks))
+    cfg = ob.Config(J=J, alpha=w.alpha, variant=w.variant, J_H=w.JH, damping=w.damping, seed=w.seed + 3)
+    tol = 1e-4 if w.variant == 1 else 2e-5
+    for t in range(2):
+        for k in range(N):
+            st.cores[k] = tr.fold2(cores_d[k].double().cpu().numpy(), w.ranks[k], w.ranks[(k + 1) % N])
+        rec = ob.step(st, Xo, cfg, t)
+        s.step(t)
+        n, In, Q = rec["n"], w.dims[rec["n"]], w.ranks[rec["n"]] * w.ranks[(rec["n"] + 1) % N]
+        assert int(s.get_debug(A._abi.DBG_MODE, np.int32, 1)[0]) == n
+        np.testing.assert_array_equal(s.get_debug(A._abi.DBG_IDX, np.int32, J * N).reshape(J, N), rec["idx"])
+        np.testing.assert_array_equal(s.get_debug(A._abi.DBG_PF, np.float64, J), rec["pF"])
+        assert rel(s.get_debug(A._abi.DBG_Z, np.float32, J * Q).reshape(J, Q), rec["Z"]) < tol
+        assert rel(s.get_debug(A._abi.DBG_E, np.float32, J * In).reshape(J, In).T, rec["E"]) < tol
+        assert rel(s.get_debug(A._abi.DBG_G, np.float32, In * Q).reshape(In, Q), rec["g"]) < tol
+        if w.variant == 1:
+            assert rel(s.get_debug(A._abi.DBG_H, np.float64, Q * Q).reshape(Q, Q), rec["h"]) < tol
+        assert rel(s.get_debug(A._abi.DBG_P, np.float32, In * Q).reshape(In, Q), rec["p"]) < tol
+        for k in range(N):
+            assert rel(cores_d[k].double().cpu().numpy(), tr.unfold2(st.cores[k])) < tol
+    s.close()

@@ -194,6 +194,29 @@ def test_scaled_variant_steps(prec, damping):
         _compare_step(case, rec, tol)
 
 
+@pytest.mark.parametrize("units", ["pieces", "fma"])
+@pytest.mark.parametrize("J_H", [0, 70])
+def test_scaled_variant_row_chunks(units, J_H):
+    """Scaled variant with I_1 = 300 rows of Q = 100 columns: the rows of G_1
+    are processed in chunks (128 rows on the tensor-core path), each CTA
+    keeps its owned rows of every chunk for the solve against the damped
+    Gram factor; with and without an independent Hessian batch H."""
+    A = api()
+    fu = A._abi.FP32_PIECES if units == "pieces" else A._abi.FP32_FMA
+    case = Case(dims=[300, 9, 11], ranks=[10, 10, 10], J=60, prec=1, alpha=0.3, variant=ob.VARIANT_SCALED,
+                damping=0.05, J_H=J_H, fp32_units=fu)
+    # 8 CTAs: three chunks of 128 rows on the pieces; 4 CTAs on the FMA units: two chunks
+    case.solver.launch_shape(cluster=8 if units == "pieces" else 4, threads=512)
+    assert case.solver.tensor_pieces() == (3 if units == "pieces" else 0)
+    case.solver.set_debug(True)
+    for t in range(6):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, 1e-4)
+
+
 def test_adagrad_steps_and_state():
     case = Case(dims=[12, 10, 11], ranks=[2, 3, 2], J=40, prec=0, rule=ob.RULE_ADAGRAD, eta=0.02)
     case.solver.set_debug(True)
