@@ -89,6 +89,14 @@ __device__ __forceinline__ void cp_async_wait_pending(int n) {
   }
 }
 
+// Split cluster barrier (all threads of every CTA arrive once, then wait once).
+__device__ __forceinline__ void cluster_arrive_release() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait_acquire() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ float to_f32(float x) { return x; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
 
@@ -302,7 +310,156 @@ __global__ void __launch_bounds__(kMaxThreads)
     return g;
   };
 
+  // samples of this CTA (the same every iteration): CTAs cw0..C-1 share the J
+  // samples (with cw0 = 1 CTA 0 factorises the scaled variant's Gram matrix
+  // while the others work on them)
+  const int cr = c - lay.cw0, CWk = C - lay.cw0;
+  const int j0 = cr < 0 ? 0 : (int)((long long)J * cr / CWk), j1 = cr < 0 ? 0 : (int)((long long)J * (cr + 1) / CWk);
+  const int jb = j1 - j0, jb4 = (jb + 3) & ~3;
+  const int jbs = min(jb, lay.sbj);   // samples whose slices are staged at a time
+  const int L = N - 1;
+  // uniform draws depend on no core: the next iteration's draws and fiber
+  // copies overlap the tail of the current one (not while recording)
+  const bool pipe = D.dist == 0 && !rec;
+  bool fronted = false;   // this iteration's draws and fiber copies were issued by the previous one
+  long long pf_t = -1;    // >= 0: the chunk loop issues front(pf_t) once the fibers are consumed
   int cur_n = 0, cur_Q = 0, cur_jb = 0, cur_j0 = 0;
+  // Draws of iteration tt (A1/A2), the per-step order/offset table and the
+  // fiber copies (A3 issue; waited for after A4).  Called at the top of an
+  // iteration, or, for uniform sampling, by the previous iteration once its
+  // last chunk has consumed the fibers (its draws depend on no core).
+  // The group is threads [gbase, gbase + gsize) (whole warps): all threads, or
+  // the upper half while the lower half reduces; its barriers are named
+  // barrier 1 when it is not the whole CTA.
+  auto front = [&](long long tt, int gbase, int gsize) {
+    const long long t = tt;
+    const int tid = threadIdx.x - gbase, NT = gsize;
+    auto gsync = [&]() {
+      if (gsize == (int)blockDim.x) __syncthreads();
+      else asm volatile("bar.sync 1, %0;" ::"r"(gsize) : "memory");
+    };
+    const int n = draw_mode(D.seed, t, N);
+    const int In = I[n];
+    auto ring = [&](int q) {
+      const int k = n + 1 + q;
+      return k >= N ? k - N : k;
+    };
+    // staged slice layout: factor s at sb + soff[s], sample jl at + jl * qpad[s];
+    // written by the last thread here, read after the sampling barrier (the
+    // readers of the previous iteration finished several barriers ago)
+    if (tid == NT - 1) {   // the last thread: the sampling below starts at thread 0
+      int off = 0;
+      for (int q = 0; q < kMaxOrder; ++q) {
+        const int k = q < L ? ring(q) : 0;
+        const int qs = R[k] * R[k + 1 == N ? 0 : k + 1];
+        order[q] = k;
+        qpad[q] = (int)round_up((size_t)qs, 16 / sizeof(T));
+        soff[q] = off;
+        if (q < L) off += jbs * qpad[q];
+      }
+    }
+
+    // ---- A1/A2: per sample, slice indices (Algorithm 2), p_F (product in ring
+    // order), weight 1/(|F| J_n p_F) and fiber column -------------------------
+    // Uniform sampling: first one thread per (sample, factor) draws the index,
+    // then one thread per sample combines them (the draws are independent).
+    const bool uni_split = D.dist == 0;
+    if (uni_split) {
+      for (int e = tid; e < L * jb; e += NT) {
+        const int sp = e / jb, jl = e - sp * jb;
+        const int k = ring(sp);
+        const uint64_t u = draw_u64(D.seed, t, kStreamF, k, (uint32_t)(j0 + jl));
+        idx_s[jl * kMaxOrder + k] = (int)mulhi64(u, (uint64_t)I[k]);
+      }
+      gsync();
+    }
+    for (int jl = tid; jl < jb4; jl += NT) {
+      if (jl >= jb) {
+        wt_s[jl] = T(0);
+        continue;
+      }
+      const bool uni = D.dist == 0;
+      const bool need_pf = !uni || rec;   // uniform: every p_F = 1/J_n, weight 1/|F| (to rounding)
+      double pF = 1.0;
+      long long col = 0, st = 1;
+      if (D.dist == 3) {   // optimal distribution: indices and p_F drawn by the sampling kernels
+        for (int sp = 0; sp < L; ++sp) {
+          const int k = ring(sp);
+          const int i = __ldcg(D.ext_idx + (size_t)(j0 + jl) * N + k);
+          idx_s[jl * kMaxOrder + k] = i;
+          col += (long long)i * st;
+          st *= I[k];
+        }
+        pF = __ldcg(D.ext_pf + j0 + jl);
+      } else if (uni) {   // indices drawn above; p_F = prod 1/I_k (only when recorded)
+        for (int sp = 0; sp < L; ++sp) {
+          const int k = ring(sp);
+          if (need_pf) pF = __dmul_rn(pF, cst[k]);
+          col += (long long)idx_s[jl * kMaxOrder + k] * st;
+          st *= I[k];
+        }
+      } else {   // leverage / Euclidean: inverse-CDF draws, p_F in ring order
+        uint64_t us[kMaxOrder];
+#pragma unroll
+        for (int sp = 0; sp < kMaxOrder; ++sp)
+          us[sp] = (sp < L) ? draw_u64(D.seed, t, kStreamF, ring(sp), (uint32_t)(j0 + jl)) : 0ull;
+#pragma unroll
+        for (int sp = 0; sp < kMaxOrder; ++sp) {
+          if (sp >= L) break;
+          const int k = ring(sp), Ik = I[k];
+          const unsigned long long *cdf = D.cdf[k];
+          const uint64_t W = __ldcg(cdf + Ik - 1);
+          const int i = cdf_search(cdf, Ik, mulhi64(us[sp], W));
+          pF = __dmul_rn(pF, __ldcg(D.prob[k] + i));
+          idx_s[jl * kMaxOrder + k] = i;
+          col += (long long)i * st;
+          st *= Ik;
+        }
+      }
+      const double w = need_pf ? __ddiv_rn(1.0, __dmul_rn(cst[8 + n], pF)) : cst[16];
+      w_s[jl] = w;
+      wt_s[jl] = need_pf ? (T)w : wt_uni;
+      col_s[jl] = col;
+      if (rec) {
+        D.dbg_pf[j0 + jl] = pF;
+        for (int k = 0; k < N; ++k)
+          D.dbg_idx[(size_t)(j0 + jl) * N + k] = (k == n) ? -1 : idx_s[jl * kMaxOrder + k];
+      }
+    }
+    if (rec && c == 0 && tid == 0) *D.dbg_n = n;
+    gsync();
+
+    // ---- A3: gather the fibers into shared memory (waited for after A4) -----
+    // Long fibers by bulk copies (one per fiber, issued by warp 0, completing on
+    // an mbarrier); short fibers (and the slices, in A4) by 16-byte per-thread
+    // asynchronous copies, which issue faster than one small bulk copy each.
+    const uint32_t fbytes = (uint32_t)round_up((size_t)In * sizeof(XT), 16);
+    const bool fiber_tma = fbytes >= kTmaFiberBytes;
+    {
+      const XT *base = static_cast<const XT *>(D.xmode[n]);
+      const long long ldg = D.ldx[n];
+      if (fiber_tma) {
+        if (tid < 32 && jb > 0) {
+          if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)jb * fbytes);
+          __syncwarp();
+          fence_proxy_async_smem();
+          for (int jl = tid; jl < jb; jl += 32)
+            tma_load_1d(xs + (size_t)jl * lay.ldxs, base + col_s[jl] * ldg, fbytes, bar);
+        }
+      } else {
+        const int nch = (int)(fbytes / 16);
+        for (int e = tid; e < jb * nch; e += NT) {
+          const int jl = e / nch, ch = e - jl * nch;
+          cp_async16(reinterpret_cast<char *>(xs + (size_t)jl * lay.ldxs) + 16 * ch,
+                     reinterpret_cast<const char *>(base + col_s[jl] * ldg) + 16 * ch);
+        }
+      }
+      // pad fiber rows [jb, jb4) read as zeros by the partial-gradient GEMM
+      for (int e = tid; e < (jb4 - jb) * lay.ldxs; e += NT)
+        xs[(size_t)(jb + e / lay.ldxs) * lay.ldxs + e % lay.ldxs] = XT(0);
+    }
+  };
+
   // Tensor-core residual and partial gradient of one chunk of <= 128 rows of
   // G_n (operands split BF16, FP32 accumulation in TMEM):
   //   D_R(i, jl) = G(i, :) Z(jl, :)^T  as hi*hi + hi*lo + lo*hi,
@@ -456,141 +613,18 @@ __global__ void __launch_bounds__(kMaxThreads)
     const int n = draw_mode(D.seed, t, N);
     const int In = I[n], Rn = R[n], Rn1 = R[(n + 1) % N], Q = Rn * Rn1;
     const int Q4 = (Q + 3) & ~3;
-    const int L = N - 1;
-    // samples of this CTA: CTAs cw0..C-1 share the J samples (with cw0 = 1 CTA 0
-    // factorises the scaled variant's Gram matrix while the others work on them)
-    const int cr = c - lay.cw0, CWk = C - lay.cw0;
-    const int j0 = cr < 0 ? 0 : (int)((long long)J * cr / CWk), j1 = cr < 0 ? 0 : (int)((long long)J * (cr + 1) / CWk);
-    const int jb = j1 - j0, jb4 = (jb + 3) & ~3;
     cur_n = n;
     cur_Q = Q;
     cur_jb = jb;
     cur_j0 = j0;
-    // core of chain factor q (ring order n+1, ..., n-1), computed where the
-    // shared copy is not yet written
-    auto ring = [&](int q) {
-      const int k = n + 1 + q;
-      return k >= N ? k - N : k;
-    };
-    // staged slice layout: factor s at sb + soff[s], sample jl at + jl * qpad[s];
-    // written by thread 0 here, read after the sampling barrier (the previous
-    // step's readers finished several barriers ago)
-    const int jbs = min(jb, lay.sbj);   // samples whose slices are staged at a time
-    if (tid == NT - 1) {   // the last thread: the sampling below starts at thread 0
-      int off = 0;
-      for (int q = 0; q < kMaxOrder; ++q) {
-        const int k = q < L ? ring(q) : 0;
-        const int qs = R[k] * R[k + 1 == N ? 0 : k + 1];
-        order[q] = k;
-        qpad[q] = (int)round_up((size_t)qs, 16 / sizeof(T));
-        soff[q] = off;
-        if (q < L) off += jbs * qpad[q];
-      }
-    }
     const int all_k = (1 << N) - 1;
     const bool sl_async = ((D.slice_tma | (1 << n)) & all_k) == all_k;   // every factor's slices 16-byte rows
     T *Gn = static_cast<T *>(D.cores[n]);
     T *accn = static_cast<T *>(D.acc[n]);
-
-    // ---- A1/A2: per sample, slice indices (Algorithm 2), p_F (product in ring
-    // order), weight 1/(|F| J_n p_F) and fiber column -------------------------
-    // Uniform sampling: first one thread per (sample, factor) draws the index,
-    // then one thread per sample combines them (the draws are independent).
-    const bool uni_split = D.dist == 0;
-    if (uni_split) {
-      for (int e = tid; e < L * jb; e += NT) {
-        const int sp = e / jb, jl = e - sp * jb;
-        const int k = ring(sp);
-        const uint64_t u = draw_u64(D.seed, t, kStreamF, k, (uint32_t)(j0 + jl));
-        idx_s[jl * kMaxOrder + k] = (int)mulhi64(u, (uint64_t)I[k]);
-      }
-      __syncthreads();
-    }
-    for (int jl = tid; jl < jb4; jl += NT) {
-      if (jl >= jb) {
-        wt_s[jl] = T(0);
-        continue;
-      }
-      const bool uni = D.dist == 0;
-      const bool need_pf = !uni || rec;   // uniform: every p_F = 1/J_n, weight 1/|F| (to rounding)
-      double pF = 1.0;
-      long long col = 0, st = 1;
-      if (D.dist == 3) {   // optimal distribution: indices and p_F drawn by the sampling kernels
-        for (int sp = 0; sp < L; ++sp) {
-          const int k = ring(sp);
-          const int i = __ldcg(D.ext_idx + (size_t)(j0 + jl) * N + k);
-          idx_s[jl * kMaxOrder + k] = i;
-          col += (long long)i * st;
-          st *= I[k];
-        }
-        pF = __ldcg(D.ext_pf + j0 + jl);
-      } else if (uni) {   // indices drawn above; p_F = prod 1/I_k (only when recorded)
-        for (int sp = 0; sp < L; ++sp) {
-          const int k = ring(sp);
-          if (need_pf) pF = __dmul_rn(pF, cst[k]);
-          col += (long long)idx_s[jl * kMaxOrder + k] * st;
-          st *= I[k];
-        }
-      } else {   // leverage / Euclidean: inverse-CDF draws, p_F in ring order
-        uint64_t us[kMaxOrder];
-#pragma unroll
-        for (int sp = 0; sp < kMaxOrder; ++sp)
-          us[sp] = (sp < L) ? draw_u64(D.seed, t, kStreamF, ring(sp), (uint32_t)(j0 + jl)) : 0ull;
-#pragma unroll
-        for (int sp = 0; sp < kMaxOrder; ++sp) {
-          if (sp >= L) break;
-          const int k = ring(sp), Ik = I[k];
-          const unsigned long long *cdf = D.cdf[k];
-          const uint64_t W = __ldcg(cdf + Ik - 1);
-          const int i = cdf_search(cdf, Ik, mulhi64(us[sp], W));
-          pF = __dmul_rn(pF, __ldcg(D.prob[k] + i));
-          idx_s[jl * kMaxOrder + k] = i;
-          col += (long long)i * st;
-          st *= Ik;
-        }
-      }
-      const double w = need_pf ? __ddiv_rn(1.0, __dmul_rn(cst[8 + n], pF)) : cst[16];
-      w_s[jl] = w;
-      wt_s[jl] = need_pf ? (T)w : wt_uni;
-      col_s[jl] = col;
-      if (rec) {
-        D.dbg_pf[j0 + jl] = pF;
-        for (int k = 0; k < N; ++k)
-          D.dbg_idx[(size_t)(j0 + jl) * N + k] = (k == n) ? -1 : idx_s[jl * kMaxOrder + k];
-      }
-    }
-    if (rec && c == 0 && tid == 0) *D.dbg_n = n;
-    __syncthreads();
-
-    // ---- A3: gather the fibers into shared memory (waited for after A4) -----
-    // Long fibers by bulk copies (one per fiber, issued by warp 0, completing on
-    // an mbarrier); short fibers (and the slices, in A4) by 16-byte per-thread
-    // asynchronous copies, which issue faster than one small bulk copy each.
     const uint32_t fbytes = (uint32_t)round_up((size_t)In * sizeof(XT), 16);
     const bool fiber_tma = fbytes >= kTmaFiberBytes;
-    {
-      const XT *base = static_cast<const XT *>(D.xmode[n]);
-      const long long ldg = D.ldx[n];
-      if (fiber_tma) {
-        if (tid < 32 && jb > 0) {
-          if (tid == 0) mbar_arrive_expect_tx(bar, (uint32_t)jb * fbytes);
-          __syncwarp();
-          fence_proxy_async_smem();
-          for (int jl = tid; jl < jb; jl += 32)
-            tma_load_1d(xs + (size_t)jl * lay.ldxs, base + col_s[jl] * ldg, fbytes, bar);
-        }
-      } else {
-        const int nch = (int)(fbytes / 16);
-        for (int e = tid; e < jb * nch; e += NT) {
-          const int jl = e / nch, ch = e - jl * nch;
-          cp_async16(reinterpret_cast<char *>(xs + (size_t)jl * lay.ldxs) + 16 * ch,
-                     reinterpret_cast<const char *>(base + col_s[jl] * ldg) + 16 * ch);
-        }
-      }
-      // pad fiber rows [jb, jb4) read as zeros by the partial-gradient GEMM
-      for (int e = tid; e < (jb4 - jb) * lay.ldxs; e += NT)
-        xs[(size_t)(jb + e / lay.ldxs) * lay.ldxs + e % lay.ldxs] = XT(0);
-    }
+    if (!fronted) front(t, 0, NT);
+    fronted = false;
 
     // ---- A4: sampled subchain rows, Z(j, r + r' R_n) = P_j(r', r) ----------
     if (lay.sb_ok) {
@@ -887,6 +921,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     const int ldg = lay.ldg;
     for (int i0 = 0; i0 < In; i0 += lay.TI) {
       const int ti = min(lay.TI, In - i0);
+      pf_t = (pipe && i0 + ti >= In && s + 1 < nsteps) ? t + 1 : -1;
       if (c < lay.cw0) {   // no samples on this CTA: a zero partial gradient
         for (int e = tid; e < ti * Q; e += NT) reg[(size_t)(e / Q) * ldq + e % Q] = T(0);
       } else {
@@ -930,7 +965,22 @@ __global__ void __launch_bounds__(kMaxThreads)
                                    [=](int ii, int q, T v) { reg[(size_t)ii * ldq + q] = v; });
         }
       }
-      cluster.sync();
+      // Last chunk of a pipelined iteration: every thread arrives (its partial
+      // gradient released); the upper half of the CTA then issues the next
+      // iteration's draws and fiber copies while the lower half waits, reduces
+      // and updates; the halves meet at the closing cluster barrier.
+      const bool split = pf_t >= 0;
+      const int rt = split ? NT / 2 : NT;   // threads of the reduction
+      if (split) {
+        if constexpr (!kTC) __syncthreads();   // the SIMT gradient GEMM's reads of xs are done
+        cluster_arrive_release();
+        if (tid >= rt) front(pf_t, rt, NT - rt);
+        cluster_wait_acquire();
+        fronted = true;
+      } else {
+        cluster.sync();
+      }
+      pf_t = -1;
       const int r0 = ti * c / C, r1 = ti * (c + 1) / C;
       // reduced gradient of one owned entry -> step rule and update (or kept for the solve)
       auto own_entry = [&](int ii, int q, T g) {
@@ -955,7 +1005,7 @@ __global__ void __launch_bounds__(kMaxThreads)
           // sums in that fixed order (deterministic), so that the owners' requests
           // spread over all CTAs instead of all hitting CTA 0 first
           const int Qv = Q >> 2;
-          for (int e = tid; e < (r1 - r0) * Qv; e += NT) {
+          for (int e = tid; tid < rt && e < (r1 - r0) * Qv; e += rt) {
             const int ii = r0 + e / Qv, q0 = (e - (e / Qv) * Qv) * 4;
             float4 v[16];
 #pragma unroll
@@ -979,13 +1029,13 @@ __global__ void __launch_bounds__(kMaxThreads)
             own_entry(ii, q0 + 3, g.w);
           }
         } else {
-          for (int e = tid; e < (r1 - r0) * Q; e += NT) {
+          for (int e = tid; tid < rt && e < (r1 - r0) * Q; e += rt) {
             const int ii = r0 + e / Q, q = e % Q;
             own_entry(ii, q, cluster_sum(reg, (size_t)ii * ldq + q));
           }
         }
       } else {
-        for (int e = tid; e < (r1 - r0) * Q; e += NT) {
+        for (int e = tid; tid < rt && e < (r1 - r0) * Q; e += rt) {
           const int ii = r0 + e / Q, q = e % Q;
           own_entry(ii, q, cluster_sum(reg, (size_t)ii * ldq + q));
         }
