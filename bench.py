@@ -394,6 +394,47 @@ def run_extras(args, device):
         out["paper_experiment_shapes"] = run_paper_shapes(args, device)
     except Exception as e:
         out["paper_shapes_error"] = repr(e)
+    try:
+        out["experiment_2"] = run_exp2(args, device)
+    except Exception as e:
+        out["experiment_2_error"] = repr(e)
+    return out
+
+
+def run_exp2(args, device):
+    """Experiment II of Sec. 4 at 300^3 (dims unstated in the paper): for each
+    condition number kappa in {1e2, 1e4, 1e6}, TR-BRSGD (alpha 5e-4) and
+    TR-ScaledBRSGD (alpha 9e-2, |H| = 1200), each with the uniform, Euclidean
+    and leverage distributions, |F| = 200, R = 5, run for a wall-clock budget
+    (the paper's MT = 10 s; `--exp2-seconds`) from the same initial cores:
+    iterations done and the RSE reached (or the error a diverging run raised)."""
+    import torch
+
+    from paper_2303_16492_gb300 import api, synth
+    out = {"seconds_per_run": args.exp2_seconds}
+    for base in synth.EXP2_WORKLOADS:
+        w = synth.workload(base)
+        X, Xtrue, init = device_problem(w, device)
+        res = {}
+        for variant_name in (base, base + "-s"):
+            wv = synth.workload(variant_name)
+            for dist_name, dist in (("U", 0), ("E", 2), ("L", 1)):
+                label = ("TR-ScaledBRSGD-" if wv.variant else "TR-BRSGD-") + dist_name
+                pc = api.ProblemConfig(dims=wv.dims, ranks=wv.ranks, J=wv.J, prec=1, alpha=wv.alpha,
+                                       variant=wv.variant, J_H=wv.JH, dist=dist, seed=wv.seed + 3)
+                s = api.Solver([pc], [X], [[c.clone() for c in init]])
+                try:
+                    t0 = time.perf_counter()
+                    done, _ = s.run(0, 10**9, chunk=250, max_seconds=args.exp2_seconds)
+                    torch.cuda.synchronize()
+                    sec = time.perf_counter() - t0
+                    res[label] = {"iterations": int(done), "seconds": round(sec, 3),
+                                  "rse": s.rel_error(0, Xtrue)}
+                except Exception as e:
+                    res[label] = {"error": repr(e)}
+                s.close()
+        out[f"kappa={1.0 / w.smin:.0e}"] = res
+        del X, Xtrue, init
     return out
 
 
@@ -657,6 +698,8 @@ def main():
     ap.add_argument("--extras", action=argparse.BooleanOptionalAction, default=True)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--time-to-rse", action=argparse.BooleanOptionalAction, default=True)
+    ap.add_argument("--exp2-seconds", type=float, default=0.25,
+                    help="wall-clock budget per run of the Experiment II sweep in the extras (the paper: 10)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

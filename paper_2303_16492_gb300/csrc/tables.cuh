@@ -68,9 +68,14 @@ __host__ __device__ inline size_t leverage_scratch_bytes(int I, int Q, size_t el
 // leverage scores): p(i) = l_i(A) / rank(A), A = G_{(2)} (I x Q).
 //   I > Q: l_i = || L^{-1} a_i^T ||^2 with A^T A = L L^T;
 //   I <= Q: A A^T = L L^T exists (full row rank), so every l_i = 1.
-// Gram and factor in the core precision, l_i accumulated in FP64.  A failed
-// factorisation (rank-deficient core) latches TRSGD_ENUMERIC and leaves the
-// table unchanged.  `smem` holds leverage_scratch_bytes(I, Q, sizeof(T)).
+// Gram and factor in the core precision, l_i accumulated in FP64.  If the
+// factorisation fails (a core numerically rank-deficient in that precision),
+// it is retried with a ridge shift delta = 1e-7 tr(M)/m * 10^a, a = 0..6, on
+// the diagonal; the resulting ridge leverage scores are normalised by their
+// sum, so the table stays exactly the distribution that is sampled (and the
+// weights 1/p stay unbiased).  If every shift fails, TRSGD_ENUMERIC is
+// latched and the table is left unchanged.  `smem` holds
+// leverage_scratch_bytes(I, Q, sizeof(T)).
 template <typename T>
 __device__ void leverage_table_cta(const T *G, int I, int Q, unsigned char *smem, double *prob,
                                    unsigned long long *cdf, int *status) {
@@ -90,12 +95,23 @@ __device__ void leverage_table_cta(const T *G, int I, int Q, unsigned char *smem
     As[e] = (i < I && q < Q) ? ld_l2(G + (size_t)i * Q + q) : T(0);
   }
   __syncthreads();
-  if (tall)   // M = A^T A, contraction over the rows i (zero rows pad I to I4)
-    gemm_s<4, true, true, T>(Q, Q, I, As, lda, As, lda, nullptr, [=](int a, int b, T v) { M[a * m4 + b] = v; });
-  else        // M = A A^T, contraction over the columns q (zero columns pad Q to Q4)
-    gemm_s<4, false, false, T>(I, I, Q, As, lda, As, lda, nullptr, [=](int a, int b, T v) { M[a * m4 + b] = v; });
-  __syncthreads();
-  const bool ok = cholesky_cta_t<T>(M, m, m4);
+  bool ok = false, ridge = false;
+  for (int attempt = 0; attempt < 8 && !ok; ++attempt) {
+    if (tall)   // M = A^T A, contraction over the rows i (zero rows pad I to I4)
+      gemm_s<4, true, true, T>(Q, Q, I, As, lda, As, lda, nullptr, [=](int a, int b, T v) { M[a * m4 + b] = v; });
+    else        // M = A A^T, contraction over the columns q (zero columns pad Q to Q4)
+      gemm_s<4, false, false, T>(I, I, Q, As, lda, As, lda, nullptr, [=](int a, int b, T v) { M[a * m4 + b] = v; });
+    __syncthreads();
+    if (attempt > 0) {   // ridge shift (every thread forms the same trace)
+      double tr = 0.0;
+      for (int k = 0; k < m; ++k) tr += (double)M[k * m4 + k];
+      const T delta = (T)(1e-7 * tr / m * pow(10.0, (double)(attempt - 1)));
+      __syncthreads();
+      for (int k = tid; k < m; k += NT) M[k * m4 + k] += delta;
+      ridge = true;
+    }
+    ok = cholesky_cta_t<T>(M, m, m4);
+  }
   if (!ok) {
     if (tid == 0 && status) atomicCAS(status, 0, 4);
     __syncthreads();
@@ -119,6 +135,18 @@ __device__ void leverage_table_cta(const T *G, int I, int Q, unsigned char *smem
     for (int i = tid; i < I; i += NT) lev[i] = __ddiv_rn(1.0, (double)I);
   }
   __syncthreads();
+  if (ridge) {   // ridge scores sum to less than the rank: normalise by their sum
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int i = 0; i < I; ++i) tot = __dadd_rn(tot, lev[i]);
+      wsc[0] = (unsigned long long)__double_as_longlong(tot);
+    }
+    __syncthreads();
+    const double tot = __longlong_as_double((long long)wsc[0]);
+    __syncthreads();
+    for (int i = tid; i < I; i += NT) lev[i] = __ddiv_rn(lev[i], tot);
+    __syncthreads();
+  }
   write_cdf_cta(lev, I, prob, cdf, wsc);
 }
 

@@ -142,8 +142,20 @@ def workload(name: str) -> Workload:
             return Workload(name, dims, [R] * 3, 200, "illcond", smin=1e-2, noise_rel=0.05, alpha=a_scaled,
                             prec=1, variant=1, JH=1000)
         return Workload(name, dims, [R] * 3, 200, "illcond", smin=1e-2, noise_rel=0.05, alpha=a_plain, prec=1)
+    # Experiment II (Sec. 4): G_{n(2)} = U_n S V^T with condition number kappa in
+    # {1e2, 1e4, 1e6}, R = 5, |F| = 200, noiseless; the dims are not stated (300^3
+    # here); plain alpha 5e-4; scaled (-s) alpha 9e-2 with |H| = 1200
+    kap = {"e2-k2": 1e2, "e2-k4": 1e4, "e2-k6": 1e6}
+    if base in kap:
+        if name.endswith("-s"):
+            return Workload(name, [300] * 3, [5] * 3, 200, "illcond", smin=1.0 / kap[base], noise_rel=0.0,
+                            alpha=9e-2, prec=1, variant=1, JH=1200)
+        return Workload(name, [300] * 3, [5] * 3, 200, "illcond", smin=1.0 / kap[base], noise_rel=0.0,
+                        alpha=5e-4, prec=1)
     raise KeyError(name)
 
+
+EXP2_WORKLOADS = ["e2-k2", "e2-k4", "e2-k6"]
 
 NEXT_WORKLOADS = ["e1", "e1s", "e1s4", "hsi-salinas", "hsi-salinas-s", "hsi-indian", "hsi-indian-s",
                   "hsi-pavia", "hsi-pavia-s"]

@@ -286,3 +286,47 @@ def test_paper_experiment_shapes(name):
         for k in range(N):
             assert rel(cores_d[k].double().cpu().numpy(), tr.unfold2(st.cores[k])) < tol
     s.close()
+
+
+@pytest.mark.parametrize("name,dist", [("e2-k6", ob.DIST_LEVERAGE), ("e2-k6-s", ob.DIST_EUCLIDEAN),
+                                       ("e2-k2-s", ob.DIST_UNIFORM)])
+def test_experiment_2_shapes(name, dist):
+    """Experiment II (Sec. 4) at 300^3: ill-conditioned U S V^T cores with
+    condition number 1e6 or 1e2, R = 5, |F| = 200, plain and scaled with
+    |H| = 1200, with non-uniform distributions built from the same cores on
+    both sides.  Two iterations from shared cores; indices bit-exact; p_F
+    bit-exact (Euclidean, uniform) or to 1e-5 (leverage of float cores: the
+    device's Gram and Cholesky in the core precision against the oracle's
+    SVD, about 1e-7 apart); intermediates within the FP32 bound."""
+    A = api()
+    w, P, Xo, Xd, init = _problem(A, name)
+    N, J = 3, w.J
+    cores_d = [torch.from_numpy(G).cuda() for G in init]
+    pc = A.ProblemConfig(dims=w.dims, ranks=w.ranks, J=J, prec=1, alpha=w.alpha, variant=w.variant, J_H=w.JH,
+                         dist=dist, seed=w.seed + 3)
+    s = A.Solver([pc], [Xd], [cores_d])
+    s.set_debug(True)
+    st = ob.State.new(to_oracle_cores([G.astype(np.float64) for G in init], w.ranks))
+    cfg = ob.Config(J=J, alpha=w.alpha, variant=w.variant, J_H=w.JH, dist=dist, seed=w.seed + 3)
+    tol = 1e-4 if w.variant == 1 else 2e-5
+    for t in range(2):
+        for k in range(N):
+            st.cores[k] = tr.fold2(cores_d[k].double().cpu().numpy(), w.ranks[k], w.ranks[(k + 1) % N])
+        rec = ob.step(st, Xo, cfg, t)
+        s.step(t)
+        n, In, Q = rec["n"], w.dims[rec["n"]], w.ranks[rec["n"]] * w.ranks[(rec["n"] + 1) % N]
+        np.testing.assert_array_equal(s.get_debug(A._abi.DBG_IDX, np.int32, J * N).reshape(J, N), rec["idx"])
+        pf = s.get_debug(A._abi.DBG_PF, np.float64, J)
+        if dist == ob.DIST_LEVERAGE:
+            np.testing.assert_allclose(pf, rec["pF"], rtol=1e-5)
+        else:
+            np.testing.assert_array_equal(pf, rec["pF"])
+        assert rel(s.get_debug(A._abi.DBG_Z, np.float32, J * Q).reshape(J, Q), rec["Z"]) < tol
+        assert rel(s.get_debug(A._abi.DBG_E, np.float32, J * In).reshape(J, In).T, rec["E"]) < tol
+        # the weights 1 / (|F| J_n p_F) carry the leverage scores' ~1e-7 into g
+        assert rel(s.get_debug(A._abi.DBG_G, np.float32, In * Q).reshape(In, Q), rec["g"]) < tol
+        if w.variant == 1:
+            assert rel(s.get_debug(A._abi.DBG_H, np.float64, Q * Q).reshape(Q, Q), rec["h"]) < tol
+        for k in range(N):
+            assert rel(cores_d[k].double().cpu().numpy(), tr.unfold2(st.cores[k])) < tol
+    s.close()

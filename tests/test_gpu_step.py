@@ -217,6 +217,30 @@ def test_scaled_variant_row_chunks(units, J_H):
         _compare_step(case, rec, 1e-4)
 
 
+@pytest.mark.parametrize("prec,J_H", [(0, 0), (0, 70), (1, 70)])
+def test_scaled_variant_leverage(prec, J_H):
+    """Scaled variant with leverage-score sampling (Lemma lev_est) for F and
+    the Hessian batch: tall cores (I_1 = 300 rows in three chunks of the
+    tensor-core path, Q = 25), the weights 1 / (|H| J_n p_H) in h."""
+    case = Case(dims=[300, 30, 28], ranks=[5, 5, 5], J=60, prec=prec, alpha=0.09, variant=ob.VARIANT_SCALED,
+                J_H=J_H, dist=ob.DIST_LEVERAGE)
+    case.solver.set_debug(True)
+    tol = 1e-10 if prec == 0 else 1e-4
+    for t in range(8):
+        for k, G in enumerate(case.device_cores()):
+            case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        d = case.debug(rec["n"])
+        np.testing.assert_array_equal(d["idx"], rec["idx"])
+        np.testing.assert_allclose(d["pF"], rec["pF"], rtol=1e-12 if prec == 0 else 1e-5)
+        assert rel(d["g"], rec["g"]) < tol
+        assert rel(d["h"], rec["h"]) < tol
+        assert rel(d["p"], rec["p"]) < tol
+        for G, O in zip(case.device_cores(), case.state.cores):
+            assert rel(G, O) < tol
+
+
 def test_adagrad_steps_and_state():
     case = Case(dims=[12, 10, 11], ranks=[2, 3, 2], J=40, prec=0, rule=ob.RULE_ADAGRAD, eta=0.02)
     case.solver.set_debug(True)
