@@ -199,7 +199,6 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, StepLayout &L) 
   L.off_desc = take(rup(sizeof(ProbDesc), 16), 16);
   L.off_idx = take((size_t)L.JB * kMaxOrder * 4, 16);
   L.off_col = take((size_t)L.JB * 8, 16);
-  L.off_w = take((size_t)L.JB * 8, 16);
   L.off_wt = take(JB4 * st, 16);
   L.off_x = take(JB4 * L.ldxs * (tc ? sx : std::max(sx, st)), 128);
   L.off_z = take(JB4 * L.ldq * st, 128);

@@ -89,38 +89,6 @@ __device__ __forceinline__ void chain_row(const T *const *cores, const int *R, i
   }
 }
 
-// Same chain with every sampled slice already staged in shared memory:
-// factor s of sample jl at sb + soff[s] + jl * qpad[s] (column-major).
-template <int RMAX, typename T>
-__device__ __forceinline__ void chain_row_staged(const T *sb, const int *soff, const int *qpad,
-                                                 const int *R, int N, const int *order, int L, int jl,
-                                                 int rp, T (&row)[RMAX]) {
-  int k = order[0];
-  int Ra = R[k], Rb = R[(k + 1) % N];
-  const T *S = sb + soff[0] + (size_t)jl * qpad[0];
-#pragma unroll
-  for (int b = 0; b < RMAX; ++b) row[b] = (b < Rb) ? S[rp + b * Ra] : T(0);
-  for (int s = 1; s < L; ++s) {
-    k = order[s];
-    Ra = R[k];
-    Rb = R[(k + 1) % N];
-    S = sb + soff[s] + (size_t)jl * qpad[s];
-    T nrow[RMAX];
-#pragma unroll
-    for (int b = 0; b < RMAX; ++b) {
-      T acc = T(0);
-      if (b < Rb) {
-#pragma unroll
-        for (int a = 0; a < RMAX; ++a)
-          if (a < Ra) acc = fma(row[a], S[a + b * Ra], acc);
-      }
-      nrow[b] = acc;
-    }
-#pragma unroll
-    for (int b = 0; b < RMAX; ++b) row[b] = nrow[b];
-  }
-}
-
 }  // namespace trsgd
 
 namespace trsgd {
@@ -229,46 +197,6 @@ __device__ __noinline__ void gemm_s(int M, int N, int K, const T *__restrict__ A
 #pragma unroll
       for (int b = 0; b < TN; ++b)
         if (m0 + a < M && nv[b]) epi(m0 + a, n0 + 32 * b, acc[a][b]);
-  }
-}
-
-// Slice chain over staged slices with loops that stop at the actual ranks
-// (no predicated-off work for ranks below RMAX).
-template <int RMAX, typename T>
-__device__ __forceinline__ void chain_row_staged2(const T *sb, const int *soff, const int *qpad,
-                                                  const int *R, int N, const int *order, int L,
-                                                  int jl, int rp, T (&row)[RMAX]) {
-  int k = order[0];
-  int Ra = R[k], Rb = R[(k + 1) % N];
-  const T *S = sb + soff[0] + (size_t)jl * qpad[0];
-#pragma unroll
-  for (int b = 0; b < RMAX; ++b) {
-    if (b >= Rb) break;
-    row[b] = S[rp + b * Ra];
-  }
-  for (int s = 1; s < L; ++s) {
-    k = order[s];
-    Ra = R[k];
-    Rb = R[(k + 1) % N];
-    S = sb + soff[s] + (size_t)jl * qpad[s];
-    T nrow[RMAX];
-#pragma unroll
-    for (int b = 0; b < RMAX; ++b) {
-      if (b >= Rb) break;
-      const T *col = S + b * Ra;
-      T acc = T(0);
-#pragma unroll
-      for (int a = 0; a < RMAX; ++a) {
-        if (a >= Ra) break;
-        acc = fma(row[a], col[a], acc);
-      }
-      nrow[b] = acc;
-    }
-#pragma unroll
-    for (int b = 0; b < RMAX; ++b) {
-      if (b >= Rb) break;
-      row[b] = nrow[b];
-    }
   }
 }
 

@@ -54,7 +54,7 @@ struct StepLayout {
   int tcp;        // BF16 pieces per tensor-core operand: 2 (BF16-mixed), 3 (FP32), 0 (FMA units)
   // off_sb aliases the region [off_reg, total): the staged slices are dead
   // before the Gram / chunk buffers and the CDF scratch are written
-  size_t off_desc, off_idx, off_col, off_w, off_wt, off_bar, off_x, off_z, off_reg, off_h64,
+  size_t off_desc, off_idx, off_col, off_wt, off_bar, off_x, off_z, off_reg, off_h64,
       off_hdiag, off_gown, off_misc, off_const, off_sb, off_p0, off_p1, off_zp[3], off_ew, off_ord,
       off_hz, off_hidx, off_hw, total;
   int JBH;        // max Hessian-batch samples per CTA

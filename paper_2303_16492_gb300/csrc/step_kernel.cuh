@@ -227,7 +227,6 @@ __global__ void __launch_bounds__(kMaxThreads)
   ProbDesc *desc_s = reinterpret_cast<ProbDesc *>(smem + lay.off_desc);
   int *idx_s = reinterpret_cast<int *>(smem + lay.off_idx);
   long long *col_s = reinterpret_cast<long long *>(smem + lay.off_col);
-  double *w_s = reinterpret_cast<double *>(smem + lay.off_w);
   T *wt_s = reinterpret_cast<T *>(smem + lay.off_wt);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + lay.off_bar);
   XT *xs = reinterpret_cast<XT *>(smem + lay.off_x);
@@ -417,7 +416,6 @@ __global__ void __launch_bounds__(kMaxThreads)
         }
       }
       const double w = need_pf ? __ddiv_rn(1.0, __dmul_rn(cst[8 + n], pF)) : cst[16];
-      w_s[jl] = w;
       wt_s[jl] = need_pf ? (T)w : wt_uni;
       col_s[jl] = col;
       if (rec) {
@@ -492,7 +490,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         const float *grow = reinterpret_cast<const float *>(Gn) + (size_t)(i0 + (live ? ii : 0)) * Q;
         float v[8];
         if (g16) {
-  #pragma unroll
+#pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int q = qb * 8 + 4 * h;
             const float4 f = (live && q < Q) ? __ldcg(reinterpret_cast<const float4 *>(grow + q))
@@ -503,7 +501,7 @@ __global__ void __launch_bounds__(kMaxThreads)
             v[4 * h + 3] = f.w;
           }
         } else {
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int q = qb * 8 + j;
             v[j] = (live && q < Q) ? __ldcg(grow + q) : 0.f;
@@ -512,10 +510,10 @@ __global__ void __launch_bounds__(kMaxThreads)
         uint4 w[NPC > 0 ? NPC : 1];
         bf16_split8<NPC>(v, w);
         const uint32_t o = kmaj_off(ii, qb * 8, QC);
-  #pragma unroll
+#pragma unroll
         for (int k = 0; k < NPC; ++k) *reinterpret_cast<uint4 *>(gp[k] + o) = w[k];
         if (stash && ii >= r0 && ii < r1) {   // FP32 values of the rows this CTA updates
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < 8; ++j)
             if (qb * 8 + j < Q) gown[(size_t)(ii - r0) * ldq + qb * 8 + j] = v[j];
         }
@@ -532,9 +530,9 @@ __global__ void __launch_bounds__(kMaxThreads)
         // piece products of total order < NPC, in the order (0,0), (0,1), ..
         for (int kb = 0; kb < KQ / 16; ++kb) {
           const uint32_t ko = (uint32_t)kb * 256;
-  #pragma unroll
+#pragma unroll
           for (int a = 0; a < NPC; ++a)
-  #pragma unroll
+#pragma unroll
             for (int b = 0; a + b < NPC; ++b)
               umma_bf16(tbase, umma_desc(smem_u32(gp[a]) + ko, 128, sbo), umma_desc(smem_u32(zp[b]) + ko, 128, sbo),
                         idr, kb > 0 || a > 0 || b > 0);
@@ -553,7 +551,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         tmem_ld8(tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(c8 * 8), v);
         if (row < ti) {
           float ev[8];
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int jl = c8 * 8 + j;
             ev[j] = 0.f;
@@ -567,7 +565,7 @@ __global__ void __launch_bounds__(kMaxThreads)
           uint4 w[EWP];
           bf16_split8<EWP>(ev, w);
           const uint32_t o = kmaj_off(row, c8 * 8, JC);
-  #pragma unroll
+#pragma unroll
           for (int k = 0; k < EWP; ++k) *reinterpret_cast<uint4 *>(ewp[k] + o) = w[k];
         }
       }
@@ -580,9 +578,9 @@ __global__ void __launch_bounds__(kMaxThreads)
         const uint32_t idp = umma_idesc_bf16(128, NP, 0, 1);
         // Ew pieces x Z pieces of total order < EWP (BF16-mixed: Ew x Z_hi)
         for (int kb = 0; kb < NR / 16; ++kb) {
-  #pragma unroll
+#pragma unroll
           for (int a = 0; a < EWP; ++a)
-  #pragma unroll
+#pragma unroll
             for (int b = 0; a + b < EWP; ++b)
               umma_bf16(tbase + 256, umma_desc(smem_u32(ewp[a]) + (uint32_t)kb * 256, 128, (uint32_t)JC * 128),
                         umma_desc(smem_u32(zp[b]) + (uint32_t)kb * 2 * QC * 128, (uint32_t)QC * 128, 128), idp,
@@ -597,7 +595,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         float v[8];
         tmem_ld8(tbase + 256 + ((uint32_t)(32 * qd) << 16) + (uint32_t)(c8 * 8), v);
         if (row < ti) {
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int q = c8 * 8 + j;
             if (q < Q) reg[(size_t)row * lay.ldq + q] = v[j];
@@ -649,7 +647,7 @@ __global__ void __launch_bounds__(kMaxThreads)
                          reinterpret_cast<const char *>(G + (size_t)idg[jl * kMaxOrder + k] * qs) + 16 * ch);
             }
           } else {
-  #pragma unroll 4
+#pragma unroll 4
             for (int e = tid; e < jbc * qs; e += NT) {
               const int jl = e / qs, off = e - jl * qs;
               sb[soff[q] + (size_t)jl * qpad[q] + off] = ld_l2(G + (size_t)idg[jl * kMaxOrder + k] * qs + off);
@@ -687,7 +685,7 @@ __global__ void __launch_bounds__(kMaxThreads)
           if (!done) {
             // general ranks: this lane's entries it = lane + 32 u, row r' and column b
             int pofs[8], pstep[8], sofs[8], dofs[8];
-  #pragma unroll
+#pragma unroll
             for (int u = 0; u < 8; ++u) {
               const int it = lane + 32 * u;
               const int rp = it / Rb, bb = it - rp * Rb;
@@ -700,7 +698,7 @@ __global__ void __launch_bounds__(kMaxThreads)
               const T *prow = src + (size_t)jl * sstride;
               const T *S = sb + soff[q] + (size_t)jl * qpad[q];
               T *drow = dst + (size_t)jl * dstride;
-  #pragma unroll
+#pragma unroll
               for (int u = 0; u < 8; ++u) {
                 if (lane + 32 * u < per) {
                   const T *pp = prow + pofs[u];
@@ -936,7 +934,7 @@ __global__ void __launch_bounds__(kMaxThreads)
                          reinterpret_cast<const char *>(Gn + (size_t)(i0 + ii) * Q) + 16 * ch);
             }
           } else {
-    #pragma unroll 4
+#pragma unroll 4
             for (int e = tid; e < ti * Q; e += NT) {
               const int ii = e / Q, q = e - ii * Q;
               gs[(size_t)ii * ldg + q] = ld_l2(Gn + (size_t)(i0 + ii) * Q + q);

@@ -241,6 +241,37 @@ def test_scaled_variant_leverage(prec, J_H):
             assert rel(G, O) < tol
 
 
+def test_leverage_table_of_rank_deficient_core():
+    """A tall float core whose columns are all equal (rank 1): its Gram cannot
+    be factored, so the leverage table is rebuilt from ridge-shifted Grams and
+    normalised.  The run goes on without a numerical error latched, every
+    drawn index is in range with a positive, finite p_F, and the cores stay
+    finite."""
+    A = api()
+    dims, ranks, J = [40, 9, 10], [4, 4, 4], 64
+    rng = np.random.default_rng(3)
+    X = torch.from_numpy(rng.standard_normal(int(np.prod(dims))).astype(np.float32)).cuda()
+    cores = [torch.from_numpy((rng.standard_normal((dims[k], ranks[k] * ranks[(k + 1) % 3])) * 0.3)
+                              .astype(np.float32)).cuda() for k in range(3)]
+    cores[0][:] = cores[0][:, :1]          # every column equal: A^T A has rank 1
+    pc = A.ProblemConfig(dims=dims, ranks=ranks, J=J, prec=1, alpha=1e-3, dist=ob.DIST_LEVERAGE, seed=5)
+    s = A.Solver([pc], [X], [cores])
+    s.set_debug(True)
+    for t in range(12):
+        s.step(t)
+        torch.cuda.synchronize()
+        n = int(s.get_debug(A._abi.DBG_MODE, np.int32, 1)[0])
+        idx = s.get_debug(A._abi.DBG_IDX, np.int32, J * 3).reshape(J, 3)
+        pf = s.get_debug(A._abi.DBG_PF, np.float64, J)
+        assert np.all(pf > 0) and np.all(np.isfinite(pf))
+        for k in range(3):
+            if k != n:
+                assert np.all((idx[:, k] >= 0) & (idx[:, k] < dims[k]))
+    for c in cores:
+        assert torch.isfinite(c).all()
+    s.close()
+
+
 def test_adagrad_steps_and_state():
     case = Case(dims=[12, 10, 11], ranks=[2, 3, 2], J=40, prec=0, rule=ob.RULE_ADAGRAD, eta=0.02)
     case.solver.set_debug(True)
