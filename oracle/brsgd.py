@@ -347,6 +347,23 @@ def run(state: State, X, cfg: Config, T: int, t0: int = 0, X_ref=None, eval_ever
 # Full-batch baselines used only as pins (Sec. 3.1 and 3.3)
 # --------------------------------------------------------------------------
 
+def gd_step(cores, X, alpha, scaled=False, damping=0.0):
+    """One iteration of the full-gradient methods of Sec. 3, every core from
+    the same iterate: TR-GD, G_{n(2)} <- G_{n(2)} - alpha grad_n (the update
+    after Eq. gradient), or TR-ScaledGD (Eq. scaled_gd), grad_n multiplied by
+    (Z^T Z + damping I)^{-1}, Z = G^{!=n}_{[2]}.  Returns the new cores."""
+    new = []
+    for n in range(len(cores)):
+        grad = tr.full_gradient(cores, X, n)
+        if scaled:
+            Z = tr.subchain_unfold(cores, n)
+            L, _ = cholesky_damped(Z.T @ Z, damping)
+            grad = np.linalg.solve(L.T, np.linalg.solve(L, grad.T)).T
+        G2 = tr.unfold2(cores[n]) - alpha * grad
+        new.append(tr.fold2(G2, cores[n].shape[0], cores[n].shape[2]))
+    return new
+
+
 def als_update(cores, X, n):
     """TR-ALS core update (Algorithm 1): G_{n(2)} = X_[n] Z (Z^T Z)^{-1}."""
     Z = tr.subchain_unfold(cores, n)

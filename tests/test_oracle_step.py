@@ -197,6 +197,32 @@ def test_full_batch_scaled_step_is_als():
     assert np.allclose(new, ob.als_update(cores, X, n), rtol=1e-9, atol=1e-10)
 
 
+def test_scaled_gd_alpha_one_is_jacobi_als():
+    """TR-ScaledGD with alpha = 1 and no damping replaces every core by its
+    TR-ALS update (Algorithm 1) computed from the same iterate: checked
+    against numpy's least-squares solver, core by core."""
+    cores = random_cores(DIMS, RANKS, seed=21)
+    X = np.random.default_rng(22).standard_normal(DIMS)
+    new = ob.gd_step(cores, X, 1.0, scaled=True)
+    for n in range(len(DIMS)):
+        assert np.allclose(tr.unfold2(new[n]), ob.als_update(cores, X, n), rtol=1e-8, atol=1e-10)
+
+
+def test_gd_first_order_decrease():
+    """TR-GD moves every core along -grad_n at once, so the loss decreases by
+    alpha * sum_n ||grad_n||^2 to first order: (f(Y) - f(Y_alpha)) / alpha
+    tends to that sum as alpha -> 0 (error O(alpha))."""
+    cores = random_cores(DIMS, RANKS, seed=23)
+    X = np.random.default_rng(24).standard_normal(DIMS)
+    f0 = tr.loss(cores, X)
+    want = sum(float(np.sum(tr.full_gradient(cores, X, n) ** 2)) for n in range(len(DIMS)))
+    errs = []
+    for alpha in (1e-7, 1e-8):
+        got = (f0 - tr.loss(ob.gd_step(cores, X, alpha), X)) / alpha
+        errs.append(abs(got - want) / want)
+    assert errs[1] < 2e-5 and errs[1] < errs[0] / 5
+
+
 def test_damping_limit_recovers_plain_step():
     """Damped preconditioner: with eta^t -> infinity and step alpha * eta^t the
     scaled step tends to the plain BRSGD step, error O(||h|| / eta^t)."""
