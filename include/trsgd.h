@@ -286,6 +286,23 @@ trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial);
  * path launches five kernels per iteration). */
 int64_t trsgd_launch_count(const trsgd_handle *h);
 
+/* One iteration of the full-gradient methods the paper compares against
+ * (Sec. 3), on problem 0 of the handle, every core from the same iterate:
+ *   grad_n = G_{n(2)} Gamma_n - M_n,  Gamma_n = Z^T Z,  M_n = X_[n] Z,
+ *   Z = G^{!=n}_{[2]} (Eq. gradient);
+ *   scaled = 0 (TR-GD):       G_{n(2)} <- G_{n(2)} - alpha grad_n;
+ *   scaled = 1 (TR-ScaledGD): G_{n(2)} <- G_{n(2)} - alpha grad_n
+ *                             (Gamma_n + damping I)^{-1} (Eq. scaled_gd).
+ * Z is formed in full (J_n x R_n R_{n+1}, device scratch allocated at the
+ * first call), M_n and Gamma_n by passes over Z and the mode-major copy of X
+ * with fixed-order sums (deterministic), the factor of Gamma_n + damping I in
+ * FP64 (the damping grows on failure as for the scaled step, then
+ * TRSGD_ENUMERIC).  FP64 and FP32 problems with uniform sampling, R_n <= 16,
+ * scaled R_n R_{n+1} <= 128; else TRSGD_EUNSUPPORTED; alpha, damping finite,
+ * damping >= 0, scaled 0 or 1, else TRSGD_EINVAL.  Asynchronous on the
+ * handle's stream; device errors are latched as for trsgd_step. */
+trsgd_status trsgd_gd_step(trsgd_handle *h, int32_t scaled, double alpha, double damping);
+
 /* BF16 pieces per tensor-core operand of the residual and gradient
  * contractions in the handle's current launch shape: 0 = the FMA units (FP64;
  * FP32 with TRSGD_FP32_FMA or where the pieces do not fit the cluster's shared

@@ -85,6 +85,7 @@ _SIGNATURES = {
     "trsgd_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "trsgd_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "trsgd_tensor_pieces": (ctypes.c_int32, [ctypes.c_void_p]),
+    "trsgd_gd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
     "trsgd_destroy": (None, [ctypes.c_void_p]),
     "trsgd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -153,6 +153,11 @@ class Solver:
     def launch_count(self) -> int:
         return int(_abi.lib().trsgd_launch_count(self._h))
 
+    def gd_step(self, scaled: bool = False, alpha: float = 1e-3, damping: float = 0.0):
+        """One full-gradient iteration (TR-GD, or TR-ScaledGD when ``scaled``) of
+        problem 0, every core from the same iterate."""
+        check(_abi.lib().trsgd_gd_step(self._h, 1 if scaled else 0, float(alpha), float(damping)), "trsgd_gd_step")
+
     def tensor_pieces(self) -> int:
         """BF16 pieces per tensor-core operand of the two contractions (0: FMA units)."""
         return int(_abi.lib().trsgd_tensor_pieces(self._h))

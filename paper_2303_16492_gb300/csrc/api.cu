@@ -66,6 +66,8 @@ struct trsgd_handle {
   bool optimal = false;   // problem 0 samples from the optimal distribution
   bool grid = false;      // whole-GPU path (grid.cu) instead of the fused cluster kernel
   GridPath gp = {};
+  GdBuffers gdb;          // full-gradient iterations (trsgd_gd_step), allocated at first use
+  bool gd_ready = false;
   OptBuffers opt = {};
   size_t dbg_bytes[8] = {};
   void *dbg_ptr[8] = {};
@@ -892,6 +894,63 @@ trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial) {
 }
 
 int64_t trsgd_launch_count(const trsgd_handle *h) { return h ? h->launches : -1; }
+
+trsgd_status trsgd_gd_step(trsgd_handle *h, int32_t scaled, double alpha, double damping) {
+  if (!h || (scaled != 0 && scaled != 1) || !std::isfinite(alpha) || !std::isfinite(damping) || damping < 0)
+    return TRSGD_EINVAL;
+  const trsgd_config &c = h->cfg[0];
+  if (h->xc_dtype == TRSGD_DTYPE_BF16 || c.dist != TRSGD_DIST_UNIFORM) return TRSGD_EUNSUPPORTED;
+  for (int k = 0; k < c.N; ++k) {
+    const int64_t Q = c.R[k] * c.R[(k + 1) % c.N];
+    if (c.R[k] > 16 || (scaled && Q > 128)) return TRSGD_EUNSUPPORTED;
+  }
+  const ProbDesc &D = h->hdesc[0];
+  GdArgs a = {};
+  a.N = c.N;
+  for (int k = 0; k < c.N; ++k) {
+    a.I[k] = (int)c.I[k];
+    a.R[k] = (int)c.R[k];
+    a.cores[k] = D.cores[k];
+    a.xmode[k] = D.xmode[k];
+    a.ldx[k] = D.ldx[k];
+  }
+  for (int n = 0; n < c.N; ++n) {
+    long long Jn = 1;
+    for (int k = 0; k < c.N; ++k)
+      if (k != n) Jn *= c.I[k];
+    a.J[n] = Jn;
+  }
+  if (!h->gd_ready) {
+    const size_t st = h->core_dtype == 0 ? 8 : 4;
+    size_t zmax = 0, pmax = 0;
+    int qmax = 1;
+    for (int n = 0; n < c.N; ++n) {
+      const size_t Q = (size_t)(c.R[n] * c.R[(n + 1) % c.N]);
+      zmax = std::max(zmax, (size_t)a.J[n] * Q);
+      pmax = std::max(pmax, std::max((size_t)c.I[n], Q) * Q);
+      qmax = std::max(qmax, (int)Q);
+    }
+    cudaError_t e = h->buf.alloc(&h->gdb.Z, zmax * st);
+    if (e == cudaSuccess) e = h->buf.alloc(&h->gdb.part, (size_t)h->gdb.max_chunks * pmax * st);
+    for (int n = 0; n < c.N && e == cudaSuccess; ++n) {
+      const size_t Q = (size_t)(c.R[n] * c.R[(n + 1) % c.N]);
+      e = h->buf.alloc(&h->gdb.M[n], (size_t)c.I[n] * Q * st);
+      void *g = nullptr;
+      if (e == cudaSuccess) e = h->buf.alloc(&g, Q * Q * sizeof(double));
+      h->gdb.Gam[n] = static_cast<double *>(g);
+    }
+    void *f = nullptr;
+    if (e == cudaSuccess) e = h->buf.alloc(&f, (size_t)qmax * qmax * sizeof(double));
+    h->gdb.fac = static_cast<double *>(f);
+    if (e == cudaSuccess) e = gd_prepare();
+    if (e != cudaSuccess) return from_cuda(e);
+    h->gd_ready = true;
+  }
+  cudaError_t e = launch_gd_iteration(h->core_dtype, a, scaled, alpha, damping, h->gdb, h->d_status, h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  h->launches += (6 + (scaled ? 1 : 0)) * c.N;   // per mode: Z, 2 x (A^T Z, reduce), factor, update
+  return TRSGD_OK;
+}
 
 int32_t trsgd_tensor_pieces(const trsgd_handle *h) {
   if (!h) return -1;

@@ -114,6 +114,27 @@ template <typename T, typename XT, int RMAX, int NPC>
 cudaError_t step_launch_t(const ProbDesc *descs, int nprob, const StepLayout &lay, int threads, long long t0,
                           int nsteps, const long long *t_dev, cudaStream_t s);
 
+// Full-gradient iterations (gd.cu): one problem's shape, cores and mode-major copies.
+struct GdArgs {
+  int N;
+  int I[8], R[8];
+  long long J[8];          // J_n = prod_{k != n} I_k
+  void *cores[8];          // G_{k(2)}, core dtype
+  const void *xmode[8];    // mode-major copies of X (core dtype)
+  long long ldx[8];
+};
+struct GdBuffers {
+  void *Z = nullptr;               // J_n x Q subchain matrix (largest mode)
+  void *part = nullptr;            // max_chunks x max(I_n, Q) x Q column-chunk partials
+  void *M[8] = {};         // M_n = X_[n] Z, I_n x Q
+  double *Gam[8] = {};     // Gamma_n = Z^T Z, Q x Q
+  double *fac = nullptr;           // FP64 Cholesky factor of Gamma_n + damping I
+  int max_chunks = 608;
+};
+cudaError_t gd_prepare();
+cudaError_t launch_gd_iteration(int core_dtype, const GdArgs &a, int scaled, double alpha, double damping,
+                                GdBuffers &b, int *status, cudaStream_t s);
+
 cudaError_t launch_mode_copy(int src_dtype, int dst_dtype, const void *X, void *out, long long A,
                              long long In, long long B, long long ld, cudaStream_t s);
 cudaError_t launch_euclid_table(int core_dtype, const void *G, int I, int Q, double *snorm,

@@ -122,6 +122,7 @@ def test_null_handle_calls(lib):
     assert lib.trsgd_set_debug(None, 1) == _abi.EINVAL
     assert lib.trsgd_launch_count(None) == -1
     assert lib.trsgd_tensor_pieces(None) == -1
+    assert lib.trsgd_gd_step(None, 0, 0.1, 0.0) == _abi.EINVAL
     lib.trsgd_destroy(None)
 
 

@@ -330,3 +330,37 @@ def test_experiment_2_shapes(name, dist):
         for k in range(N):
             assert rel(cores_d[k].double().cpu().numpy(), tr.unfold2(st.cores[k])) < tol
     s.close()
+
+
+@pytest.mark.parametrize("scaled", [False, True], ids=["gd", "scaled_gd"])
+def test_experiment_1_full_gradient_iteration(scaled):
+    """One TR-GD / TR-ScaledGD iteration at the Experiment I size (300^3, R =
+    10, J_n = 90,000 columns per mode): the device forms Z, X_[n] Z and Z^T Z
+    from the mode-major copies; the oracle from X = TR(planted) built on the
+    host.  Every updated core within the FP32 bound (sums over 9e4 terms)."""
+    A = api()
+    from paper_2303_16492_gb300 import synth
+    w = synth.workload("e1")
+    planted = synth.planted_cores(w)
+    P = to_oracle_cores(planted, w.ranks)
+    X = tr.reconstruct(P)
+    Xd = torch.from_numpy(np.ascontiguousarray(X.ravel(order="F")).astype(np.float32)).cuda()
+    X = Xd.double().cpu().numpy().reshape(w.dims, order="F")
+    init = [G.astype(np.float32) for G in synth.initial_cores(w, float(np.sum(X ** 2)))]
+    cores_d = [torch.from_numpy(G).cuda() for G in init]
+    pc = A.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, seed=w.seed + 3)
+    s = A.Solver([pc], [Xd], [cores_d])
+    start = to_oracle_cores([G.astype(np.float64) for G in init], w.ranks)
+    if scaled:
+        alpha = 1.0   # the ALS update of every core
+    else:             # a step of ~5 % of the cores, so that the step itself is compared
+        unit = ob.gd_step(start, X, 1.0)
+        alpha = 0.05 * np.sqrt(sum(np.sum(g ** 2) for g in start)) / np.sqrt(
+            sum(np.sum((u - g) ** 2) for u, g in zip(unit, start)))
+    want = ob.gd_step(start, X, alpha, scaled=scaled)
+    s.gd_step(scaled=scaled, alpha=alpha)
+    torch.cuda.synchronize()
+    for k in range(3):
+        got = cores_d[k].double().cpu().numpy() - tr.unfold2(start[k])
+        assert rel(got, tr.unfold2(want[k]) - tr.unfold2(start[k])) < (1e-4 if scaled else 2e-5)
+    s.close()

@@ -272,6 +272,44 @@ def test_leverage_table_of_rank_deficient_core():
     s.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("scaled", [False, True], ids=["gd", "scaled_gd"])
+@pytest.mark.parametrize("shape", [dict(dims=[12, 9, 10], ranks=[3, 4, 2]),
+                                   dict(dims=[7, 6, 5, 8], ranks=[2, 3, 2, 3])],
+                         ids=["N3", "N4"])
+def test_full_gradient_iterations(shape, scaled, prec):
+    """TR-GD and TR-ScaledGD (Sec. 3, Eq. gradient and Eq. scaled_gd): every
+    core updated from the same iterate, three iterations, each compared with
+    the oracle from shared cores."""
+    case = Case(prec=prec, J=16, alpha=0.05, **shape)
+    damping = 1e-3 if scaled else 0.0
+    tol = 1e-10 if prec == 0 else (1e-4 if scaled else 2e-5)
+    for _ in range(3):
+        start = case.device_cores()
+        # the step is compared, so that a wrong gradient cannot hide behind the
+        # cores' own size: alpha makes it ~5 % of the cores
+        unit = ob.gd_step(start, case.X, 1.0, scaled=scaled, damping=damping)
+        du = np.sqrt(sum(np.sum((u - g) ** 2) for u, g in zip(unit, start)))
+        alpha = 0.05 * np.sqrt(sum(np.sum(g ** 2) for g in start)) / du
+        want = ob.gd_step(start, case.X, alpha, scaled=scaled, damping=damping)
+        case.solver.gd_step(scaled=scaled, alpha=alpha, damping=damping)
+        torch.cuda.synchronize()
+        for G, O, S in zip(case.device_cores(), want, start):
+            assert rel(G - S, O - S) < tol
+
+
+def test_full_gradient_rejects_unsupported():
+    """Non-uniform handles (their sampling tables would go stale) and
+    invalid arguments are refused on the host."""
+    A = api()
+    case = Case(dims=[8, 7, 9], ranks=[2, 2, 2], J=8, prec=1, dist=ob.DIST_EUCLIDEAN)
+    with pytest.raises(A._abi.TrsgdError):
+        case.solver.gd_step(alpha=0.1)
+    case = Case(dims=[8, 7, 9], ranks=[2, 2, 2], J=8, prec=1)
+    with pytest.raises(A._abi.TrsgdError):
+        case.solver.gd_step(alpha=float("nan"))
+
+
 def test_adagrad_steps_and_state():
     case = Case(dims=[12, 10, 11], ranks=[2, 3, 2], J=40, prec=0, rule=ob.RULE_ADAGRAD, eta=0.02)
     case.solver.set_debug(True)
