@@ -398,6 +398,45 @@ def run_extras(args, device):
         out["experiment_2"] = run_exp2(args, device)
     except Exception as e:
         out["experiment_2_error"] = repr(e)
+    try:
+        out["full_gradient_e1"] = run_full_gradient(args, device)
+    except Exception as e:
+        out["full_gradient_error"] = repr(e)
+    return out
+
+
+def run_full_gradient(args, device, iters=50):
+    """The full-gradient methods the paper compares against, on Experiment I
+    (300^3, R = 10) with the paper's steps (TR-GD alpha = 6e-7, TR-ScaledGD
+    alpha = 0.5): iterations/s (device events over `iters` iterations, each
+    updating all three cores from the same iterate) and the RSE reached, next
+    to TR-BRSGD's steps/s on the same problem (the per-iteration contrast of
+    Sec. 4)."""
+    import torch
+
+    from paper_2303_16492_gb300 import api, synth
+    w = synth.workload("e1")
+    X, Xtrue, init = device_problem(w, device)
+    out = {"iterations": iters}
+    for label, scaled, alpha in (("TR-GD", False, 6e-7), ("TR-ScaledGD", True, 0.5)):
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=1, alpha=w.alpha, seed=w.seed + 3)
+        s = api.Solver([pc], [X], [[c.clone() for c in init]])
+        try:
+            s.gd_step(scaled=scaled, alpha=alpha)   # scratch allocation and warm-up
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(iters):
+                s.gd_step(scaled=scaled, alpha=alpha)
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b)
+            out[label] = {"alpha": alpha, "iterations_per_s": round(iters / (ms * 1e-3), 1),
+                          "ms_per_iteration": round(ms / iters, 4), "rse_after": s.rel_error(0, Xtrue)}
+        except Exception as e:
+            out[label] = {"error": repr(e)}
+        s.close()
+    del X, Xtrue, init
     return out
 
 
