@@ -546,27 +546,31 @@ __global__ void __launch_bounds__(kMaxThreads)
       const int row = 32 * qd + lane;
       const int JC = NR / 8;
       T *dbg_e = rec ? static_cast<T *>(D.dbg_e) : nullptr;
-      for (int c8 = wg; c8 < NR / 8; c8 += nwg) {
-        float v[8];
-        tmem_ld8(tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(c8 * 8), v);
+      for (int c16 = wg; c16 < NR / 16; c16 += nwg) {   // 16 TMEM columns per load (NR: multiple of 16)
+        float v[16];
+        tmem_ld16(tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(c16 * 16), v);
         if (row < ti) {
-          float ev[8];
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int jl = c8 * 8 + j;
-            ev[j] = 0.f;
-            if (jl < jb) {
-              const float x = to_f32(xs[(size_t)jl * lay.ldxs + i0 + row]);
-              const float e = v[j] - x;
-              if (dbg_e) dbg_e[(size_t)(cur_j0 + jl) * In + i0 + row] = e;
-              ev[j] = e * wt_s[jl];
+          for (int h = 0; h < 2; ++h) {
+            const int c8 = 2 * c16 + h;
+            float ev[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const int jl = c8 * 8 + j;
+              ev[j] = 0.f;
+              if (jl < jb) {
+                const float x = to_f32(xs[(size_t)jl * lay.ldxs + i0 + row]);
+                const float e = v[8 * h + j] - x;
+                if (dbg_e) dbg_e[(size_t)(cur_j0 + jl) * In + i0 + row] = e;
+                ev[j] = e * wt_s[jl];
+              }
             }
-          }
-          uint4 w[EWP];
-          bf16_split8<EWP>(ev, w);
-          const uint32_t o = kmaj_off(row, c8 * 8, JC);
+            uint4 w[EWP];
+            bf16_split8<EWP>(ev, w);
+            const uint32_t o = kmaj_off(row, c8 * 8, JC);
 #pragma unroll
-          for (int k = 0; k < EWP; ++k) *reinterpret_cast<uint4 *>(ewp[k] + o) = w[k];
+            for (int k = 0; k < EWP; ++k) *reinterpret_cast<uint4 *>(ewp[k] + o) = w[k];
+          }
         }
       }
       fence_proxy_async_smem();
@@ -591,13 +595,13 @@ __global__ void __launch_bounds__(kMaxThreads)
       if (!mbar_wait_bounded(bar_mma, mphase, kWaitLimit)) latch_status(D.status, kStatusTimeout);
       mphase ^= 1u;
       tc_fence_after();
-      for (int c8 = wg; c8 < NP / 8; c8 += nwg) {
-        float v[8];
-        tmem_ld8(tbase + 256 + ((uint32_t)(32 * qd) << 16) + (uint32_t)(c8 * 8), v);
+      for (int c16 = wg; c16 < NP / 16; c16 += nwg) {   // NP: multiple of 16
+        float v[16];
+        tmem_ld16(tbase + 256 + ((uint32_t)(32 * qd) << 16) + (uint32_t)(c16 * 16), v);
         if (row < ti) {
 #pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int q = c8 * 8 + j;
+          for (int j = 0; j < 16; ++j) {
+            const int q = c16 * 16 + j;
             if (q < Q) reg[(size_t)row * lay.ldq + q] = v[j];
           }
         }
