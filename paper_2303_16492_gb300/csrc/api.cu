@@ -145,7 +145,7 @@ static trsgd_status validate(const trsgd_config *cfg, int32_t np) {
 // Z and Z^T.  Tail region [off_reg, total): G_n chunk / partial gradient
 // (reg), the FP64 Gram (scaled), the owned rows; the staged slices of the
 // chain and the CDF scratch alias the same tail.
-static bool make_layout_p(const trsgd_handle &h, int C, int tcp, StepLayout &L) {
+static bool make_layout_p(const trsgd_handle &h, int C, int tcp, bool tab, StepLayout &L) {
   const size_t st = h.core_dtype == 0 ? 8 : 4;
   const size_t sx = dtype_size(h.xc_dtype);
   int Imax = 1, Qmax = 1, Jmax = 1, QH = 0;
@@ -198,6 +198,24 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, StepLayout &L) 
   L.off_misc = take(64, 16);
   L.off_const = take(32 * 8, 16);
   L.off_ord = take(3 * kMaxOrder * 4, 16);   // chain order, staged-slice offsets and pitches
+  // leverage / Euclidean: the CDF (u64) and p (f64) of the sampled cores of a step
+  L.tab_ok = 0;
+  if (tab) {
+    size_t tb = 0;
+    for (const auto &c : h.cfg) {
+      if (c.dist != TRSGD_DIST_LEVERAGE && c.dist != TRSGD_DIST_EUCLIDEAN) continue;
+      for (int n = 0; n < c.N; ++n) {
+        size_t b = 0;
+        for (int k = 0; k < c.N; ++k)
+          if (k != n) b += (size_t)c.I[k] * 16;
+        tb = std::max(tb, b);
+      }
+    }
+    if (tb > 0) {
+      L.off_tab = take(tb, 16);
+      L.tab_ok = 1;
+    }
+  }
   L.off_desc = take(rup(sizeof(ProbDesc), 16), 16);
   L.off_idx = take((size_t)L.JB * kMaxOrder * 4, 16);
   L.off_col = take((size_t)L.JB * 8, 16);
@@ -289,9 +307,16 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, StepLayout &L) 
 // BF16-mixed: two pieces; FP32: three pieces when they fit, else the FMA
 // units; FP64: the FMA units.
 static bool make_layout(const trsgd_handle &h, int C, StepLayout &L) {
-  if (h.xc_dtype == TRSGD_DTYPE_BF16) return make_layout_p(h, C, 2, L);
-  if (h.core_dtype == 1 && h.fp32_pieces && make_layout_p(h, C, 3, L)) return true;
-  return make_layout_p(h, C, 0, L);
+  // with the staged sampling tables if they fit, else without
+  for (int tab = 1; tab >= 0; --tab) {
+    if (h.xc_dtype == TRSGD_DTYPE_BF16) {
+      if (make_layout_p(h, C, 2, tab, L)) return true;
+      continue;
+    }
+    if (h.core_dtype == 1 && h.fp32_pieces && make_layout_p(h, C, 3, tab, L)) return true;
+    if (make_layout_p(h, C, 0, tab, L)) return true;
+  }
+  return false;
 }
 
 static int default_cluster(const trsgd_handle &h) {

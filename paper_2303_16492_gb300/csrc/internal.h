@@ -49,13 +49,14 @@ struct StepLayout {
   int rows_own;   // max rows of g owned by one CTA
   int sb_ok;      // sampled slices staged in shared memory (else read through L2)
   int sbj;        // samples whose slices are staged at a time (the chain runs per group)
+  int tab_ok;     // leverage / Euclidean tables of the sampled cores staged in shared memory
   int pstride;    // per-sample stride of the chain intermediates
   int qp, jbp;    // tensor-core path: Q and samples padded to 16 (tile extents)
   int tcp;        // BF16 pieces per tensor-core operand: 2 (BF16-mixed), 3 (FP32), 0 (FMA units)
   // off_sb aliases the region [off_reg, total): the staged slices are dead
   // before the Gram / chunk buffers and the CDF scratch are written
   size_t off_desc, off_idx, off_col, off_wt, off_bar, off_x, off_z, off_reg, off_h64,
-      off_hdiag, off_gown, off_misc, off_const, off_sb, off_p0, off_p1, off_zp[3], off_ew, off_ord,
+      off_hdiag, off_gown, off_misc, off_const, off_sb, off_p0, off_p1, off_zp[3], off_ew, off_ord, off_tab,
       off_hz, off_hidx, off_hw, total;
   int JBH;        // max Hessian-batch samples per CTA
   int cw0;        // first CTA that takes samples: 1 for the scaled variant with C > 1 (CTA 0

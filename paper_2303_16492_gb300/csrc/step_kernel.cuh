@@ -97,6 +97,18 @@ __device__ __forceinline__ void cluster_wait_acquire() {
   asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// Smallest i in [0, n) with target < cdf[i], cdf in shared memory (the same
+// search as cdf_search on the global table).
+__device__ __forceinline__ int cdf_search_smem(const unsigned long long *cdf, int n, uint64_t target) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (cdf[mid] > target) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ float to_f32(float x) { return x; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 x) { return __bfloat162float(x); }
 
@@ -363,6 +375,37 @@ __global__ void __launch_bounds__(kMaxThreads)
     // Uniform sampling: first one thread per (sample, factor) draws the index,
     // then one thread per sample combines them (the draws are independent).
     const bool uni_split = D.dist == 0;
+    // Leverage / Euclidean with the tables staged: the CDF and p of the L sampled
+    // cores are copied to shared memory (factor sp at offset toff(sp)), then one
+    // thread per (sample, factor) searches; p_F is formed per sample below.
+    const bool tab_split = (D.dist == 1 || D.dist == 2) && lay.tab_ok;
+    unsigned long long *tcdf = reinterpret_cast<unsigned long long *>(smem + lay.off_tab);
+    int ttot = 0;
+    for (int sp = 0; sp < L; ++sp) ttot += I[ring(sp)];
+    double *tprob = reinterpret_cast<double *>(tcdf + ttot);
+    auto toff = [&](int sp) {
+      int o = 0;
+      for (int q = 0; q < sp; ++q) o += I[ring(q)];
+      return o;
+    };
+    if (tab_split) {
+      for (int e = tid; e < ttot; e += NT) {
+        int sp = 0, i = e;
+        while (i >= I[ring(sp)]) i -= I[ring(sp++)];
+        const int k = ring(sp);
+        tcdf[e] = __ldcg(D.cdf[k] + i);
+        tprob[e] = __ldcg(D.prob[k] + i);
+      }
+      gsync();
+      for (int e = tid; e < L * jb; e += NT) {
+        const int sp = e / jb, jl = e - sp * jb;
+        const int k = ring(sp), Ik = I[k];
+        const unsigned long long *cdf = tcdf + toff(sp);
+        const uint64_t u = draw_u64(D.seed, t, kStreamF, k, (uint32_t)(j0 + jl));
+        idx_s[jl * kMaxOrder + k] = cdf_search_smem(cdf, Ik, mulhi64(u, cdf[Ik - 1]));
+      }
+      gsync();
+    }
     if (uni_split) {
       for (int e = tid; e < L * jb; e += NT) {
         const int sp = e / jb, jl = e - sp * jb;
@@ -390,6 +433,13 @@ __global__ void __launch_bounds__(kMaxThreads)
           st *= I[k];
         }
         pF = __ldcg(D.ext_pf + j0 + jl);
+      } else if (tab_split) {   // indices drawn above; p_F = prod p_k(i_k) in ring order
+        for (int sp = 0; sp < L; ++sp) {
+          const int k = ring(sp), i = idx_s[jl * kMaxOrder + k];
+          pF = __dmul_rn(pF, tprob[toff(sp) + i]);
+          col += (long long)i * st;
+          st *= I[k];
+        }
       } else if (uni) {   // indices drawn above; p_F = prod 1/I_k (only when recorded)
         for (int sp = 0; sp < L; ++sp) {
           const int k = ring(sp);
@@ -1202,13 +1252,7 @@ __global__ void __launch_bounds__(kMaxThreads)
           wsc[i] = __double2ull_rn(__dmul_rn(p, 4503599627370496.0));  // * 2^52, exact
         }
         __syncthreads();
-        if (tid == 0) {
-          unsigned long long run = 0;
-          for (int i = 0; i < In; ++i) {
-            run += wsc[i];
-            wsc[i] = run;
-          }
-        }
+        scan_u64_warp0(wsc, In);
         __syncthreads();
         for (int i = tid; i < In; i += NT) D.cdf[n][i] = wsc[i];
       }

@@ -32,6 +32,28 @@ __device__ __noinline__ bool cholesky_cta_t(T *A, int m, int ld) {
   return true;
 }
 
+// Inclusive prefix sums of w[0..n) in place, by warp 0 (the other threads
+// return at once; callers put barriers around it).  Integer sums: exact in
+// any order.  Lane l scans the segment [l s, (l + 1) s), s = ceil(n / 32), then
+// adds the exclusive scan of the segment totals.
+__device__ __forceinline__ void scan_u64_warp0(unsigned long long *w, int n) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x, seg = (n + 31) / 32;
+  const int a = min(n, lane * seg), b = min(n, a + seg);
+  unsigned long long run = 0;
+  for (int i = a; i < b; ++i) {
+    run += w[i];
+    w[i] = run;
+  }
+  unsigned long long incl = run;
+  for (int d = 1; d < 32; d <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl += v;
+  }
+  const unsigned long long off = incl - run;
+  for (int i = a; i < b; ++i) w[i] += off;
+}
+
 // prob[i] = p[i] (given) and cdf = inclusive prefix sums of round(p * 2^52).
 // scratch: In unsigned long long entries of shared memory.
 __device__ __forceinline__ void write_cdf_cta(const double *p, int In, double *prob,
@@ -42,13 +64,7 @@ __device__ __forceinline__ void write_cdf_cta(const double *p, int In, double *p
     wsc[i] = __double2ull_rn(__dmul_rn(p[i], 4503599627370496.0));  // * 2^52, exact scaling
   }
   __syncthreads();
-  if (tid == 0) {
-    unsigned long long run = 0;
-    for (int i = 0; i < In; ++i) {
-      run += wsc[i];
-      wsc[i] = run;
-    }
-  }
+  scan_u64_warp0(wsc, In);
   __syncthreads();
   for (int i = tid; i < In; i += NT) cdf[i] = wsc[i];
   __syncthreads();
