@@ -126,9 +126,9 @@ __device__ __forceinline__ T dotk(const T *p, const T *s) {
 // staged slice itself (column-major).  A group of RU / CB lanes per sample:
 // lane bb owns the CB output columns bb*CB .., whose entries of S_q stay in
 // registers, so every loaded value of P_q serves CB outputs and a warp covers
-// 32 / (RU / CB) samples.  Column-major P_q (FIRST) is accumulated as outer
-// products of its columns, row-major P_q as dot products with its rows; either
-// way each output sums a = 0 .. RU-1 in order with fused multiply-adds.
+// 32 / (RU / CB) samples.  Each output is a dot product of a row of P_q (read
+// with stride RU when P_q is the column-major staged slice, FIRST) with a
+// column of S_q, summed a = 0 .. RU-1 in order with fused multiply-adds.
 template <int RU, int CB, bool FIRST, typename T>
 __device__ __noinline__ void chain_factor_uniform(const T *src, int sstride, const T *sfac, int qpad, T *dst,
                                                   int dstride, int jb) {
@@ -151,36 +151,18 @@ __device__ __noinline__ void chain_factor_uniform(const T *src, int sstride, con
       for (int a = 0; a < RU; ++a) col[c][a] = S[(b0 + c) * RU + a];
     T *Dp = dst + (size_t)jc * dstride + b0;
     if constexpr (FIRST) {
-      T acc[RU][CB];
-#pragma unroll
-      for (int r = 0; r < RU; ++r)
-#pragma unroll
-        for (int c = 0; c < CB; ++c) acc[r][c] = T(0);
 #pragma unroll 2
-      for (int a = 0; a < RU; ++a) {
-        T pc[RU];   // column a of P_q
-        if constexpr (sizeof(T) == 4) {
-          const float2 *p2 = reinterpret_cast<const float2 *>(P + a * RU);
+      for (int r = 0; r < RU; ++r) {
+        T pr[RU];   // row r of the column-major P_q (stride RU)
 #pragma unroll
-          for (int r2 = 0; r2 < RU / 2; ++r2) {
-            const float2 v = p2[r2];
-            pc[2 * r2] = v.x;
-            pc[2 * r2 + 1] = v.y;
-          }
-        } else {
+        for (int a = 0; a < RU; ++a) pr[a] = P[r + a * RU];
 #pragma unroll
-          for (int r = 0; r < RU; ++r) pc[r] = P[a * RU + r];
+        for (int c = 0; c < CB; ++c) {
+          T acc = T(0);
+#pragma unroll
+          for (int a = 0; a < RU; ++a) acc = fma(pr[a], col[c][a], acc);
+          if (ok) Dp[r * RU + c] = acc;
         }
-#pragma unroll
-        for (int r = 0; r < RU; ++r)
-#pragma unroll
-          for (int c = 0; c < CB; ++c) acc[r][c] = fma(pc[r], col[c][a], acc[r][c]);
-      }
-      if (ok) {
-#pragma unroll
-        for (int r = 0; r < RU; ++r)
-#pragma unroll
-          for (int c = 0; c < CB; ++c) Dp[r * RU + c] = acc[r][c];
       }
     } else {
 #pragma unroll 2
