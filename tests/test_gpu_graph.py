@@ -102,3 +102,27 @@ def test_checkpoint_resume_is_bit_exact(rule, dist):
     _same(cores_b, ref_cores)
     ref.close()
     b.close()
+
+
+@pytest.mark.parametrize("threads", [128, 256, 512])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_pipelined_launch_equals_single_steps(threads, prec):
+    """Within one launch of many uniform iterations, the draws and fiber copies
+    of iteration t+1 are issued by half of each CTA while the other half
+    reduces iteration t.  The draws depend on t only, so one launch of 40
+    iterations must give the same cores, bit for bit, as 40 launches of one
+    iteration (no pipelining), for every block size."""
+    c = Case([12, 9, 10, 7], [3, 4, 2, 3], 40, seed=5, prec=prec, alpha=0.05)
+    start = [t.clone() for t in c.cores_d]
+    c.solver.close()
+    a, ca = _fresh(c, cores=start)
+    b, cb = _fresh(c, cores=start)
+    for s in (a, b):
+        s.launch_shape(cluster=4, threads=threads)
+    a.run(0, 40)                 # one launch (no stopping checks)
+    for t in range(40):
+        b.step(t)
+    torch.cuda.synchronize()
+    _same(ca, cb)
+    a.close()
+    b.close()
