@@ -244,6 +244,9 @@ def run_ours(args):
                                  + ("; the two contractions run on the tensor cores as three BF16 pieces per "
                                     "operand, the rest of the step on the FP32 pipes" if pieces == 3 else ""),
                     "hbm_frac": round(by / (ms_per_step * 1e-3) / 1e9 / pk.get("hbm_gbs", 6652.0), 5),
+                    # one problem occupies one cluster: its SMs' share of the same peak
+                    "sms_used": cluster,
+                    "frac_of_sms_used": round(achieved_tflops / (alu_peak * cluster / 152.0), 4),
                     "algorithmic_bytes_per_step": int(by), "algorithmic_flops_per_step": int(fl)}
 
     e2e = run_e2e(args, w, solver, X, init, device) if rank == 0 and not args.no_e2e else None
