@@ -514,7 +514,11 @@ __global__ void __launch_bounds__(kMaxThreads)
       // gown, so that the update reads them from shared memory
       const bool stash = !scaled;
       const int r0 = ti * c / C, r1 = ti * (c + 1) / C;
-      for (int e = tid; e < 128 * QC; e += NT) {
+      // only the core-matrix rows that hold rows of the chunk: row i of both
+      // products depends on row i of G (and of Ew) only, and rows >= ti of the
+      // results are never read
+      const int ti8 = (ti + 7) & ~7;
+      for (int e = tid; e < ti8 * QC; e += NT) {
         // 8 consecutive threads: the 8 rows of one core matrix, so that each
         // piece store of a warp covers 512 contiguous bytes (no bank conflicts)
         const int rest = e >> 3, qb = rest % QC, ii = (rest / QC) * 8 + (e & 7);
