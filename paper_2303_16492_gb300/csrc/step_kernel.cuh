@@ -4,34 +4,47 @@
 // (Algorithm 3 with Algorithm 2).  The CTAs of a cluster split the |F|
 // samples of each step; everything a step needs stays on chip:
 //
-//   A1 slice indices (Philox, Algorithm 2) of this CTA's samples;
+//   A1 slice indices (Philox, Algorithm 2) of this CTA's samples, one thread
+//      per (sample, factor) for uniform sampling and for the leverage /
+//      Euclidean tables staged in shared memory;
 //   A2 p_F (product in ring order), weights 1/(|F| J_n p_F), fiber columns;
-//   A3 gather: the mode-n fibers of X from its mode-major copy and every
-//      sampled slice G_k(i_k), by per-thread 16-byte asynchronous copies
-//      (large fibers: TMA bulk copies completing on an mbarrier);
-//   A4 sampled subchain rows Z(j, r + r' R_n) = P_j(r', r), one thread per
-//      row of P_j = G_{n+1}(i_{n+1}) ... G_{n-1}(i_{n-1});
+//   A3 the mode-n fibers of X from its mode-major copy, by 16-byte
+//      asynchronous copies (fibers of 1 KB or more: TMA bulk copies completing
+//      on an mbarrier), waited for after A4;
+//   A4 per group of samples whose slices fit: the sampled slices G_k(i_k)
+//      staged in shared memory (one cp.async group per factor), then the
+//      sampled subchain rows Z(j, r + r' R_n) = P_j(r', r),
+//      P_j = G_{n+1}(i_{n+1}) ... G_{n-1}(i_{n-1}), factor by factor;
 //   S  (scaled variant) partial Gram Z^T D Z, reduced over the cluster into
 //      CTA 0, which factors h + eta^t I (Cholesky in the Gram-solve scalar:
 //      FP64, or double-float for float cores; damping grown on failure) and
 //      writes the factor to global memory.  In the scaled variant CTA 0 takes
 //      no samples, so the factorisation overlaps the other CTAs' B and C;
 //   B  per chunk of G_n rows: residual E = G_n Z^T - X_S (Eq. S_gradient),
-//      weighted in place over the fibers;
-//   C  partial gradient (E D) Z of this CTA's samples;
+//      weighted by 1/(|F| J_n p_F);
+//   C  partial gradient (E D) Z of this CTA's samples.  B and C run on the
+//      tensor cores (tcgen05, accumulators in TMEM) with every operand held
+//      as BF16 pieces (three for FP32, two for BF16-mixed), else on the FMA
+//      units;
 //   R  reduction of the partials over the cluster through distributed shared
-//      memory in fixed CTA order (deterministic), then the step rule (fixed
-//      alpha or AdaGrad) on the rows this CTA owns, written to G_n in HBM;
+//      memory, each element summed in a fixed order (owner c pulls CTAs
+//      c+1, c+2, ... mod C: deterministic), then the step rule (fixed alpha
+//      or AdaGrad) on the rows this CTA owns, written to G_n in HBM;
 //   scaled: p = -g h^{-1} on the owned rows by two triangular solves
 //      against CTA 0's factor (Eq. scaledsg_direction, damped form);
-//   Euclidean distribution: slice norms of the updated rows and CTA 0's
-//      integer CDF of core n for the next iteration (Lemma euc_est).
+//   Euclidean / leverage distribution: CTA 0 rebuilds the table of core n for
+//      the next iteration (Lemma euc_est, Lemma lev_est).
+//
+// With uniform sampling the draws of iteration t+1 depend on no core: once
+// the last chunk of iteration t has consumed the fibers, the upper half of
+// each CTA issues A1-A3 of t+1 (named barrier 1) while the lower half
+// reduces and updates; both meet at the closing cluster barrier.
 //
 // Cluster barriers (barrier.cluster, release/acquire) separate the phases.
 // Cores and sampling tables are read through L2 only (ld.global.cg /
 // cp.async.cg) because other CTAs of the cluster rewrite them between steps.
-// The only spin-wait (the TMA mbarrier) is bounded and latches
-// TRSGD_ETIMEOUT.
+// The spin-waits (the fiber TMA and the MMA completion mbarriers) are
+// bounded and latch TRSGD_ETIMEOUT.
 #pragma once
 
 #include "blocks.cuh"
