@@ -504,10 +504,12 @@ __global__ void __launch_bounds__(kMaxThreads)
   };
 
   // Tensor-core residual and partial gradient of one chunk of <= 128 rows of
-  // G_n (operands split BF16, FP32 accumulation in TMEM):
-  //   D_R(i, jl) = G(i, :) Z(jl, :)^T  as hi*hi + hi*lo + lo*hi,
-  //   Ew(i, jl)  = w_jl (D_R(i, jl) - X_S(jl, i))              (epilogue),
-  //   D_P(i, q)  = sum_jl Ew(i, jl) Z(jl, q)   (Z_hi read MN-major),
+  // G_n (operands as NPC BF16 pieces, FP32 accumulation in TMEM):
+  //   D_R(i, jl) = G(i, :) Z(jl, :)^T  as the piece products of total order
+  //                < NPC (NPC = 2: hi*hi + hi*lo + lo*hi; NPC = 3: six),
+  //   Ew(i, jl)  = w_jl (D_R(i, jl) - X_S(jl, i))   (epilogue; EWP pieces),
+  //   D_P(i, q)  = sum_jl Ew(i, jl) Z(jl, q)        (Z read MN-major; products
+  //                of total order < EWP: Ew x Z_hi for BF16-mixed),
   // then D_P -> reg[i][q] (FP32) for the cluster reduction.
   auto tc_chunk = [&](int ti, int i0) {
     if constexpr (kTC) {
