@@ -14,6 +14,7 @@ template <> struct GramScalar<double> { using type = double; };
 __device__ __forceinline__ double gs_mul(double a, double b) { return a * b; }
 __device__ __forceinline__ double gs_fnms(double a, double b, double c) { return fma(-a, b, c); }   // c - a b
 __device__ __forceinline__ double gs_div(double a, double b) { return a / b; }
+__device__ __forceinline__ double gs_rcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ double gs_sqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ double gs_add(double a, double b) { return a + b; }
 __device__ __forceinline__ bool gs_pos(double a) { return a > 0.0 && isfinite(a); }
@@ -26,6 +27,7 @@ __device__ __forceinline__ double gs_ldcg(const double *p) { return __ldcg(p); }
 __device__ __forceinline__ df64 gs_mul(df64 a, df64 b) { return df_mul(a, b); }
 __device__ __forceinline__ df64 gs_fnms(df64 a, df64 b, df64 c) { return df_fnms_fast(a, b, c); }
 __device__ __forceinline__ df64 gs_div(df64 a, df64 b) { return df_div(a, b); }
+__device__ __forceinline__ df64 gs_rcp(df64 a) { return df_rcp(a); }
 __device__ __forceinline__ df64 gs_sqrt(df64 a) { return df_sqrt(a); }
 __device__ __forceinline__ df64 gs_add(df64 a, df64 b) { return df_add(a, b); }
 __device__ __forceinline__ bool gs_pos(df64 a) { return a.hi > 0.f && isfinite(a.hi); }
@@ -48,20 +50,27 @@ template <typename V> __device__ __forceinline__ V gs_zero() {
 
 // Cholesky factorisation of the damped Q x Q Gram matrix by one CTA, entries
 // held in registers.  The lower triangle is cut into 4 x 4 blocks; thread t
-// owns block t (and t + blockDim.x when NBS = 2) of the row-major packed
-// block triangle.  A (symmetric, row-major, leading dim lda) is only read, so
+// owns block t (and t + blockDim.x when NBS = 2) of the column-major packed
+// block triangle, so that the blocks of a panel and those right of it are
+// contiguous runs of threads (few, full warps).  A (symmetric, row-major, leading dim lda) is only read, so
 // a failed attempt restarts from it with a larger `extra` on the diagonal.
 //
-// Square-root-free right-looking elimination: at pivot k the owners of
-// column k publish it (unscaled) into one half of a double buffer, one
-// barrier, then every entry with i >= j > k becomes a_ij - a_ik (a_jk / a_kk)
-// (4 + 4 column values and 16 updates per thread).  The owner of a_{k+1,k+1}
-// stores its reciprocal for the next pivot.  Afterwards L_ij = a_ij / sqrt(a_jj).
+// Square-root-free right-looking elimination, one block column (4 pivots)
+// at a time: (1) the owner of the diagonal block eliminates it in registers
+// (pivots d_u, 1/d_u and the multipliers l_{j,u} = a_{j,u} / d_u) and
+// publishes them; (2) the owners of the blocks below it eliminate their rows
+// against those multipliers and publish the results w_{i,u}; (3) every block
+// right of the column takes the rank-4 update a_ij - sum_u w_iu (w_ju / d_u).
+// Each entry sees the same operations in the same order as pivot-by-pivot
+// elimination, with two barriers per 4 pivots; the published values are
+// double-buffered by block-column parity, the rows w_i stored block-innermost
+// (entry (r, v) of block row b at (4 r + v) ceil(Q/4) + b) so that a warp's
+// consecutive blocks read consecutive words.  Afterwards L_ij = a_ij / sqrt(a_jj).
 //
 // Writes L column-major (out[j * Q + i], i >= j) and 1 / L_jj (out[Q * Q + j])
-// to global memory; colbuf holds 2 * Q and pinv Q scalars of shared memory.
-// Returns false at the first non-positive or non-finite pivot, the same
-// decision in every thread, right after a barrier; returns true after a
+// to global memory; colbuf holds 32 ceil(Q/4) + 64 <= 8 Q + 96 and pinv Q
+// scalars of shared memory.  Returns false at the first non-positive or non-finite pivot, the
+// same decision in every thread, right after a barrier; returns true after a
 // final barrier, so colbuf and pinv are free again in both cases.
 // Needs (Q/4)(Q/4 + 1)/2 <= NBS * blockDim.x.
 template <typename V, int NBS>
@@ -72,6 +81,7 @@ __device__ __noinline__ bool gram_factor_reg(const V *A, int Q, int lda, double 
   V one, ex;
   gs_one(one);
   gs_from_double(extra, ex);
+  const V zero = gs_zero<V>();
   int bi[NBS], bj[NBS];
   bool own[NBS];
   V a[NBS][4][4];
@@ -79,66 +89,94 @@ __device__ __noinline__ bool gram_factor_reg(const V *A, int Q, int lda, double 
   for (int s = 0; s < NBS; ++s) {
     const int b = tid + s * NT;
     own[s] = b < nblk;
-    int r = (int)((sqrtf(8.f * (float)b + 1.f) - 1.f) * 0.5f);
-    while (r > 0 && r * (r + 1) / 2 > b) --r;
-    while ((r + 1) * (r + 2) / 2 <= b) ++r;
-    bi[s] = own[s] ? r : 0;
-    bj[s] = own[s] ? b - r * (r + 1) / 2 : 0;
+    int c = 0, off = 0;   // block column c holds blocks off .. off + Qb - c - 1
+    while (c < Qb && off + (Qb - c) <= b) off += Qb - c++;
+    bi[s] = own[s] ? c + (b - off) : 0;
+    bj[s] = own[s] ? c : 0;
 #pragma unroll
     for (int r4 = 0; r4 < 4; ++r4)
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int i = 4 * bi[s] + r4, j = 4 * bj[s] + u;
-        a[s][r4][u] = gs_zero<V>();
+        a[s][r4][u] = zero;
         if (own[s] && j <= i && i < Q) {
           a[s][r4][u] = A[(size_t)i * lda + j];
           if (i == j) a[s][r4][u] = gs_add(a[s][r4][u], ex);
         }
       }
   }
-  if (tid == 0) pinv[0] = gs_div(one, a[0][0][0]);
-  for (int k = 0; k < Q; ++k) {
-    const int kb = k >> 2, ku = k & 3;
-    V *cb = colbuf + (k & 1) * Q;
+  for (int kb = 0; kb < Qb; ++kb) {
+    V *W = colbuf + (kb & 1) * 16 * Qb;               // w_{4b+r,v} at (4 r + v) Qb + b
+    V *P = colbuf + 32 * Qb + (kb & 1) * 32;          // d[4], 1/d[4], l[j][u] at 8 + 4 j + u, flag at 24
+    // (1) the diagonal block
 #pragma unroll
-    for (int s = 0; s < NBS; ++s)
-      if (own[s] && bj[s] == kb)
+    for (int s = 0; s < NBS; ++s) {
+      if (!own[s] || bi[s] != kb || bj[s] != kb) continue;
+      bool okb = true;
 #pragma unroll
-        for (int r4 = 0; r4 < 4; ++r4) {
-          const int i = 4 * bi[s] + r4;
-          V v = a[s][r4][0];
-#pragma unroll
-          for (int u = 1; u < 4; ++u)
-            if (u == ku) v = a[s][r4][u];
-          if (i >= k && i < Q) cb[i] = v;
+      for (int u = 0; u < 4; ++u) {
+        const int k = 4 * kb + u;
+        V inv = one, lj[4];
+        if (k < Q) {
+          const V d = a[s][u][u];
+          if (!gs_pos(d)) okb = false;
+          inv = gs_rcp(d);
+          pinv[k] = inv;
+          P[u] = d;
+        } else {
+          P[u] = one;
         }
+        P[4 + u] = inv;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) lj[j] = (j > u && k < Q) ? gs_mul(a[s][j][u], inv) : zero;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j > u && j <= i) a[s][i][j] = gs_fnms(a[s][i][u], lj[j], a[s][i][j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[8 + 4 * j + u] = lj[j];
+      }
+      P[24] = okb ? one : zero;
+    }
     __syncthreads();
-    if (!gs_pos(cb[k])) {   // same value, same decision in every thread
+    if (!gs_pos(P[24])) {   // same value, same decision in every thread
       __syncthreads();
       return false;
     }
-    const V invd = pinv[k];
+    // (2) the blocks below it: w_{i,u} = a_{i,u} - sum_{v<u} w_{i,v} l_{u,v}
 #pragma unroll
     for (int s = 0; s < NBS; ++s) {
-      if (!own[s] || 4 * bj[s] + 3 <= k) continue;   // no column right of k in this block
-      V ci[4], tj[4];
+      if (!own[s] || bj[s] != kb || bi[s] <= kb) continue;
 #pragma unroll
-      for (int r4 = 0; r4 < 4; ++r4) ci[r4] = cb[min(4 * bi[s] + r4, Q - 1)];
+      for (int r4 = 0; r4 < 4; ++r4) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) tj[u] = gs_mul(cb[min(4 * bj[s] + u, Q - 1)], invd);
+        for (int u = 1; u < 4; ++u)
 #pragma unroll
-      for (int r4 = 0; r4 < 4; ++r4)
+          for (int v = 0; v < u; ++v) a[s][r4][u] = gs_fnms(a[s][r4][v], P[8 + 4 * u + v], a[s][r4][u]);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int i = 4 * bi[s] + r4, j = 4 * bj[s] + u;
-          const V nv = gs_fnms(ci[r4], tj[u], a[s][r4][u]);
-          if (j > k && j <= i && i < Q) a[s][r4][u] = nv;
-        }
-      const int k1 = k + 1;
-      if (k1 < Q && bi[s] == (k1 >> 2) && bj[s] == (k1 >> 2)) {
+        for (int u = 0; u < 4; ++u) W[(4 * r4 + u) * Qb + bi[s]] = a[s][r4][u];
+      }
+    }
+    __syncthreads();
+    // (3) the blocks right of it: rank-4 update with the published rows
+#pragma unroll
+    for (int s = 0; s < NBS; ++s) {
+      if (!own[s] || bj[s] <= kb) continue;
+      V tj[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) tj[u][v] = gs_mul(W[(4 * u + v) * Qb + bj[s]], P[4 + v]);
+#pragma unroll
+      for (int r4 = 0; r4 < 4; ++r4) {
+        V wi[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) wi[v] = W[(4 * r4 + v) * Qb + bi[s]];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
-          if (u == (k1 & 3)) pinv[k1] = gs_div(one, a[s][u][u]);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) a[s][r4][u] = gs_fnms(wi[v], tj[u][v], a[s][r4][u]);
       }
     }
   }

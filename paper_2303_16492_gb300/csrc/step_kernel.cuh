@@ -937,7 +937,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         const V *A = reinterpret_cast<const V *>(h64);
         const V *hd = reinterpret_cast<const V *>(hdiag);
         V *colbuf = reinterpret_cast<V *>(smem + lay.off_reg);   // reg is free here
-        V *pinv = colbuf + 2 * Q;
+        V *pinv = colbuf + 8 * Q + 96;   // past the factorisation's published blocks
         V *lout = static_cast<V *>(D.lfac);
         if (tid == 0) {
           double tr = 0.0;
