@@ -250,6 +250,8 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, bool tab, StepL
     size_t reg = std::max((size_t)ti * L.ldg, (size_t)ti * L.ldq);
     if (scaled) reg = std::max(reg, (size_t)QH * L.ldq);
     size_t b = reg * st;
+    if (scaled)   // the direction's blocked solves: inverted diagonal blocks and one warp's buffer at least
+      b = std::max(b, (size_t)gram_solve_scratch(QH, 1) * 8);
     if (tcp == 2)   // split-BF16 G chunk (hi, lo) | partial gradient FP32 + Ew tile
       b = std::max(std::max(b, (size_t)2 * 128 * L.qp * 2),
                    rup((size_t)128 * L.ldq * st, 128) + (size_t)128 * L.jbp * 2);
@@ -266,6 +268,11 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, bool tab, StepL
   if (tail_bytes(TI) > avail) return false;
   L.TI = TI;
   L.rows_own = own_rows_for(TI);
+  L.nsolve = 0;
+  if (scaled) {   // as many solving warps (up to 16) as the reg region has buffers for
+    const size_t spare = reg_bytes(TI) - (size_t)gram_solve_scratch(QH, 0) * 8;
+    L.nsolve = (int)std::min<size_t>(std::min<size_t>(16, (size_t)L.rows_own), spare / ((size_t)(QH + kGsB) * 8));
+  }
   off = tail0;
   L.off_reg = take(reg_bytes(TI), 128);
   L.off_ew = tcp == 3 ? L.off_reg : L.off_reg + rup((size_t)128 * L.ldq * st, 128);

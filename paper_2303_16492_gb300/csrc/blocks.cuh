@@ -115,10 +115,14 @@ __device__ __forceinline__ void ld4(const T *p, T (&v)[4]) {
 // l owns n = n0 + l + 32*b (BKN: contiguous per warp; n-major B: conflict-free
 // 16-byte reads when ldb = 4 mod 32).  Every pointer/stride used with a
 // 4-wide load is 4-element aligned.  epi(m, n, v) once per valid output.
+// A, B and bscale (or null) point into dynamic shared memory.
 template <int TN, bool AKM, bool BKN, typename T, typename Epi>
 __device__ __noinline__ void gemm_s(int M, int N, int K, const T *__restrict__ A, int lda,
                                     const T *__restrict__ B, int ldb, const T *__restrict__ bscale,
                                     Epi epi) {
+  A = smem_ptr(A);   // operands in dynamic shared memory
+  B = smem_ptr(B);
+  if (bscale) bscale = smem_ptr(bscale);
   constexpr int TM = 4;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;

@@ -206,6 +206,18 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 }
 
 // 16 consecutive 32-bit TMEM columns of this thread's lane, one wait.
+// Pointer p into this CTA's dynamic shared memory, re-derived from an extern
+// __shared__ symbol plus an offset so that loads and stores through it in a
+// non-inlined function use the shared-memory instructions: a pointer
+// parameter alone is generic, and generic accesses take the longer L1TEX path.
+// p must point into dynamic shared memory.
+extern __shared__ __align__(16) unsigned char trsgd_dyn_smem[];
+template <typename P>
+__device__ __forceinline__ P *smem_ptr(P *p) {
+  const uint32_t off = (uint32_t)(__cvta_generic_to_shared((const void *)p) - __cvta_generic_to_shared(trsgd_dyn_smem));
+  return reinterpret_cast<P *>(trsgd_dyn_smem + off);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"

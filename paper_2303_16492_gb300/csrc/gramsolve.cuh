@@ -4,7 +4,9 @@
 // (df64.cuh) for float cores; the gs_* overloads below hide the difference.
 #pragma once
 
+#include "common.cuh"
 #include "df64.cuh"
+#include "internal.h"
 
 namespace trsgd {
 
@@ -17,6 +19,7 @@ __device__ __forceinline__ double gs_div(double a, double b) { return a / b; }
 __device__ __forceinline__ double gs_rcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ double gs_sqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ double gs_add(double a, double b) { return a + b; }
+__device__ __forceinline__ double gs_neg(double a) { return -a; }
 __device__ __forceinline__ bool gs_pos(double a) { return a > 0.0 && isfinite(a); }
 __device__ __forceinline__ double gs_to_double(double a) { return a; }
 __device__ __forceinline__ void gs_from_double(double d, double &out) { out = d; }
@@ -30,6 +33,7 @@ __device__ __forceinline__ df64 gs_div(df64 a, df64 b) { return df_div(a, b); }
 __device__ __forceinline__ df64 gs_rcp(df64 a) { return df_rcp(a); }
 __device__ __forceinline__ df64 gs_sqrt(df64 a) { return df_sqrt(a); }
 __device__ __forceinline__ df64 gs_add(df64 a, df64 b) { return df_add(a, b); }
+__device__ __forceinline__ df64 gs_neg(df64 a) { return df_neg(a); }
 __device__ __forceinline__ bool gs_pos(df64 a) { return a.hi > 0.f && isfinite(a.hi); }
 __device__ __forceinline__ double gs_to_double(df64 a) { return df_to_double(a); }
 __device__ __forceinline__ void gs_from_double(double d, df64 &out) { out = df_from_double(d); }
@@ -76,6 +80,9 @@ template <typename V> __device__ __forceinline__ V gs_zero() {
 template <typename V, int NBS>
 __device__ __noinline__ bool gram_factor_reg(const V *A, int Q, int lda, double extra, V *colbuf, V *pinv,
                                              V *out) {
+  A = smem_ptr(A);
+  colbuf = smem_ptr(colbuf);
+  pinv = smem_ptr(pinv);
   const int tid = threadIdx.x, NT = blockDim.x;
   const int Qb = (Q + 3) >> 2, nblk = Qb * (Qb + 1) / 2;
   V one, ex;
@@ -199,6 +206,121 @@ __device__ __noinline__ bool gram_factor_reg(const V *A, int Q, int lda, double 
   for (int j = tid; j < Q; j += NT) out[(size_t)Q * Q + j] = gs_sqrt(pinv[j]);
   __syncthreads();   // colbuf and pinv may be reused by the caller
   return true;
+}
+
+
+// Inverse of the b-th diagonal block of L (a forward substitution per column,
+// the columns independent): one warp, lane j computing column j,
+//   X_jj = 1 / L_jj,  X_ij = -(1 / L_ii) sum_{j <= k < i} L_ik X_kj  (i > j),
+// zero above the diagonal.  L is read column-major at pitch ldl (entry (q, k)
+// at Lc[k ldl + q]) with 1 / L_qq at ivc[q]; block b's entry (i, j) goes to
+// Dc[b kGsB (kGsB + 1) + j (kGsB + 1) + i] (odd pitch: a column and a row are
+// both free of bank conflicts).  Each lane reads back only its own column.
+template <typename V>
+__device__ __noinline__ void gram_block_inverse(const V *Lc, int ldl, const V *ivc, int Q, int b, V *Dc) {
+  const int j = threadIdx.x & 31, q0 = kGsB * b, nbk = min(kGsB, Q - q0);
+  if (j >= nbk) return;
+  Lc = smem_ptr(Lc);
+  ivc = smem_ptr(ivc);
+  Dc = smem_ptr(Dc);
+  V *X = Dc + b * kGsB * (kGsB + 1) + j * (kGsB + 1);
+  const V zero = gs_zero<V>();
+  for (int i = 0; i < nbk; ++i) {
+    const V *Li = Lc + q0 + i;   // L(q0 + i, q0 + k) at Li[(q0 + k) ldl]
+    V a0 = zero, a1 = zero, a2 = zero, a3 = zero;   // - sum L_ik X_kj in four parts
+    int k = j;
+    for (; k + 3 < i; k += 4) {
+      a0 = gs_fnms(Li[(q0 + k) * ldl], X[k], a0);
+      a1 = gs_fnms(Li[(q0 + k + 1) * ldl], X[k + 1], a1);
+      a2 = gs_fnms(Li[(q0 + k + 2) * ldl], X[k + 2], a2);
+      a3 = gs_fnms(Li[(q0 + k + 3) * ldl], X[k + 3], a3);
+    }
+    for (; k < i; ++k) a0 = gs_fnms(Li[(q0 + k) * ldl], X[k], a0);
+    const V s = gs_add(gs_add(a0, a1), gs_add(a2, a3));
+    X[i] = i < j ? zero : (i == j ? ivc[q0 + i] : gs_mul(s, ivc[q0 + i]));
+  }
+}
+
+// One warp solves h x = -g^T for one row g of the gradient, with h = L L^T
+// factored by gram_factor_reg, block by block with the inverted diagonal
+// blocks D_b^{-1} of gram_block_inverse:
+//   forward   y_b = D_b^{-1} (-g_b - sum_{c<b} L_bc y_c),
+//   backward  x_b = D_b^{-T} (y_b - sum_{c>b} L_cb^T x_c),
+// lane l holding entry kGsB b + l of each block.  Every sum is a dot product
+// with independent terms, so a sweep has nb sequential steps instead of Q.
+// `row` (shared memory, Q entries) holds g on entry and x on return (x = 0
+// when ok is false); buf is this warp's Q + kGsB entries of shared memory.
+template <typename T, typename V>
+__device__ __noinline__ void gram_solve_row(const V *Lc, int ldl, const V *Dc, int Q, bool ok, T *row, V *buf) {
+  const int lane = threadIdx.x & 31, nb = (Q + kGsB - 1) / kGsB;
+  const V zero = gs_zero<V>();
+  Lc = smem_ptr(Lc);
+  Dc = smem_ptr(Dc);
+  row = smem_ptr(row);
+  buf = smem_ptr(buf);
+  V *ys = buf, *rs = buf + Q;
+  if (!ok) {
+    for (int q = lane; q < Q; q += 32) row[q] = T(0);
+    return;
+  }
+  for (int b = 0; b < nb; ++b) {   // forward
+    const int q0 = kGsB * b, nbk = min(kGsB, Q - q0), q = q0 + lane, qc = min(q, Q - 1);
+    V a0, a1 = zero, a2 = zero, a3 = zero;
+    gs_from_double(q < Q ? -(double)row[qc] : 0.0, a0);
+    for (int k = 0; k < q0; k += 4) {   // q0 is a multiple of 4
+      a0 = gs_fnms(Lc[k * ldl + qc], ys[k], a0);
+      a1 = gs_fnms(Lc[(k + 1) * ldl + qc], ys[k + 1], a1);
+      a2 = gs_fnms(Lc[(k + 2) * ldl + qc], ys[k + 2], a2);
+      a3 = gs_fnms(Lc[(k + 3) * ldl + qc], ys[k + 3], a3);
+    }
+    rs[lane] = gs_add(gs_add(a0, a1), gs_add(a2, a3));
+    __syncwarp();
+    const V *Db = Dc + b * kGsB * (kGsB + 1);   // entry (i, j) at Db[j (kGsB + 1) + i]
+    const int lc = min(lane, nbk - 1);
+    a0 = a1 = a2 = a3 = zero;                     // - sum_j D(l, j) r_j
+    int j = 0;
+    for (; j + 3 < nbk; j += 4) {
+      a0 = gs_fnms(Db[j * (kGsB + 1) + lc], rs[j], a0);
+      a1 = gs_fnms(Db[(j + 1) * (kGsB + 1) + lc], rs[j + 1], a1);
+      a2 = gs_fnms(Db[(j + 2) * (kGsB + 1) + lc], rs[j + 2], a2);
+      a3 = gs_fnms(Db[(j + 3) * (kGsB + 1) + lc], rs[j + 3], a3);
+    }
+    for (; j < nbk; ++j) a0 = gs_fnms(Db[j * (kGsB + 1) + lc], rs[j], a0);
+    const V y = gs_neg(gs_add(gs_add(a0, a1), gs_add(a2, a3)));
+    __syncwarp();
+    if (q < Q) ys[q] = y;
+    __syncwarp();
+  }
+  for (int b = nb - 1; b >= 0; --b) {   // backward; ys[k] holds x_k for k beyond block b
+    const int q0 = kGsB * b, nbk = min(kGsB, Q - q0), q = q0 + lane, qc = min(q, Q - 1);
+    V a0 = q < Q ? ys[qc] : zero, a1 = zero, a2 = zero, a3 = zero;
+    const V *Lr = Lc + (size_t)qc * ldl;        // L(k, q) at Lr[k]
+    int k = q0 + nbk;
+    for (; k + 3 < Q; k += 4) {
+      a0 = gs_fnms(Lr[k], ys[k], a0);
+      a1 = gs_fnms(Lr[k + 1], ys[k + 1], a1);
+      a2 = gs_fnms(Lr[k + 2], ys[k + 2], a2);
+      a3 = gs_fnms(Lr[k + 3], ys[k + 3], a3);
+    }
+    for (; k < Q; ++k) a0 = gs_fnms(Lr[k], ys[k], a0);
+    rs[lane] = gs_add(gs_add(a0, a1), gs_add(a2, a3));
+    __syncwarp();
+    const V *Db = Dc + b * kGsB * (kGsB + 1) + min(lane, nbk - 1) * (kGsB + 1);   // D(j, l) at Db[j]
+    a0 = a1 = a2 = a3 = zero;                     // - sum_j D(j, l) r_j
+    int j = 0;
+    for (; j + 3 < nbk; j += 4) {
+      a0 = gs_fnms(Db[j], rs[j], a0);
+      a1 = gs_fnms(Db[j + 1], rs[j + 1], a1);
+      a2 = gs_fnms(Db[j + 2], rs[j + 2], a2);
+      a3 = gs_fnms(Db[j + 3], rs[j + 3], a3);
+    }
+    for (; j < nbk; ++j) a0 = gs_fnms(Db[j], rs[j], a0);
+    const V x = gs_neg(gs_add(gs_add(a0, a1), gs_add(a2, a3)));
+    __syncwarp();
+    if (q < Q) ys[q] = x;
+    __syncwarp();
+  }
+  for (int q = lane; q < Q; q += 32) row[q] = (T)gs_to_double(ys[q]);
 }
 
 }  // namespace trsgd

@@ -53,6 +53,7 @@ struct StepLayout {
   int pstride;    // per-sample stride of the chain intermediates
   int qp, jbp;    // tensor-core path: Q and samples padded to 16 (tile extents)
   int tcp;        // BF16 pieces per tensor-core operand: 2 (BF16-mixed), 3 (FP32), 0 (FMA units)
+  int nsolve;     // scaled variant: warps that solve rows of the direction (one buffer each in the reg region)
   // off_sb aliases the region [off_reg, total): the staged slices are dead
   // before the Gram / chunk buffers and the CDF scratch are written
   size_t off_desc, off_idx, off_col, off_wt, off_bar, off_x, off_z, off_reg, off_h64,
@@ -62,6 +63,19 @@ struct StepLayout {
   int cw0;        // first CTA that takes samples: 1 for the scaled variant with C > 1 (CTA 0
                   // factorises the Gram matrix meanwhile), else 0
 };
+
+// Block size of the scaled variant's blocked triangular solves (gramsolve.cuh):
+// the diagonal blocks of the Gram factor L are kGsB x kGsB (the last one
+// Q - kGsB (nb - 1) wide), nb = ceil(Q / kGsB).
+constexpr int kGsB = 32;
+
+// Entries (8 bytes each) of shared memory the blocked solves use: the
+// inverted diagonal blocks of L (block b at b kGsB (kGsB + 1), column j of it
+// at + j (kGsB + 1); the last block only as wide as it is), then one buffer of
+// Q + kGsB per solving warp.
+__host__ __device__ constexpr int gram_solve_scratch(int Q, int warps) {
+  return ((Q - 1) / kGsB) * kGsB * (kGsB + 1) + (Q - (Q - 1) / kGsB * kGsB) * (kGsB + 1) + warps * (Q + kGsB);
+}
 
 // Device buffers of the optimal distribution (sized for the largest J_n).
 struct OptBuffers {

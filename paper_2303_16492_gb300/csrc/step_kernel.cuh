@@ -142,11 +142,15 @@ __device__ __forceinline__ T dotk(const T *p, const T *s) {
 // 32 / (RU / CB) samples.  Each output is a dot product of a row of P_q (read
 // with stride RU when P_q is the column-major staged slice, FIRST) with a
 // column of S_q, summed a = 0 .. RU-1 in order with fused multiply-adds.
+// src, sfac and dst point into dynamic shared memory.
 template <int RU, int CB, bool FIRST, typename T>
 __device__ __noinline__ void chain_factor_uniform(const T *src, int sstride, const T *sfac, int qpad, T *dst,
                                                   int dstride, int jb) {
   static_assert(RU % 2 == 0 && RU % CB == 0, "even rank, whole lane groups");
   constexpr int LPS = RU / CB, G = 32 / LPS;
+  src = smem_ptr(src);   // all three in dynamic shared memory
+  sfac = smem_ptr(sfac);
+  dst = smem_ptr(dst);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int g = lane / LPS, bb = lane - g * LPS;
   const bool lane_ok = g < G;
@@ -1114,8 +1118,9 @@ __global__ void __launch_bounds__(kMaxThreads)
       // every CTA copies the factor (written by CTA 0 before the chunk loop's
       // barriers) into its own shared memory at an odd pitch, so that both a
       // column (forward solve) and a row (backward solve) of L are read
-      // without bank conflicts; then one warp per owned row solves
-      // L y = -g^T and L^T x = y in the Gram-solve scalar.
+      // without bank conflicts, and inverts its 32 x 32 diagonal blocks (one
+      // warp each, in the reg region, free here); then one warp per owned row
+      // solves L y = -g^T and L^T x = y blockwise in the Gram-solve scalar.
       using V = typename GramScalar<T>::type;
       const int ldl = Q | 1;
       V *Lc = reinterpret_cast<V *>(h64);
@@ -1142,71 +1147,27 @@ __global__ void __launch_bounds__(kMaxThreads)
         for (int q = tid; q < Q; q += NT) ivc[q] = gs_ldcg(Lg + (size_t)Q * Q + q);
       }
       __syncthreads();
-      for (int rr = warp; rr < own_rows; rr += nw) {
+      V *Dc = reinterpret_cast<V *>(reg);   // inverted diagonal blocks, then a buffer per solving warp
+      const int nbq = (Q + kGsB - 1) / kGsB;
+      if (ok && warp < nbq) gram_block_inverse<V>(Lc, ldl, ivc, Q, warp, Dc);
+      __syncthreads();
+      const int nsv = min(nw, lay.nsolve);   // solving warps, one buffer each after the blocks
+      V *wbuf = Dc + gram_solve_scratch(Q, warp);
+      for (int rr = warp; warp < nsv && rr < own_rows; rr += nsv) {
         const int i = own_row(rr);
-        V y[QM];
-#pragma unroll
-        for (int m = 0; m < QM; ++m) {
-          const int q = lane + 32 * m;
-          gs_from_double((q < Q) ? -(double)gown[(size_t)rr * ldq + q] : 0.0, y[m]);
-        }
-        if (ok) {
-          // branch-free sweeps: every lane of a live 32-block updates (clamped
-          // addresses, results selected); blocks the sweep has left are skipped
-          // with warp-uniform branches
-          int qc[QM];
-#pragma unroll
-          for (int m = 0; m < QM; ++m) qc[m] = min(lane + 32 * m, Q - 1);
-          for (int k = 0; k < Q; ++k) {        // L y = -g^T (column sweep)
-            const int mk = k >> 5;
-            V yk = gs_shfl(y[0], k & 31);
-#pragma unroll
-            for (int m = 1; m < QM; ++m) {
-              const V sm = gs_shfl(y[m], k & 31);
-              if (mk == m) yk = sm;
-            }
-            yk = gs_mul(yk, ivc[k]);
-            const V *col = Lc + k * ldl;
-#pragma unroll
-            for (int m = 0; m < QM; ++m) {
-              if (m < mk || 32 * m >= Q) continue;
-              const int q = lane + 32 * m;
-              const V nv = gs_fnms(col[qc[m]], yk, y[m]);
-              y[m] = (q > k) ? nv : ((q == k) ? yk : y[m]);
-            }
-          }
-          for (int k = Q - 1; k >= 0; --k) {   // L^T x = y (row sweep)
-            const int mk = k >> 5;
-            V xk = gs_shfl(y[0], k & 31);
-#pragma unroll
-            for (int m = 1; m < QM; ++m) {
-              const V sm = gs_shfl(y[m], k & 31);
-              if (mk == m) xk = sm;
-            }
-            xk = gs_mul(xk, ivc[k]);
-#pragma unroll
-            for (int m = 0; m < QM; ++m) {
-              if (m > mk) continue;
-              const int q = lane + 32 * m;
-              const V nv = gs_fnms(Lc[qc[m] * ldl + k], xk, y[m]);
-              y[m] = (q < k) ? nv : ((q == k) ? xk : y[m]);
-            }
-          }
-        } else {
-#pragma unroll
-          for (int m = 0; m < QM; ++m) gs_from_double(0.0, y[m]);
-        }
+        T *grow = gown + (size_t)rr * ldq;
+        gram_solve_row<T, V>(Lc, ldl, Dc, Q, ok, grow, wbuf);   // g in, p out
         __syncwarp();
 #pragma unroll
         for (int m = 0; m < QM; ++m) {
           const int q = lane + 32 * m;
           if (q >= Q) continue;
           const size_t gi = (size_t)i * Q + q;
-          const T p = (T)gs_to_double(y[m]);
+          const T p = grow[q];
           const T nv = ld_l2(Gn + gi) + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
           if (!isfinite(nv)) latch_status(D.status, kStatusNumeric);
           Gn[gi] = nv;
-          gown[(size_t)rr * ldq + q] = nv;
+          grow[q] = nv;
           if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
         }
       }

@@ -12,6 +12,7 @@ namespace trsgd {
 // decision in every thread).
 template <typename T>
 __device__ __noinline__ bool cholesky_cta_t(T *A, int m, int ld) {
+  A = smem_ptr(A);   // dynamic shared memory
   const int tid = threadIdx.x, NT = blockDim.x;
   for (int k = 0; k < m; ++k) {
     __syncthreads();
