@@ -122,10 +122,11 @@ cudaError_t launch_step(int core_dtype, int x_dtype, int rmax, const ProbDesc *d
 cudaError_t launch_advance_counter(long long *t, long long T, int set, cudaStream_t s);
 cudaError_t step_kernel_prepare(int core_dtype, int x_dtype, int rmax, const StepLayout &lay);
 int step_max_smem();
-// instantiated per (core type, fiber type, BF16 pieces) in step_<variant>.cu
-template <typename T, typename XT, int RMAX, int NPC>
+// instantiated per (core type, fiber type, BF16 pieces) in step_<variant>.cu, with
+// the scaled variant compiled in (SC, step_<variant>_scaled.cu) or out
+template <typename T, typename XT, int RMAX, int NPC, bool SC>
 cudaError_t step_prepare_t(const StepLayout &lay);
-template <typename T, typename XT, int RMAX, int NPC>
+template <typename T, typename XT, int RMAX, int NPC, bool SC>
 cudaError_t step_launch_t(const ProbDesc *descs, int nprob, const StepLayout &lay, int threads, long long t0,
                           int nsteps, const long long *t_dev, cudaStream_t s);
 

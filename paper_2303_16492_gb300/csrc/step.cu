@@ -8,12 +8,20 @@ namespace trsgd {
 // RMAX: register length of one chain row; the smallest of 4, 8, 12, 16 that
 // holds every rank of the problem.  Pieces: lay.tcp (FP32 cores only; the
 // BF16-mixed mode always runs on two pieces).
-#define TRSGD_DISPATCH_R(FN, T, XT, NPC, ...)                      \
+#define TRSGD_DISPATCH_RS(FN, T, XT, NPC, SC, ...)                 \
   do {                                                             \
-    if (rmax <= 4) return FN<T, XT, 4, NPC>(__VA_ARGS__);          \
-    if (rmax <= 8) return FN<T, XT, 8, NPC>(__VA_ARGS__);          \
-    if (rmax <= 12) return FN<T, XT, 12, NPC>(__VA_ARGS__);        \
-    return FN<T, XT, 16, NPC>(__VA_ARGS__);                        \
+    if (rmax <= 4) return FN<T, XT, 4, NPC, SC>(__VA_ARGS__);      \
+    if (rmax <= 8) return FN<T, XT, 8, NPC, SC>(__VA_ARGS__);      \
+    if (rmax <= 12) return FN<T, XT, 12, NPC, SC>(__VA_ARGS__);    \
+    return FN<T, XT, 16, NPC, SC>(__VA_ARGS__);                    \
+  } while (0)
+
+// the scaled variant's code only in the kernels of launches that hold a
+// scaled problem (its Gram buffers in the layout)
+#define TRSGD_DISPATCH_R(FN, T, XT, NPC, ...)                                        \
+  do {                                                                               \
+    if (lay.QH > 0) TRSGD_DISPATCH_RS(FN, T, XT, NPC, true, __VA_ARGS__);            \
+    TRSGD_DISPATCH_RS(FN, T, XT, NPC, false, __VA_ARGS__);                           \
   } while (0)
 
 #define TRSGD_DISPATCH(FN, ...)                                                      \

@@ -2,5 +2,5 @@
 #include "step_kernel.cuh"
 
 namespace trsgd {
-TRSGD_STEP_INSTANTIATE(float, __nv_bfloat16, 2)
+TRSGD_STEP_INSTANTIATE(float, __nv_bfloat16, 2, false)
 }  // namespace trsgd

@@ -2,5 +2,5 @@
 #include "step_kernel.cuh"
 
 namespace trsgd {
-TRSGD_STEP_INSTANTIATE(float, float, 3)
+TRSGD_STEP_INSTANTIATE(float, float, 3, false)
 }  // namespace trsgd

@@ -2,5 +2,5 @@
 #include "step_kernel.cuh"
 
 namespace trsgd {
-TRSGD_STEP_INSTANTIATE(double, double, 0)
+TRSGD_STEP_INSTANTIATE(double, double, 0, false)
 }  // namespace trsgd

@@ -224,7 +224,7 @@ __device__ __forceinline__ T step_delta(int rule, T alpha, T eta, T b, double ep
   return sc * p;
 }
 
-template <typename T, typename XT, int RMAX, int NPC>
+template <typename T, typename XT, int RMAX, int NPC, bool SC>
 __global__ void __launch_bounds__(kMaxThreads)
     step_cluster_kernel(const ProbDesc *__restrict__ descs, StepLayout lay, long long t0, int nsteps,
                         const long long *__restrict__ t_dev) {
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kMaxThreads)
   // dims and ranks read from the shared descriptor: small per-thread arrays
   // indexed at run time would live in local memory (L2 round trips)
   const int *I = D.I, *R = D.R;
-  const bool scaled = D.variant == 1;
+  const bool scaled = SC && D.variant == 1;   // SC false: the scaled variant is compiled out
   const bool rec = D.dbg && pidx == 0;
   int ru = R[0];   // the common rank when all ranks are equal, else 0
   for (int k = 1; k < N; ++k)
@@ -1228,15 +1228,15 @@ __global__ void __launch_bounds__(kMaxThreads)
   }
 }
 
-template <typename T, typename XT, int RMAX, int NPC>
+template <typename T, typename XT, int RMAX, int NPC, bool SC>
 cudaError_t step_prepare_t(const StepLayout &lay) {
-  auto k = step_cluster_kernel<T, XT, RMAX, NPC>;
+  auto k = step_cluster_kernel<T, XT, RMAX, NPC, SC>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lay.total);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
-template <typename T, typename XT, int RMAX, int NPC>
+template <typename T, typename XT, int RMAX, int NPC, bool SC>
 cudaError_t step_launch_t(const ProbDesc *descs, int nprob, const StepLayout &lay, int threads, long long t0,
                           int nsteps, const long long *t_dev, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
@@ -1251,19 +1251,20 @@ cudaError_t step_launch_t(const ProbDesc *descs, int nprob, const StepLayout &la
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, step_cluster_kernel<T, XT, RMAX, NPC>, descs, lay, t0, nsteps, t_dev);
+  return cudaLaunchKernelEx(&cfg, step_cluster_kernel<T, XT, RMAX, NPC, SC>, descs, lay, t0, nsteps, t_dev);
 }
 
-// One translation unit per (core type, fiber type, pieces) instantiates the
-// four chain-row lengths, so that the variants compile in parallel.
-#define TRSGD_STEP_INSTANTIATE_R(T, XT, R, NPC)                                                        \
-  template cudaError_t step_prepare_t<T, XT, R, NPC>(const StepLayout &);                              \
-  template cudaError_t step_launch_t<T, XT, R, NPC>(const ProbDesc *, int, const StepLayout &, int,   \
-                                                    long long, int, const long long *, cudaStream_t);
-#define TRSGD_STEP_INSTANTIATE(T, XT, NPC)      \
-  TRSGD_STEP_INSTANTIATE_R(T, XT, 4, NPC)       \
-  TRSGD_STEP_INSTANTIATE_R(T, XT, 8, NPC)       \
-  TRSGD_STEP_INSTANTIATE_R(T, XT, 12, NPC)      \
-  TRSGD_STEP_INSTANTIATE_R(T, XT, 16, NPC)
+// One translation unit per (core type, fiber type, pieces, scaled variant
+// compiled in) instantiates the four chain-row lengths, so that the variants
+// compile in parallel.
+#define TRSGD_STEP_INSTANTIATE_R(T, XT, R, NPC, SC)                                                      \
+  template cudaError_t step_prepare_t<T, XT, R, NPC, SC>(const StepLayout &);                            \
+  template cudaError_t step_launch_t<T, XT, R, NPC, SC>(const ProbDesc *, int, const StepLayout &, int, \
+                                                        long long, int, const long long *, cudaStream_t);
+#define TRSGD_STEP_INSTANTIATE(T, XT, NPC, SC)      \
+  TRSGD_STEP_INSTANTIATE_R(T, XT, 4, NPC, SC)       \
+  TRSGD_STEP_INSTANTIATE_R(T, XT, 8, NPC, SC)       \
+  TRSGD_STEP_INSTANTIATE_R(T, XT, 12, NPC, SC)      \
+  TRSGD_STEP_INSTANTIATE_R(T, XT, 16, NPC, SC)
 
 }  // namespace trsgd
