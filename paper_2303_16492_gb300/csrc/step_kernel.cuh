@@ -16,10 +16,11 @@
 //      sampled subchain rows Z(j, r + r' R_n) = P_j(r', r),
 //      P_j = G_{n+1}(i_{n+1}) ... G_{n-1}(i_{n-1}), factor by factor;
 //   S  (scaled variant) partial Gram Z^T D Z, reduced over the cluster into
-//      CTA 0, which factors h + eta^t I (Cholesky in the Gram-solve scalar:
-//      FP64, or double-float for float cores; damping grown on failure) and
-//      writes the factor to global memory.  In the scaled variant CTA 0 takes
-//      no samples, so the factorisation overlaps the other CTAs' B and C;
+//      CTA 0, which factors h + eta^t I (blocked square-root-free Cholesky
+//      in the Gram-solve scalar: FP64, or double-float for float cores;
+//      damping grown on failure) and writes the factor to global memory.  In
+//      the scaled variant CTA 0 takes no samples, so the factorisation
+//      overlaps the other CTAs' B and C;
 //   B  per chunk of G_n rows: residual E = G_n Z^T - X_S (Eq. S_gradient),
 //      weighted by 1/(|F| J_n p_F);
 //   C  partial gradient (E D) Z of this CTA's samples.  B and C run on the
@@ -30,8 +31,9 @@
 //      memory, each element summed in a fixed order (owner c pulls CTAs
 //      c+1, c+2, ... mod C: deterministic), then the step rule (fixed alpha
 //      or AdaGrad) on the rows this CTA owns, written to G_n in HBM;
-//   scaled: p = -g h^{-1} on the owned rows by two triangular solves
-//      against CTA 0's factor (Eq. scaledsg_direction, damped form);
+//   scaled: p = -g h^{-1} on the owned rows by two blocked triangular solves
+//      against CTA 0's factor, whose 32 x 32 diagonal blocks every CTA
+//      inverts first (Eq. scaledsg_direction, damped form);
 //   Euclidean / leverage distribution: CTA 0 rebuilds the table of core n for
 //      the next iteration (Lemma euc_est, Lemma lev_est).
 //
@@ -39,6 +41,9 @@
 // the last chunk of iteration t has consumed the fibers, the upper half of
 // each CTA issues A1-A3 of t+1 (named barrier 1) while the lower half
 // reduces and updates; both meet at the closing cluster barrier.
+//
+// The template argument SC compiles the scaled variant in; launches without
+// a scaled problem use the instantiation without it (fewer registers).
 //
 // Cluster barriers (barrier.cluster, release/acquire) separate the phases.
 // Cores and sampling tables are read through L2 only (ld.global.cg /
