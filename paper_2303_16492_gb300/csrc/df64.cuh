@@ -2,7 +2,7 @@
 // unevaluated sum hi + lo of two floats (about 48 significant bits).  Built
 // from the error-free transformations of Knuth (two-sum, TAOCP vol. 2) and
 // Dekker (fast two-sum; two-product, here through a fused multiply-add), with
-// one Newton correction for division and square root.  Used for the scaled
+// one Newton correction for reciprocal and square root.  Used for the scaled
 // variant's Gram factorisation and triangular solves, where native FP64 is
 // about 60x slower than FP32 on this GPU.
 #pragma once
@@ -43,14 +43,11 @@ __device__ __forceinline__ df64 df_mul(df64 a, df64 b) {
   return df_fast_two_sum(p, e);
 }
 
-// c - a * b
-__device__ __forceinline__ df64 df_fnms(df64 a, df64 b, df64 c) { return df_add(c, df_neg(df_mul(a, b))); }
-
 // c - a * b with one renormalisation: the leading product a.hi b.hi is split
 // exactly (Dekker's two-product through an FMA), its difference with c.hi is
 // formed exactly (Knuth's two-sum), and the remaining small terms (the
 // product's error, the cross terms, c.lo) are added in float before a final
-// fast two-sum.  15 float operations instead of the 27 of df_fnms; the extra
+// fast two-sum.  15 float operations instead of the 27 of df_add(c, -df_mul(a, b)); the extra
 // rounding is a float rounding of terms of relative size 2^-24, so the
 // result keeps about 44 of the 48 bits.
 __device__ __forceinline__ df64 df_fnms_fast(df64 a, df64 b, df64 c) {
@@ -64,13 +61,6 @@ __device__ __forceinline__ df64 df_fnms_fast(df64 a, df64 b, df64 c) {
   lo = fmaf(-a.lo, b.hi, lo);
   lo += err;
   return df_fast_two_sum(s, lo);
-}
-
-__device__ __forceinline__ df64 df_div(df64 a, df64 b) {
-  const float q1 = a.hi / b.hi;
-  const df64 r = df_add(a, df_neg(df_mul(df64{q1, 0.f}, b)));
-  const float q2 = r.hi / b.hi;
-  return df_fast_two_sum(q1, q2);
 }
 
 // 1 / b: the fast approximate float reciprocal (relative error d0 of a few

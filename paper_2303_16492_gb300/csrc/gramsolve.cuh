@@ -15,7 +15,6 @@ template <> struct GramScalar<double> { using type = double; };
 
 __device__ __forceinline__ double gs_mul(double a, double b) { return a * b; }
 __device__ __forceinline__ double gs_fnms(double a, double b, double c) { return fma(-a, b, c); }   // c - a b
-__device__ __forceinline__ double gs_div(double a, double b) { return a / b; }
 __device__ __forceinline__ double gs_rcp(double a) { return 1.0 / a; }
 __device__ __forceinline__ double gs_sqrt(double a) { return sqrt(a); }
 __device__ __forceinline__ double gs_add(double a, double b) { return a + b; }
@@ -24,12 +23,10 @@ __device__ __forceinline__ bool gs_pos(double a) { return a > 0.0 && isfinite(a)
 __device__ __forceinline__ double gs_to_double(double a) { return a; }
 __device__ __forceinline__ void gs_from_double(double d, double &out) { out = d; }
 __device__ __forceinline__ void gs_one(double &out) { out = 1.0; }
-__device__ __forceinline__ double gs_shfl(double a, int src) { return __shfl_sync(0xffffffffu, a, src); }
 __device__ __forceinline__ double gs_ldcg(const double *p) { return __ldcg(p); }
 
 __device__ __forceinline__ df64 gs_mul(df64 a, df64 b) { return df_mul(a, b); }
 __device__ __forceinline__ df64 gs_fnms(df64 a, df64 b, df64 c) { return df_fnms_fast(a, b, c); }
-__device__ __forceinline__ df64 gs_div(df64 a, df64 b) { return df_div(a, b); }
 __device__ __forceinline__ df64 gs_rcp(df64 a) { return df_rcp(a); }
 __device__ __forceinline__ df64 gs_sqrt(df64 a) { return df_sqrt(a); }
 __device__ __forceinline__ df64 gs_add(df64 a, df64 b) { return df_add(a, b); }
@@ -38,9 +35,6 @@ __device__ __forceinline__ bool gs_pos(df64 a) { return a.hi > 0.f && isfinite(a
 __device__ __forceinline__ double gs_to_double(df64 a) { return df_to_double(a); }
 __device__ __forceinline__ void gs_from_double(double d, df64 &out) { out = df_from_double(d); }
 __device__ __forceinline__ void gs_one(df64 &out) { out = df64{1.f, 0.f}; }
-__device__ __forceinline__ df64 gs_shfl(df64 a, int src) {
-  return df64{__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src)};
-}
 __device__ __forceinline__ df64 gs_ldcg(const df64 *p) {
   const float2 v = __ldcg(reinterpret_cast<const float2 *>(p));
   return df64{v.x, v.y};
