@@ -194,6 +194,26 @@ def test_scaled_variant_steps(prec, damping):
         _compare_step(case, rec, tol)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("ranks", [[3, 11, 3], [6, 8, 7]])
+def test_scaled_variant_ragged_diagonal_blocks(prec, ranks):
+    """Eq. scaledsg_direction through the blocked solves when Q is not a
+    multiple of their 32-row diagonal blocks: Q = 33 (the last block one row)
+    and 9 for ranks 3, 11, 3; Q = 48, 56, 42 (two blocks, the second ragged)
+    for ranks 6, 8, 7; FP64 and double-float solves."""
+    case = Case(dims=[12, 11, 10], ranks=ranks, J=120, prec=prec, alpha=0.3, variant=ob.VARIANT_SCALED,
+                damping=0.05)
+    case.solver.set_debug(True)
+    tol = 1e-11 if prec == 0 else 1e-4
+    for t in range(6):
+        if prec == 1:
+            for k, G in enumerate(case.device_cores()):
+                case.state.cores[k] = G
+        rec = ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        _compare_step(case, rec, tol)
+
+
 @pytest.mark.parametrize("units", ["pieces", "fma"])
 @pytest.mark.parametrize("J_H", [0, 70])
 def test_scaled_variant_row_chunks(units, J_H):
