@@ -318,3 +318,100 @@ def test_adjoint_all_cores_central_differences(n):
         assert np.allclose(fd, grads[k], rtol=1e-6, atol=1e-8)
     g = ob.estimate_gradient(cores, X, n, idx, pF)[3]
     assert np.allclose(tr.unfold2(grads[n]), g, rtol=1e-12, atol=1e-14)
+
+
+def test_hessian_mean_with_independent_H_by_enumeration():
+    """Sec. 3.3, the unbiased-Hessian lemma: with |H| i.i.d. draws from a
+    non-uniform p, E[h] = Z^T Z / J_n, Z = G^{!=n}_{[2]} in full.  Exact
+    expectation by enumerating every ordered pair of columns (|H| = 2, weight
+    p(c1) p(c2)): a normalisation by any count other than |H| (for instance
+    the 1/(|F| J_n) printed in Eq. S_hessian, with |F| != |H|) moves the
+    mean by the ratio of the two counts."""
+    cores = random_cores(DIMS, RANKS, seed=41)
+    for n in range(3):
+        dists = [ob.euclidean_dist(G) for G in cores]
+        idx_all = _all_columns(DIMS, n)
+        q = ob.sample_probability(idx_all, n, dists)
+        Zf = tr.subchain_unfold(cores, n)
+        Jn = Zf.shape[0]
+        assert abs(q.sum() - 1.0) < 1e-12 and np.ptp(q) > 0
+        mean = np.zeros((Zf.shape[1], Zf.shape[1]))
+        for c1 in range(Jn):
+            for c2 in range(Jn):
+                rows = [c1, c2]
+                mean += q[c1] * q[c2] * ob.preconditioner(Zf[rows], q[rows], Jn)
+        assert np.allclose(mean, Zf.T @ Zf / Jn, rtol=1e-12, atol=1e-14)
+
+
+def test_step_hessian_mean_uses_the_H_batch():
+    """The step's own h with an independent H (|H| = 7, |F| = 3, Euclidean
+    p_H): alpha = 0 keeps the cores fixed, so over M iterations the mean of
+    the recorded h minus the damping is a Monte-Carlo estimate of
+    Z^T Z / J_n (unbiased-Hessian lemma, Sec. 3.3).  Each entry lies within
+    5 standard errors (its variance from the exact single-draw enumeration);
+    a 1/(|F| J_n) normalisation would put the mean at 7/3 of the target."""
+    cores = random_cores(DIMS, RANKS, seed=42)
+    X = np.random.default_rng(43).standard_normal(DIMS)
+    n, JH, M, damping = 1, 7, 1500, 1e-3
+    cfg = ob.Config(J=3, J_H=JH, dist=ob.DIST_EUCLIDEAN, variant=ob.VARIANT_SCALED, alpha=0.0,
+                    damping=damping, seed=44)
+    st = ob.State.new(cores)
+    hs = np.array([ob.step(st, X, cfg, t, force_mode=n)["h"] for t in range(M)])
+    Q = hs.shape[1]
+    hs -= damping * np.eye(Q)[None]
+    dists = [ob.euclidean_dist(G) for G in cores]
+    idx_all = _all_columns(DIMS, n)
+    q = ob.sample_probability(idx_all, n, dists)
+    Zf = tr.subchain_unfold(cores, n)
+    Jn = Zf.shape[0]
+    target = Zf.T @ Zf / Jn
+    singles = np.einsum("ca,cb->cab", Zf, Zf) / (q[:, None, None] * Jn)
+    var1 = np.einsum("c,cab->ab", q, (singles - target[None]) ** 2)
+    se = np.sqrt(var1 / (JH * M)) + 1e-15
+    assert np.all(np.abs(hs.mean(axis=0) - target) < 5 * se)
+    wrong = target * JH / 3
+    assert np.mean(np.abs(hs.mean(axis=0) - wrong) > 5 * se) > 0.5
+
+
+def test_damping_ladder_sequence_and_failure():
+    """Reading of the damped preconditioner (Sec. 3.3): when the Cholesky
+    factorisation of h + eta I fails, the damping becomes
+    eta + 1e-12 tr(h)/Q * 10^m for m = 0, 1, ..., 6, and the step fails after
+    that.  h = diag(1, 1, 1, -c) fails while the added damping is below c:
+    c = 1e-9 first factors at m = 4 (7.5e-9 > 1e-9 > 7.5e-10); c = 1 never
+    does; a zero h (no trace to scale) fails at once."""
+    c = 1e-9
+    h = np.diag([1.0, 1.0, 1.0, -c])
+    L, used = ob.cholesky_damped(h, 0.0)
+    tr_h = 3.0 - c
+    assert used == pytest.approx(1e-12 * tr_h / 4 * 1e4, rel=1e-14)
+    assert np.allclose(L @ L.T, h + used * np.eye(4), rtol=1e-14, atol=1e-18)
+    for m in range(4):   # every earlier rung leaves a negative pivot
+        assert -c + 1e-12 * tr_h / 4 * 10.0 ** m < 0
+    # an explicit damping that already suffices is used unchanged
+    L, used = ob.cholesky_damped(np.diag([1.0, 1.0, 0.0]), 0.5)
+    assert used == 0.5 and np.allclose(np.diag(L), np.sqrt([1.5, 1.5, 0.5]))
+    # exact zero pivot: the first rung (m = 0) already factors
+    L, used = ob.cholesky_damped(np.diag([2.0, 0.0, 2.0, 0.0]), 0.0)
+    assert used == pytest.approx(1e-12 * 4.0 / 4, rel=1e-14)
+    with pytest.raises(ob.NumericError):
+        ob.cholesky_damped(np.diag([1.0, 1.0, 1.0, -1.0]), 0.0)
+    with pytest.raises(ob.NumericError):
+        ob.cholesky_damped(np.zeros((3, 3)), 0.0)
+
+
+def test_scaled_step_with_zero_subchain_fails_and_damped_one_does_not():
+    """Degenerate case of the scaled variant: with every core but G_n zero,
+    Z = 0, so h = 0 and no rung of the ladder can factor it (the step raises);
+    with a damping eta > 0, h = eta I and the direction -g / eta is zero
+    because g = 0 too."""
+    cores = random_cores(DIMS, RANKS, seed=45)
+    X = np.random.default_rng(46).standard_normal(DIMS)
+    n = 0
+    zc = [G if k == n else np.zeros_like(G) for k, G in enumerate(cores)]
+    with pytest.raises(ob.NumericError):
+        ob.step(ob.State.new(zc), X, ob.Config(J=5, variant=ob.VARIANT_SCALED, seed=1), 0, force_mode=n)
+    rec = ob.step(ob.State.new(zc), X, ob.Config(J=5, variant=ob.VARIANT_SCALED, damping=0.25, seed=1), 0,
+                  force_mode=n)
+    assert np.array_equal(rec["h"], 0.25 * np.eye(rec["h"].shape[0]))
+    assert not np.any(rec["p"])
