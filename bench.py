@@ -128,9 +128,9 @@ def device_problem(w, device, seed_offset=0):
     return X, Xtrue, init
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per step, from the ncu capture
-# summarised in profiles/step_cluster_kernel_c2_fp32.md (101.38 MB over 200
-# steps); a kernel changed since its capture has no entry (traffic null)
+# dram__bytes_read.sum + dram__bytes_write.sum per step of the c2 step kernel,
+# from one ncu capture of 200 steps (101.38 MB); a kernel changed since its
+# capture has no entry (traffic null)
 MEASURED_TRAFFIC_PER_STEP = {("c2", "step_cluster_kernel<float,float,12,3,false>"): 506913}
 
 

@@ -196,22 +196,26 @@ trsgd_status trsgd_rel_error(trsgd_handle *h, int32_t problem,
  * allocator (a framework's caching pool or a fixed per-process budget), or a
  * latency-sensitive caller that cannot accept the implicit device
  * synchronisation an allocation or free may cause.  It needs no handle.
- *   Same result as trsgd_rel_error: RSE = ||TR(G) - X_ref||_F / ||X_ref||_F
- *   (Sec. 4), reduced in FP64 in a fixed order.  N, I, R, dtype (F64 or F32,
+ *   Same result as trsgd_rel_error: RSE = ||TR(G) - X_ref||_F / ||X_ref||_F,
+ *   reduced in FP64 in a fixed order.  N, I, R, dtype (F64 or F32,
  *   for the cores and X_ref) and cores_dev as in trsgd_reconstruct; Xref_dev
  *   a tensor of dims I (i_1 fastest); out_dev receives one double on the
  *   device.  Enqueued on `stream`, no synchronisation.
  * Scratch: one pair of FP64 partial sums per tile of 64 columns of X_[1],
  *   held in a fixed array inside the library (1 MiB on every GPU that loads
  *   the library, kept until the process exits).  Sizes beyond it, i.e.
- *   prod_{k>1} I_k > 4,194,304, return TRSGD_EINVAL; ranks above 16 return
- *   TRSGD_EUNSUPPORTED.  Every call overwrites the entries it uses, so nothing
+ *   prod_{k>1} I_k > 4,194,304, return TRSGD_EINVAL; ranks above 16, or
+ *   R_1 R_2 too large for the tiles' shared memory, return
+ *   TRSGD_EUNSUPPORTED; a failed launch returns TRSGD_ECUDA.  Every call
+ *   overwrites the entries it uses, so nothing
  *   needs clearing, but all calls share the array: calls that can overlap on
  *   the GPU (different streams without ordering between them) race and must
  *   be serialised by the caller.
  * The first call on each device looks up the array's device address with that
- * device current (cudaGetSymbolAddress); make that first call before any
- * stream capture.  No cudaMalloc, cudaFree or allocating library routine is
+ * device current (cudaGetSymbolAddress) and keeps it for the life of the
+ * process; make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) invalidates the kept address: do not call this entry
+ * point after one.  No cudaMalloc, cudaFree or allocating library routine is
  * called. */
 trsgd_status trsgd_rel_error_static(int32_t N, const int64_t *I, const int64_t *R, int32_t dtype,
                                     const void *const *cores_dev, const void *Xref_dev,

@@ -19,7 +19,7 @@ subchain and data of Algorithm 2 (SSDTP):
   7. G_{n(2)} += alpha p (Eq. update_brsgd) or the AdaGrad step of the Remark
      after Algorithm 3.
 
-Readings of points the paper leaves open (each is listed in the design notes):
+Readings of points the paper leaves open:
   * Eq. S_gradient is implemented literally; its expectation is the full
     gradient divided by J_n (the factor J_n in f_i of Sec. 3.1 is not
     carried into the estimator).

@@ -58,6 +58,8 @@ struct trsgd_handle {
   int threads = 512;
   int *d_status = nullptr;
   double *d_sums = nullptr;
+  double *d_rse_part = nullptr;   // per-CTA sums of the relative error, problem with the most tiles
+  long long rse_part_n = 0;
   long long *d_t = nullptr;   // device-resident iteration counter (trsgd_step_counter)
   std::vector<const void *> X;
   int64_t t_next = 0;
@@ -656,10 +658,15 @@ trsgd_status trsgd_rel_error(trsgd_handle *h, int32_t problem, const void *Xref_
   const ProbDesc &D = h->hdesc[problem];
   if (c.x_dtype != TRSGD_DTYPE_F64 && c.x_dtype != TRSGD_DTYPE_F32) return TRSGD_EUNSUPPORTED;
   const void *ref = Xref_dev ? Xref_dev : h->X[problem];
-  cudaError_t e = cudaMemsetAsync(h->d_sums, 0, 16, h->stream);
-  if (e != cudaSuccess) return from_cuda(e);
+  const long long np = reconstruct_partials(h->core_dtype, c.N, D.I, D.R);
+  cudaError_t e = cudaSuccess;
+  if (np > h->rse_part_n) {   // grown once to the largest problem evaluated
+    if ((e = h->buf.alloc((void **)&h->d_rse_part, (size_t)np * sizeof(double))) != cudaSuccess)
+      return from_cuda(e);
+    h->rse_part_n = np;
+  }
   e = launch_reconstruct(h->core_dtype, c.N, D.I, D.R, (const void *const *)D.cores, nullptr, ref, h->d_sums,
-                         h->stream);
+                         h->d_rse_part, h->stream);
   if (e != cudaSuccess) return from_cuda(e);
   double sums[2];
   e = cudaMemcpyAsync(sums, h->d_sums, 16, cudaMemcpyDeviceToHost, h->stream);
@@ -727,7 +734,7 @@ trsgd_status trsgd_reconstruct(int32_t N, const int64_t *I, const int64_t *R, in
     Ri[k] = (int)R[k];
   }
   return from_cuda(launch_reconstruct(dtype == TRSGD_DTYPE_F64 ? 0 : 1, N, Ii, Ri, cores_dev, X_dev, nullptr,
-                                      nullptr, static_cast<cudaStream_t>(stream)));
+                                      nullptr, nullptr, static_cast<cudaStream_t>(stream)));
 }
 
 trsgd_status trsgd_sampled_loss_grad(int32_t N, const int64_t *I, const int64_t *R, int32_t n, int64_t J,

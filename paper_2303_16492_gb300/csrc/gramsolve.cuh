@@ -79,6 +79,10 @@ __device__ __noinline__ bool gram_factor_reg(const V *A, int Q, int lda, double 
   pinv = smem_ptr(pinv);
   const int tid = threadIdx.x, NT = blockDim.x;
   const int Qb = (Q + 3) >> 2, nblk = Qb * (Qb + 1) / 2;
+  // a launch shape with too few threads for the block triangle would leave
+  // diagonal blocks without an owner: fail (uniformly) instead of factoring
+  // with stale pivots
+  if (nblk > NBS * NT) return false;
   V one, ex;
   gs_one(one);
   gs_from_double(extra, ex);

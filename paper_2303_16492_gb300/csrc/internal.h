@@ -157,9 +157,12 @@ cudaError_t launch_euclid_table(int core_dtype, const void *G, int I, int Q, dou
                                 double *prob, unsigned long long *cdf, cudaStream_t s);
 cudaError_t launch_leverage_table(int core_dtype, const void *G, int I, int Q, double *prob,
                                   unsigned long long *cdf, int *status, cudaStream_t s);
+// sums (nullable) receives sum (x - x_ref)^2 and sum x_ref^2, reduced in a
+// fixed order through `partials` (reconstruct_partials(...) doubles).
 cudaError_t launch_reconstruct(int dtype, int N, const int *I, const int *R,
                                const void *const *cores, void *X, const void *Xref,
-                               double *sums, cudaStream_t s);
+                               double *sums, double *partials, cudaStream_t s);
+long long reconstruct_partials(int dtype, int N, const int *I, const int *R);
 cudaError_t launch_sampled_loss_grad(int N, const int *I, const int *R, int n, int J,
                                      const int *idx, const float *XS, const float *w,
                                      const float *const *cores, float *const *grads,

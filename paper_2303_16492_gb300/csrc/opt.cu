@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(256) opt_weights_kernel(OptArgs p) {
   T *gt = zt + (size_t)Q * kOptCols;                   // [Q][TI]
   double *colsq = reinterpret_cast<double *>(gt + (size_t)Q * p.TI);   // [kOptCols]
   double *znrm = colsq + kOptCols;                     // [kOptCols]
+  double *dsq = znrm + kOptCols;                       // [kOptCols][TI] squared residuals of a row chunk
   const T *cores_c[kMaxOrder];
   int R[kMaxOrder], order[kMaxOrder];
 #pragma unroll
@@ -93,8 +94,15 @@ __global__ void __launch_bounds__(256) opt_weights_kernel(OptArgs p) {
     gemm_tn<4, 2, T>(jb, ti, Q, zt, kOptCols, gt, p.TI, nullptr, [&](int jl, int ii, T v) {
       const double x = (double)to_compute(X[(cbase + jl) * p.ldx + i0 + ii]);
       const double d = (double)v - x;
-      atomicAdd(colsq + jl, d * d);
+      dsq[(size_t)jl * p.TI + ii] = d * d;
     });
+    __syncthreads();
+    // column sums in increasing row order, one thread per column (deterministic)
+    for (int jl = threadIdx.x; jl < jb; jl += blockDim.x) {
+      double s = colsq[jl];
+      for (int ii = 0; ii < ti; ++ii) s += dsq[(size_t)jl * p.TI + ii];
+      colsq[jl] = s;
+    }
   }
   __syncthreads();
   for (int jl = threadIdx.x; jl < jb; jl += blockDim.x) p.a[cbase + jl] = sqrt(colsq[jl]) * sqrt(znrm[jl]);
@@ -203,10 +211,13 @@ template <typename T, typename XT, int RMAX>
 static cudaError_t opt_weights_t(OptArgs p, cudaStream_t s) {
   const int Q = p.R[p.n] * p.R[(p.n + 1) % p.N];
   p.TI = 64;
-  size_t smem = (size_t)Q * (kOptCols + p.TI) * sizeof(T) + 2 * kOptCols * sizeof(double);
+  auto bytes = [&](int ti) {
+    return (size_t)Q * (kOptCols + ti) * sizeof(T) + (2 + (size_t)ti) * kOptCols * sizeof(double);
+  };
+  size_t smem = bytes(p.TI);
   while (smem > 200 * 1024 && p.TI > 8) {
     p.TI /= 2;
-    smem = (size_t)Q * (kOptCols + p.TI) * sizeof(T) + 2 * kOptCols * sizeof(double);
+    smem = bytes(p.TI);
   }
   if (smem > 200 * 1024) return cudaErrorInvalidValue;
   auto k = opt_weights_kernel<T, XT, RMAX>;

@@ -163,7 +163,8 @@ struct ReconArgs {
   const void *cores[kMaxOrder];
   void *X;
   const void *Xref;
-  double *sums;
+  double *sums;       // [2]: sum (x - x_ref)^2, sum x_ref^2 (or null)
+  double *partials;   // [2 * blocks]: the same two sums per CTA, reduced in a fixed order
   long long J1;
   int JT, TI;
 };
@@ -242,31 +243,68 @@ __global__ void __launch_bounds__(256) reconstruct_kernel(ReconArgs a) {
     if (threadIdx.x == 0) {
       double A = 0.0, B = 0.0;
       for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { A += red[0][k]; B += red[1][k]; }
-      atomicAdd(a.sums, A);
-      atomicAdd(a.sums + 1, B);
+      a.partials[2 * blockIdx.x] = A;
+      a.partials[2 * blockIdx.x + 1] = B;
     }
   }
+}
+
+// Fixed-order sum of the per-CTA pairs: thread t adds CTAs t, t + 256, ... in
+// increasing order, then thread 0 adds the 256 thread sums in order (the
+// result does not depend on the schedule of the CTAs).
+__global__ void __launch_bounds__(256) reconstruct_sums_kernel(const double *partials, long long nblocks,
+                                                              double *sums) {
+  __shared__ double sd[256], sr[256];
+  double A = 0.0, B = 0.0;
+  for (long long b = threadIdx.x; b < nblocks; b += blockDim.x) {
+    A += partials[2 * b];
+    B += partials[2 * b + 1];
+  }
+  sd[threadIdx.x] = A;
+  sr[threadIdx.x] = B;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double x = 0.0, y = 0.0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      x += sd[t];
+      y += sr[t];
+    }
+    sums[0] = x;
+    sums[1] = y;
+  }
+}
+
+// Column tile JT (= TI) of the reconstruction: 64, halved while the two
+// shared-memory tiles exceed 200 KB.
+static int recon_tile(int Q, size_t esize) {
+  int jt = 64;
+  while ((size_t)Q * 2 * jt * esize > 200 * 1024 && jt > 8) jt /= 2;
+  return jt;
 }
 
 template <typename T, int RMAX>
 static cudaError_t recon_t(ReconArgs a, cudaStream_t s) {
   const int Q = a.R[0] * a.R[1];
-  size_t smem = (size_t)Q * (a.JT + a.TI) * sizeof(T);
-  while (smem > 200 * 1024 && a.JT > 8) {
-    a.JT /= 2;
-    a.TI = a.JT;
-    smem = (size_t)Q * (a.JT + a.TI) * sizeof(T);
-  }
+  a.JT = a.TI = recon_tile(Q, sizeof(T));
+  const size_t smem = (size_t)Q * (a.JT + a.TI) * sizeof(T);
   auto k = reconstruct_kernel<T, RMAX>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long long blocks = (a.J1 + a.JT - 1) / a.JT;
   k<<<(unsigned)blocks, 256, smem, s>>>(a);
+  if (a.sums) reconstruct_sums_kernel<<<1, 256, 0, s>>>(a.partials, blocks, a.sums);
   return cudaGetLastError();
 }
 
+long long reconstruct_partials(int dtype, int N, const int *I, const int *R) {
+  long long J1 = 1;
+  for (int k = 1; k < N; ++k) J1 *= I[k];
+  const int jt = recon_tile(R[0] * R[1], dtype == 0 ? 8 : 4);
+  return 2 * ((J1 + jt - 1) / jt);
+}
+
 cudaError_t launch_reconstruct(int dtype, int N, const int *I, const int *R, const void *const *cores,
-                               void *X, const void *Xref, double *sums, cudaStream_t s) {
+                               void *X, const void *Xref, double *sums, double *partials, cudaStream_t s) {
   ReconArgs a = {};
   a.N = N;
   int rmax = 1;
@@ -281,6 +319,8 @@ cudaError_t launch_reconstruct(int dtype, int N, const int *I, const int *R, con
   a.X = X;
   a.Xref = Xref;
   a.sums = sums;
+  a.partials = partials;
+  if (sums && !partials) return cudaErrorInvalidValue;
   a.J1 = J1;
   a.JT = 64;
   a.TI = 64;

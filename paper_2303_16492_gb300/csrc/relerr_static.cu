@@ -134,8 +134,11 @@ __global__ void __launch_bounds__(256) relerr_finish_kernel(const double *partia
   }
 }
 
+// *too_big is set (and nothing launched) when the tiles of G_{1(2)} and of the
+// subchain rows do not fit in shared memory; other failures are CUDA errors.
 template <typename T, int RMAX>
-static cudaError_t relerr_static_t(StaticArgs a, double *scratch, int ntiles, double *out, cudaStream_t s) {
+static cudaError_t relerr_static_t(StaticArgs a, double *scratch, int ntiles, double *out, cudaStream_t s,
+                                   bool *too_big) {
   const int Q = a.R[0] * a.R[1];
   a.TI = kTileCols;
   size_t smem = (size_t)Q * (kTileCols + a.TI) * sizeof(T);
@@ -143,7 +146,8 @@ static cudaError_t relerr_static_t(StaticArgs a, double *scratch, int ntiles, do
     a.TI /= 2;
     smem = (size_t)Q * (kTileCols + a.TI) * sizeof(T);
   }
-  if (smem > 200 * 1024) return cudaErrorInvalidValue;
+  *too_big = smem > 200 * 1024;
+  if (*too_big) return cudaSuccess;
   auto k = relerr_tiles_kernel<T, RMAX>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -153,7 +157,8 @@ static cudaError_t relerr_static_t(StaticArgs a, double *scratch, int ntiles, do
 }
 
 // Device address of the scratch array, looked up once per device (with that
-// device current) and reused.
+// device current) and reused for the life of the process: a device reset
+// (cudaDeviceReset) unloads the module, and the cached address is then stale.
 static double *scratch_for_current_device(cudaError_t *err) {
   static std::mutex mu;
   static double *addr[kMaxDevices] = {};
@@ -193,25 +198,31 @@ extern "C" trsgd_status trsgd_rel_error_static(int32_t N, const int64_t *I, cons
     a.R[k] = (int)R[k];
     a.cores[k] = cores_dev[k];
     rmax = R[k] > rmax ? (int)R[k] : rmax;
-    if (k > 0) J1 *= I[k];
+    // beyond the fixed scratch: prod_{k>1} I_k > 4,194,304 (checked before each
+    // product, so the running product stays far inside 64 bits)
+    if (k > 0) {
+      if (J1 > (long long)kMaxTiles * kTileCols / I[k]) return TRSGD_EINVAL;
+      J1 *= I[k];
+    }
   }
   const long long ntiles = (J1 + kTileCols - 1) / kTileCols;
-  if (ntiles > kMaxTiles) return TRSGD_EINVAL;   // beyond the fixed scratch: prod_{k>1} I_k > 4,194,304
+  if (ntiles > kMaxTiles) return TRSGD_EINVAL;
   a.Xref = Xref_dev;
   a.J1 = J1;
   cudaError_t e = cudaSuccess;
   double *scratch = scratch_for_current_device(&e);
   if (!scratch) return TRSGD_ECUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  bool too_big = false;
   if (dtype == TRSGD_DTYPE_F64) {
-    if (rmax <= 4) e = relerr_static_t<double, 4>(a, scratch, (int)ntiles, out_dev, s);
-    else if (rmax <= 8) e = relerr_static_t<double, 8>(a, scratch, (int)ntiles, out_dev, s);
-    else e = relerr_static_t<double, 16>(a, scratch, (int)ntiles, out_dev, s);
+    if (rmax <= 4) e = relerr_static_t<double, 4>(a, scratch, (int)ntiles, out_dev, s, &too_big);
+    else if (rmax <= 8) e = relerr_static_t<double, 8>(a, scratch, (int)ntiles, out_dev, s, &too_big);
+    else e = relerr_static_t<double, 16>(a, scratch, (int)ntiles, out_dev, s, &too_big);
   } else {
-    if (rmax <= 4) e = relerr_static_t<float, 4>(a, scratch, (int)ntiles, out_dev, s);
-    else if (rmax <= 8) e = relerr_static_t<float, 8>(a, scratch, (int)ntiles, out_dev, s);
-    else e = relerr_static_t<float, 16>(a, scratch, (int)ntiles, out_dev, s);
+    if (rmax <= 4) e = relerr_static_t<float, 4>(a, scratch, (int)ntiles, out_dev, s, &too_big);
+    else if (rmax <= 8) e = relerr_static_t<float, 8>(a, scratch, (int)ntiles, out_dev, s, &too_big);
+    else e = relerr_static_t<float, 16>(a, scratch, (int)ntiles, out_dev, s, &too_big);
   }
-  if (e == cudaErrorInvalidValue) return TRSGD_EUNSUPPORTED;
+  if (too_big) return TRSGD_EUNSUPPORTED;
   return e == cudaSuccess ? TRSGD_OK : TRSGD_ECUDA;
 }
