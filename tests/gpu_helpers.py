@@ -21,9 +21,59 @@ def api():
 
 
 def rel(a, b):
+    """Frobenius relative difference (reported in messages; every parity
+    assertion is element by element, see assert_close)."""
     a = np.asarray(a, dtype=np.float64)
     b = np.asarray(b, dtype=np.float64)
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def rms(x):
+    x = np.asarray(x, dtype=np.float64)
+    return float(np.sqrt(np.mean(x * x))) if x.size else 0.0
+
+
+# Element-wise parity bound: |got - want| <= rtol * (|want| + K_RMS * rms(want)) + atol,
+# element by element.  The rms term is the scale of the quantity: an element
+# whose exact value is near zero after cancellation still carries rounding of
+# the size of the typical element (sums of products of that size), so its
+# error is bounded relative to the rms, not to itself.  K_RMS = 8 covers the
+# largest of ~1e6 independent roundings of one rms-relative size (about 5
+# standard deviations) with margin; one element off by a whole rms (a wrong
+# row, a dropped term) exceeds it by four orders of magnitude at rtol = 2e-5.
+K_RMS = 8.0
+
+
+def assert_close(got, want, rtol, what="", atol=0.0, k=K_RMS):
+    got = np.asarray(got, dtype=np.float64)
+    want = np.asarray(want, dtype=np.float64)
+    assert got.shape == want.shape, f"{what}: shape {got.shape} != {want.shape}"
+    bound = rtol * (np.abs(want) + k * rms(want)) + atol
+    err = np.abs(got - want)
+    bad = ~(err <= bound)
+    if bad.any():
+        i = np.unravel_index(int(np.argmax(np.where(bad, err / np.maximum(bound, 1e-300), -1.0))), err.shape)
+        raise AssertionError(
+            f"{what}: {int(bad.sum())} of {bad.size} elements outside rtol={rtol:g} (x{k:g} rms); "
+            f"worst at {tuple(int(v) for v in i)}: got {got[i]!r}, want {want[i]!r}, bound {bound[i]:.3e}; "
+            f"Frobenius rel {rel(got, want):.3e}")
+
+
+def store_eps(dtype_np):
+    """Unit roundoff of the stored core dtype (its rounding of G + step)."""
+    return 2.0 ** -53 if np.dtype(dtype_np) == np.float64 else 2.0 ** -24
+
+
+def assert_update_close(dev_after, dev_before, ora_after, ora_before, rtol, eps, what="core"):
+    """Cores compared through the step they took: (G_after - G_before) on the
+    device against (O_after - O_before) of the oracle, element by element,
+    plus the rounding of the stored core (2 eps |O_after|).  A wrong update
+    smaller than the core itself cannot hide behind the core's size.  The
+    cores themselves are compared too."""
+    for k, (G, S, O, T) in enumerate(zip(dev_after, dev_before, ora_after, ora_before)):
+        G, S, O, T = (np.asarray(v, dtype=np.float64) for v in (G, S, O, T))
+        assert_close(G - S, O - T, rtol, f"{what} {k} update", atol=2.0 * eps * np.abs(O))
+        assert_close(G, O, rtol, f"{what} {k}")
 
 
 class Case:
@@ -68,6 +118,31 @@ class Case:
         N = len(self.dims)
         return [tr.fold2(c.double().cpu().numpy(), self.ranks[n], self.ranks[(n + 1) % N])
                 for n, c in enumerate(self.cores_d)]
+
+    def resync(self):
+        """Oracle state := device cores (so both take the next step from the
+        same iterate); remembered as the starting point of that step."""
+        cores = self.device_cores()
+        for k, G in enumerate(cores):
+            self.state.cores[k] = G
+        self.before = ([G.copy() for G in cores], [G.copy() for G in cores])
+        return cores
+
+    def snapshot(self):
+        """Remember both sides' cores before a step taken without resync."""
+        self.before = (self.device_cores(), [G.copy() for G in self.state.cores])
+
+    def assert_cores(self, rtol):
+        """Cores after a step: the update element by element against the
+        oracle's (from the remembered starting points), and the cores."""
+        dev = self.device_cores()
+        before = getattr(self, "before", None)
+        if before is None:
+            for k, (G, O) in enumerate(zip(dev, self.state.cores)):
+                assert_close(G, O, rtol, f"core {k}")
+            return
+        assert_update_close(dev, before[0], self.state.cores, before[1], rtol, store_eps(self.dtype_np))
+        self.before = None
 
     def debug(self, rec_n):
         A = self.A

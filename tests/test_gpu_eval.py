@@ -7,7 +7,7 @@ import torch
 from oracle import brsgd as ob
 from oracle import tr
 from tests._util import random_cores, to_lib_cores
-from tests.gpu_helpers import Case, api, cuda, rel
+from tests.gpu_helpers import Case, api, cuda, assert_close
 
 pytestmark = [pytest.mark.gpu, cuda]
 
@@ -22,7 +22,7 @@ def test_reconstruct_matches_element_formula(dims, ranks, prec):
     dt = torch.float64 if prec == 0 else torch.float32
     cd = [torch.from_numpy(G).to("cuda", dt) for G in to_lib_cores(cores)]
     got = A.reconstruct(cd, dims, ranks).double().cpu().numpy().reshape(dims, order="F")
-    assert rel(got, want) < (1e-13 if prec == 0 else 2e-6)
+    assert_close(got, want, (1e-13 if prec == 0 else 2e-6), "got")
 
 
 def test_rel_error_matches_oracle():
@@ -55,7 +55,7 @@ def test_adjoint_all_cores_matches_oracle(dims, ranks, n):
     lg, gg = A.sampled_loss_grad(cd, dims, ranks, n, idx_d, XS_d, w_d)
     assert abs(float(lg.item()) - loss) < 1e-5 * abs(loss)
     for k in range(len(dims)):
-        assert rel(gg[k].double().cpu().numpy(), tr.unfold2(grads[k])) < 3e-5
+        assert_close(gg[k].double().cpu().numpy(), tr.unfold2(grads[k]), 3e-5, "gg[k]")
 
 
 def test_autograd_function_backward():
@@ -75,7 +75,7 @@ def test_autograd_function_backward():
     L = A.TRLoss.apply(idx_d, XS_d, w_d, dims, ranks, n, *cd)
     (2.0 * L).backward()
     for k in range(3):
-        assert rel(cd[k].grad.double().cpu().numpy(), 2.0 * tr.unfold2(grads[k])) < 3e-5
+        assert_close(cd[k].grad.double().cpu().numpy(), 2.0 * tr.unfold2(grads[k]), 3e-5, "cd[k]")
 
 
 def test_batched_problems_match_independent_oracle_runs():
@@ -103,4 +103,4 @@ def test_batched_problems_match_independent_oracle_runs():
         st, X = states[p]
         ob.run(st, X, cfgs[p], 40)
         for k in range(3):
-            assert rel(cores_d[p][k].cpu().numpy(), tr.unfold2(st.cores[k])) < 1e-11
+            assert_close(cores_d[p][k].cpu().numpy(), tr.unfold2(st.cores[k]), 1e-11, "cores_d[p][k]")

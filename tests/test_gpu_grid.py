@@ -18,7 +18,7 @@ import pytest
 import torch
 
 from oracle import brsgd as ob
-from tests.gpu_helpers import Case, api, cuda, rel
+from tests.gpu_helpers import Case, api, cuda, assert_close
 
 pytestmark = [pytest.mark.gpu, cuda]
 
@@ -57,13 +57,12 @@ def _check(case, rec, bf16):
     assert d["n"] == rec["n"]
     np.testing.assert_array_equal(d["idx"], rec["idx"])
     np.testing.assert_array_equal(d["pF"], rec["pF"])
-    assert rel(d["Z"], rec["Z"]) < 2e-5
+    assert_close(d["Z"], rec["Z"], 2e-5, "Z")
     tol_e, tol_g, tol_c = (1e-2, 2e-2, 1e-3) if bf16 else (2e-5, 2e-5, 2e-5)
-    assert rel(d["E"], rec["E"]) < tol_e
-    assert rel(d["g"], rec["g"]) < tol_g
-    assert rel(d["p"], rec["p"]) < tol_g
-    for G, O in zip(case.device_cores(), case.state.cores):
-        assert rel(G, O) < tol_c
+    assert_close(d["E"], rec["E"], tol_e, "E")
+    assert_close(d["g"], rec["g"], tol_g, "g")
+    assert_close(d["p"], rec["p"], tol_g, "p")
+    case.assert_cores(tol_c)
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s["dims"])) + f"_R{s['ranks'][0]}")
@@ -72,8 +71,7 @@ def test_grid_single_steps(shape, bf16):
     case = _grid_case(shape, bf16)
     assert case.solver.launch_shape() == (0, 256)
     for t in range(4):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _check(case, rec, bf16)
@@ -83,8 +81,7 @@ def test_grid_adagrad_steps():
     """AdaGrad on the grid path: accumulators and steps against the oracle."""
     case = _grid_case(SHAPES[0], False, rule=ob.RULE_ADAGRAD, eta=0.05)
     for t in range(4):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         acc = [np.empty((case.dims[k], case.Q(k)), dtype=np.float32) for k in range(3)]
         for k in range(3):
             case.solver.adagrad_state(0, k, acc[k])
@@ -107,7 +104,6 @@ def test_grid_is_chosen_for_large_ranks_and_follows_the_oracle():
     for t in range(30):
         ob.step(case.state, case.X, case.ocfg, t)
     case.solver.run(0, 30)
-    for G, O in zip(case.device_cores(), case.state.cores):
-        assert rel(G, O) < 1e-4
+    case.assert_cores(1e-4)
     assert abs(case.solver.rel_error(0, case.Xtd) - float(
         np.linalg.norm(ob.tr.reconstruct(case.state.cores) - case.X_true) / np.linalg.norm(case.X_true))) < 1e-4

@@ -16,7 +16,7 @@ import torch
 
 from oracle import brsgd as ob
 from oracle import tr
-from tests.gpu_helpers import Case, api, cuda, rel
+from tests.gpu_helpers import Case, api, assert_close, cuda
 
 pytestmark = [pytest.mark.gpu, cuda]
 
@@ -26,15 +26,14 @@ def _compare_step(case, rec, tol, check_p=True):
     assert d["n"] == rec["n"]
     np.testing.assert_array_equal(d["idx"], rec["idx"])
     np.testing.assert_array_equal(d["pF"], rec["pF"])
-    assert rel(d["Z"], rec["Z"]) < tol
-    assert rel(d["E"], rec["E"]) < tol
-    assert rel(d["g"], rec["g"]) < tol
+    assert_close(d["Z"], rec["Z"], tol, "Z")
+    assert_close(d["E"], rec["E"], tol, "E")
+    assert_close(d["g"], rec["g"], tol, "g")
     if check_p:
-        assert rel(d["p"], rec["p"]) < tol
+        assert_close(d["p"], rec["p"], tol, "p")
     if "h" in d and rec["h"] is not None:
-        assert rel(d["h"], rec["h"]) < tol
-    for G, O in zip(case.device_cores(), case.state.cores):
-        assert rel(G, O) < tol
+        assert_close(d["h"], rec["h"], tol, "h")
+    case.assert_cores(tol)
 
 
 SHAPES_FP32 = [
@@ -62,8 +61,7 @@ def test_fp32_single_steps(shape, cluster, units):
     case.solver.set_debug(True)
     for t in range(4):
         # restart both sides from identical cores so each step is a single-step comparison
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, 2e-5)
@@ -80,8 +78,7 @@ def test_fp32_uniform_rank_chain(rank, cluster):
     case.solver.launch_shape(cluster=cluster, threads=512)
     case.solver.set_debug(True)
     for t in range(4):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, 2e-5)
@@ -96,8 +93,7 @@ def test_fp32_slices_staged_in_groups(cluster):
     case.solver.launch_shape(cluster=cluster, threads=512)
     case.solver.set_debug(True)
     for t in range(4):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, 2e-5)
@@ -110,8 +106,7 @@ def test_fp32_chunked_rows_ragged_tail():
     case.solver.launch_shape(cluster=16, threads=512)
     case.solver.set_debug(True)
     for t in range(3):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, 3e-5)
@@ -123,6 +118,7 @@ def test_fp64_single_steps(cluster):
     case.solver.launch_shape(cluster=cluster, threads=512)
     case.solver.set_debug(True)
     for t in range(6):
+        case.snapshot()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, 1e-12)
@@ -156,7 +152,7 @@ def test_fp64_trajectory_2000_steps():
     rse_gpu = s.rel_error(0, Xtd)
     for n, G in enumerate(cores):
         O = tr.unfold2(st.cores[n])
-        assert rel(G.cpu().numpy(), O) < 1e-10
+        assert_close(G.cpu().numpy(), O, 1e-10, "G")
     assert abs(rse_gpu - rse_oracle) <= 1e-10 * rse_oracle
 
 
@@ -170,8 +166,7 @@ def test_euclidean_distribution_steps(prec):
     for t in range(6):
         # restart the oracle from the device cores: its tables are then built from
         # the same values as the kernel's in-kernel table update, so p_F is bit-exact
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, tol)
@@ -187,8 +182,9 @@ def test_scaled_variant_steps(prec, damping):
     tol = 1e-11 if prec == 0 else 1e-4
     for t in range(5):
         if prec == 1:
-            for k, G in enumerate(case.device_cores()):
-                case.state.cores[k] = G
+            case.resync()
+        else:
+            case.snapshot()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, tol)
@@ -207,8 +203,9 @@ def test_scaled_variant_ragged_diagonal_blocks(prec, ranks):
     tol = 1e-11 if prec == 0 else 1e-4
     for t in range(6):
         if prec == 1:
-            for k, G in enumerate(case.device_cores()):
-                case.state.cores[k] = G
+            case.resync()
+        else:
+            case.snapshot()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, tol)
@@ -230,8 +227,7 @@ def test_scaled_variant_row_chunks(units, J_H):
     assert case.solver.tensor_pieces() == (3 if units == "pieces" else 0)
     case.solver.set_debug(True)
     for t in range(6):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, 1e-4)
@@ -247,18 +243,16 @@ def test_scaled_variant_leverage(prec, J_H):
     case.solver.set_debug(True)
     tol = 1e-10 if prec == 0 else 1e-4
     for t in range(8):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         d = case.debug(rec["n"])
         np.testing.assert_array_equal(d["idx"], rec["idx"])
         np.testing.assert_allclose(d["pF"], rec["pF"], rtol=1e-12 if prec == 0 else 1e-5)
-        assert rel(d["g"], rec["g"]) < tol
-        assert rel(d["h"], rec["h"]) < tol
-        assert rel(d["p"], rec["p"]) < tol
-        for G, O in zip(case.device_cores(), case.state.cores):
-            assert rel(G, O) < tol
+        assert_close(d["g"], rec["g"], tol, "g")
+        assert_close(d["h"], rec["h"], tol, "h")
+        assert_close(d["p"], rec["p"], tol, "p")
+        case.assert_cores(tol)
 
 
 def test_leverage_table_of_rank_deficient_core():
@@ -315,7 +309,7 @@ def test_full_gradient_iterations(shape, scaled, prec):
         case.solver.gd_step(scaled=scaled, alpha=alpha, damping=damping)
         torch.cuda.synchronize()
         for G, O, S in zip(case.device_cores(), want, start):
-            assert rel(G - S, O - S) < tol
+            assert_close(G - S, O - S, tol, "core update")
 
 
 def test_full_gradient_rejects_unsupported():
@@ -334,6 +328,7 @@ def test_adagrad_steps_and_state():
     case = Case(dims=[12, 10, 11], ranks=[2, 3, 2], J=40, prec=0, rule=ob.RULE_ADAGRAD, eta=0.02)
     case.solver.set_debug(True)
     for t in range(8):
+        case.snapshot()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, 1e-12)
@@ -348,8 +343,7 @@ def test_scaled_adagrad_fp32():
                 rule=ob.RULE_ADAGRAD, eta=0.05, damping=1e-3)
     case.solver.set_debug(True)
     for t in range(4):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         acc = [np.empty((case.dims[k], case.Q(k)), dtype=np.float32) for k in range(3)]
         for k in range(3):
             case.solver.adagrad_state(0, k, acc[k])
@@ -406,17 +400,15 @@ def test_bf16_mixed_tensor_core_steps(shape, cluster):
     case.solver.launch_shape(cluster=cluster, threads=512)
     case.solver.set_debug(True)
     for t in range(4):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         d = case.debug(rec["n"])
         np.testing.assert_array_equal(d["idx"], rec["idx"])
-        assert rel(d["Z"], rec["Z"]) < 2e-5
-        assert rel(d["E"], rec["E"]) < 2e-4
-        assert rel(d["g"], rec["g"]) < 1e-2
-        for G, O in zip(case.device_cores(), case.state.cores):
-            assert rel(G, O) < 1e-4
+        assert_close(d["Z"], rec["Z"], 2e-5, "Z")
+        assert_close(d["E"], rec["E"], 2e-4, "E")
+        assert_close(d["g"], rec["g"], 1e-2, "g")
+        case.assert_cores(1e-4)
 
 
 @pytest.mark.parametrize("prec,dims,ranks", [
@@ -432,16 +424,14 @@ def test_leverage_distribution_steps(prec, dims, ranks):
     case.solver.set_debug(True)
     tol = 1e-12 if prec == 0 else 2e-5
     for t in range(6):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         d = case.debug(rec["n"])
         np.testing.assert_array_equal(d["idx"], rec["idx"])
-        assert rel(d["pF"], rec["pF"]) < 1e-12
-        assert rel(d["g"], rec["g"]) < tol
-        for G, O in zip(case.device_cores(), case.state.cores):
-            assert rel(G, O) < tol
+        assert_close(d["pF"], rec["pF"], 1e-12, "pF")
+        assert_close(d["g"], rec["g"], tol, "g")
+        case.assert_cores(tol)
 
 
 @pytest.mark.parametrize("prec,dist", [(0, ob.DIST_UNIFORM), (0, ob.DIST_EUCLIDEAN), (1, ob.DIST_UNIFORM)])
@@ -453,8 +443,7 @@ def test_scaled_independent_hessian_batch(prec, dist):
     case.solver.set_debug(True)
     tol = 1e-11 if prec == 0 else 1e-4
     for t in range(4):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         _compare_step(case, rec, tol)
@@ -477,16 +466,14 @@ def test_optimal_distribution_fp64_steps():
     case = Case(dims=[9, 8, 10], ranks=[2, 3, 2], J=40, prec=0, alpha=0.05, dist=ob.DIST_OPTIMAL, noise_rel=0.2)
     case.solver.set_debug(True)
     for t in range(5):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         rec = ob.step(case.state, case.X, case.ocfg, t)
         case.solver.step(t)
         d = case.debug(rec["n"])
         np.testing.assert_array_equal(d["idx"], rec["idx"])
-        assert rel(d["pF"], rec["pF"]) < 1e-12
-        assert rel(d["g"], rec["g"]) < 1e-11
-        for G, O in zip(case.device_cores(), case.state.cores):
-            assert rel(G, O) < 1e-11
+        assert_close(d["pF"], rec["pF"], 1e-12, "pF")
+        assert_close(d["g"], rec["g"], 1e-11, "g")
+        case.assert_cores(1e-11)
 
 
 def test_optimal_distribution_fp32_draws_valid():
@@ -498,8 +485,7 @@ def test_optimal_distribution_fp32_draws_valid():
     case = Case(dims=[12, 10, 11], ranks=[3, 3, 3], J=64, prec=1, alpha=0.05, dist=ob.DIST_OPTIMAL, noise_rel=0.2)
     case.solver.set_debug(True)
     for t in range(3):
-        for k, G in enumerate(case.device_cores()):
-            case.state.cores[k] = G
+        case.resync()
         n = ob.draw_mode(case.ocfg.seed, t, 3)
         q = ob.optimal_dist(case.state.cores, case.X, n)
         _, cdf = px.integer_weights(q)

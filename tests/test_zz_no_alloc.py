@@ -1,7 +1,8 @@
 """trsgd_rel_error_static: the relative error for callers that cannot
 allocate device memory (their memory belongs to another allocator, or they
 cannot accept the synchronisation an allocation may cause).  Checked through
-the C-ABI against the handle-based trsgd_rel_error on two calls in a row.
+the C-ABI against the handle-based trsgd_rel_error and against the oracle's
+RSE of the same cores, on two calls in a row.
 
 This file sorts last so that a run stopping at the first failure has already
 run every other test; it also passes alone in a fresh process."""
@@ -11,7 +12,8 @@ import numpy as np
 import pytest
 import torch
 
-from tests._util import make_problem, random_cores, to_lib_cores
+from oracle import tr
+from tests._util import make_problem, random_cores, to_lib_cores, to_oracle_cores
 from tests.gpu_helpers import api, cuda
 
 pytestmark = [pytest.mark.gpu, cuda]
@@ -49,6 +51,10 @@ def test_static_rel_error_matches_rel_error_twice(prec):
         torch.cuda.synchronize()
         got = float(out.item())
         assert abs(got - want) <= tol * want, (call, got, want)
+        # the oracle's RSE of the cores the device holds now (FP64, Sec. 4)
+        ora = tr.rse(to_oracle_cores([c.double().cpu().numpy() for c in cores], ranks), X.astype(
+            np.float64 if prec == 0 else np.float32).astype(np.float64))
+        assert abs(got - ora) <= tol * ora, (call, got, ora)
         s.step(call)          # move the cores so that the second call sees new values
         torch.cuda.synchronize()
     s.close()
@@ -64,6 +70,13 @@ def test_static_rel_error_rejects_oversize_and_bad_args():
     st = lib.trsgd_rel_error_static(3, I, R, 1, _ptrs(cores), ctypes.c_void_p(out.data_ptr()),
                                     ctypes.c_void_p(out.data_ptr()), None)
     assert st == A._abi.EINVAL
+    # four large dims: the running product of I_2..I_4 would pass 2^63; the
+    # bound is checked before each multiplication
+    cores4 = cores + [cores[0]]
+    I4 = (ctypes.c_int64 * 4)(2, 1 << 30, 1 << 30, 1 << 30)
+    R4 = (ctypes.c_int64 * 4)(1, 1, 1, 1)
+    assert lib.trsgd_rel_error_static(4, I4, R4, 1, _ptrs(cores4), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(out.data_ptr()), None) == A._abi.EINVAL
     I2 = (ctypes.c_int64 * 3)(2, 2, 2)
     assert lib.trsgd_rel_error_static(3, I2, R, 1, _ptrs(cores), None, ctypes.c_void_p(out.data_ptr()),
                                       None) == A._abi.EINVAL
