@@ -64,16 +64,18 @@ def store_eps(dtype_np):
     return 2.0 ** -53 if np.dtype(dtype_np) == np.float64 else 2.0 ** -24
 
 
-def assert_update_close(dev_after, dev_before, ora_after, ora_before, rtol, eps, what="core"):
+def assert_update_close(dev_after, dev_before, ora_after, ora_before, rtol, eps, what="core", rtol_core=None):
     """Cores compared through the step they took: (G_after - G_before) on the
     device against (O_after - O_before) of the oracle, element by element,
     plus the rounding of the stored core (2 eps |O_after|).  A wrong update
     smaller than the core itself cannot hide behind the core's size.  The
-    cores themselves are compared too."""
+    cores themselves are compared too (rtol_core, default rtol).  The update
+    is alpha p (or the AdaGrad step of p), so its tolerance is that of the
+    direction."""
     for k, (G, S, O, T) in enumerate(zip(dev_after, dev_before, ora_after, ora_before)):
         G, S, O, T = (np.asarray(v, dtype=np.float64) for v in (G, S, O, T))
         assert_close(G - S, O - T, rtol, f"{what} {k} update", atol=2.0 * eps * np.abs(O))
-        assert_close(G, O, rtol, f"{what} {k}")
+        assert_close(G, O, rtol if rtol_core is None else rtol_core, f"{what} {k}")
 
 
 class Case:
@@ -132,16 +134,18 @@ class Case:
         """Remember both sides' cores before a step taken without resync."""
         self.before = (self.device_cores(), [G.copy() for G in self.state.cores])
 
-    def assert_cores(self, rtol):
+    def assert_cores(self, rtol, rtol_update=None):
         """Cores after a step: the update element by element against the
-        oracle's (from the remembered starting points), and the cores."""
+        oracle's (from the remembered starting points; rtol_update, default
+        rtol), and the cores (rtol)."""
         dev = self.device_cores()
         before = getattr(self, "before", None)
         if before is None:
             for k, (G, O) in enumerate(zip(dev, self.state.cores)):
                 assert_close(G, O, rtol, f"core {k}")
             return
-        assert_update_close(dev, before[0], self.state.cores, before[1], rtol, store_eps(self.dtype_np))
+        assert_update_close(dev, before[0], self.state.cores, before[1],
+                            rtol if rtol_update is None else rtol_update, store_eps(self.dtype_np), rtol_core=rtol)
         self.before = None
 
     def debug(self, rec_n):

