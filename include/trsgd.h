@@ -87,8 +87,10 @@ typedef enum { TRSGD_DTYPE_F64 = 0, TRSGD_DTYPE_F32 = 1, TRSGD_DTYPE_BF16 = 2 } 
  * GRID: a short sequence of kernels over the whole GPU per iteration, the
  *   residual and gradient contractions on the tensor cores (tcgen05, BF16
  *   operands; FP32 as three BF16 pieces per operand); one problem, uniform
- *   sampling, plain variant, FP32 / BF16-mixed, R_n <= 32,
- *   R_n R_{n+1} <= 512.
+ *   sampling, plain and scaled variants, FP32 / BF16-mixed, R_n <= 32,
+ *   R_n R_{n+1} <= 512.  The scaled variant's Gram matrix is formed on the
+ *   tensor cores from three BF16 pieces of Z (FP32 accuracy in either
+ *   mode), then factored and applied in double-float arithmetic.
  * AUTO: CLUSTER when the problem fits it, else GRID. */
 typedef enum { TRSGD_PATH_AUTO = 0, TRSGD_PATH_CLUSTER = 1, TRSGD_PATH_GRID = 2 } trsgd_path;
 
@@ -252,6 +254,16 @@ trsgd_status trsgd_sampled_loss_grad(int32_t N, const int64_t *I, const int64_t 
  * trsgd_get_debug.  on = 0 stops recording. */
 trsgd_status trsgd_set_debug(trsgd_handle *h, int32_t on);
 
+/* Failure-path testing of the fused kernel: the number of polls of every
+ * bounded mbarrier wait (tensor-core completion, bulk fiber copies) before it
+ * latches TRSGD_ETIMEOUT.  A timed-out wait is followed by a second wait of
+ * the default length that drains the outstanding operation, and the launch
+ * runs to its end (its CTAs leave together); the host reads TRSGD_ETIMEOUT
+ * at the next synchronising call.  polls = 0 restores the default (2^22);
+ * a negative value makes every first try time out.  Applies to every problem
+ * of the handle.  Synchronising. */
+trsgd_status trsgd_set_wait_limit(trsgd_handle *h, int64_t polls);
+
 typedef enum {
   TRSGD_DBG_MODE = 0,   /* int32 [1]                                   */
   TRSGD_DBG_IDX = 1,    /* int32 [J][N], entry n = -1                  */
@@ -285,9 +297,55 @@ trsgd_status trsgd_launch_shape(trsgd_handle *h, int32_t set, int32_t *cluster,
                                 int32_t *threads);
 trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial);
 
+/* Sample-sharded iteration: data parallelism over the samples of
+ * Eq. S_gradient (and of Eq. S_hessian for the scaled variant), whose
+ * estimators are sums over samples.  Every rank holds the same X and the
+ * same cores, draws the same mode and the same Philox counters for
+ * iteration t, and takes a disjoint range of the |F| (and |H|) samples; the
+ * ranks exchange their FP32 partial sums once per iteration and all apply the
+ * same update.  Whole-GPU path only (TRSGD_EUNSUPPORTED otherwise).
+ *
+ * The samples of a batch fall into split units (a multiple of 256 samples,
+ * fixed by the problem and the device); one partial is one unit's sum
+ * (gelems = I_n R_n R_{n+1} floats for the gradient, helems =
+ * (R_n R_{n+1})^2 for the Gram).  trsgd_shard_plan deals the units of
+ * iteration t to `world` ranks in contiguous runs (rank r gets units
+ * [r U / world, (r+1) U / world) of U); a rank may get none.
+ *   trsgd_shard_plan    host-only; fills *out for rank `rank` of `world`.
+ *   trsgd_step_partial  writes this rank's partials, then zeros up to
+ *                       gsplits_max (hsplits_max) partials, into gpart_dev
+ *                       (hpart_dev, scaled only; else may be NULL).  Async.
+ *   trsgd_step_apply    sums gsplits partials of gparts_dev (and hsplits of
+ *                       hparts_dev) in increasing index, then the direction,
+ *                       step rule and update of G_n.  Pass the ranks'
+ *                       buffers gathered in rank order (an all-gather): the
+ *                       zero padding leaves every sum unchanged, so the
+ *                       result is bit-identical to trsgd_step(t) on one
+ *                       device, and identical on every rank.  Async.
+ * The buffers are caller device memory of gsplits_max * gelems (per rank) or
+ * world * gsplits_max * gelems (gathered) floats. */
+typedef struct {
+  int32_t mode;                     /* n of iteration t                        */
+  int64_t j0, j1;                   /* this rank's samples of F                */
+  int64_t h0, h1;                   /* this rank's samples of H (J_H > 0)      */
+  int64_t gunit, hunit;             /* samples per unit of F and H             */
+  int64_t gsplits, hsplits;         /* partials this rank computes             */
+  int64_t gsplits_max, hsplits_max; /* the largest count over the ranks        */
+  int64_t gelems, helems;           /* floats per partial                      */
+} trsgd_shard;
+
+trsgd_status trsgd_shard_plan(trsgd_handle *h, int64_t t, int32_t rank, int32_t world, trsgd_shard *out);
+trsgd_status trsgd_step_partial(trsgd_handle *h, int64_t t, const trsgd_shard *plan, float *gpart_dev,
+                                float *hpart_dev);
+trsgd_status trsgd_step_apply(trsgd_handle *h, int64_t t, const float *gparts_dev, int64_t gsplits,
+                              const float *hparts_dev, int64_t hsplits);
+
 /* Number of iteration kernels enqueued by this handle so far (the fused
  * kernel counts once per launch of any number of iterations; the whole-GPU
- * path launches five kernels per iteration). */
+ * path launches per iteration: G_n's pieces, the samples, one transpose per
+ * kept piece of Z, the residual, the gradient and the update; the scaled
+ * variant replaces the update by the Gram, its factorisation and the
+ * direction, plus the H batch's samples and transposes when J_H > 0). */
 int64_t trsgd_launch_count(const trsgd_handle *h);
 
 /* One iteration of the full-gradient methods the paper compares against

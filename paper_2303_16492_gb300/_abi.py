@@ -43,6 +43,18 @@ class Config(ctypes.Structure):
     ]
 
 
+class Shard(ctypes.Structure):
+    _fields_ = [
+        ("mode", ctypes.c_int32),
+        ("j0", ctypes.c_int64), ("j1", ctypes.c_int64),
+        ("h0", ctypes.c_int64), ("h1", ctypes.c_int64),
+        ("gunit", ctypes.c_int64), ("hunit", ctypes.c_int64),
+        ("gsplits", ctypes.c_int64), ("hsplits", ctypes.c_int64),
+        ("gsplits_max", ctypes.c_int64), ("hsplits_max", ctypes.c_int64),
+        ("gelems", ctypes.c_int64), ("helems", ctypes.c_int64),
+    ]
+
+
 class TrsgdError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -86,6 +98,13 @@ _SIGNATURES = {
     "trsgd_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
     "trsgd_tensor_pieces": (ctypes.c_int32, [ctypes.c_void_p]),
     "trsgd_gd_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_double]),
+    "trsgd_shard_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                        ctypes.POINTER(Shard)]),
+    "trsgd_step_partial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(Shard), ctypes.c_void_p,
+                                          ctypes.c_void_p]),
+    "trsgd_step_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_int64]),
+    "trsgd_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
     "trsgd_destroy": (None, [ctypes.c_void_p]),
     "trsgd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

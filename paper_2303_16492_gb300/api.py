@@ -158,6 +158,29 @@ class Solver:
         problem 0, every core from the same iterate."""
         check(_abi.lib().trsgd_gd_step(self._h, 1 if scaled else 0, float(alpha), float(damping)), "trsgd_gd_step")
 
+    def set_wait_limit(self, polls: int):
+        """trsgd_set_wait_limit (failure-path testing; 0 restores the default)."""
+        check(_abi.lib().trsgd_set_wait_limit(self._h, int(polls)), "trsgd_set_wait_limit")
+
+    def shard_plan(self, t: int, rank: int, world: int) -> _abi.Shard:
+        """trsgd_shard_plan: this rank's sample ranges of iteration t."""
+        sh = _abi.Shard()
+        check(_abi.lib().trsgd_shard_plan(self._h, int(t), int(rank), int(world), ctypes.byref(sh)),
+              "trsgd_shard_plan")
+        return sh
+
+    def step_partial(self, t: int, plan: _abi.Shard, gpart, hpart=None):
+        """trsgd_step_partial into FP32 device buffers of gsplits_max (hsplits_max) partials."""
+        hp = ctypes.c_void_p(hpart.data_ptr()) if hpart is not None else None
+        check(_abi.lib().trsgd_step_partial(self._h, int(t), ctypes.byref(plan), ctypes.c_void_p(gpart.data_ptr()),
+                                            hp), "trsgd_step_partial")
+
+    def step_apply(self, t: int, gparts, gsplits: int, hparts=None, hsplits: int = 0):
+        """trsgd_step_apply over the gathered partials (rank order)."""
+        hp = ctypes.c_void_p(hparts.data_ptr()) if hparts is not None else None
+        check(_abi.lib().trsgd_step_apply(self._h, int(t), ctypes.c_void_p(gparts.data_ptr()), int(gsplits), hp,
+                                          int(hsplits)), "trsgd_step_apply")
+
     def tensor_pieces(self) -> int:
         """BF16 pieces per tensor-core operand of the two contractions (0: FMA units)."""
         return int(_abi.lib().trsgd_tensor_pieces(self._h))

@@ -95,11 +95,12 @@ static bool cluster_fits(const trsgd_config *cfg, int32_t np) {
 static bool grid_fits(const trsgd_config *cfg, int32_t np) {
   if (np != 1) return false;
   const trsgd_config &c = cfg[0];
-  if (c.dist != TRSGD_DIST_UNIFORM || c.variant != TRSGD_PLAIN || c.prec == TRSGD_FP64) return false;
+  if (c.dist != TRSGD_DIST_UNIFORM || c.prec == TRSGD_FP64) return false;
   if (c.prec == TRSGD_FP32 && c.fp32_units == TRSGD_FP32_FMA) return false;   // pieces only
-  if (c.J > (1LL << 24)) return false;
+  if (c.J > (1LL << 24) || c.J_H > (1LL << 24)) return false;
   for (int k = 0; k < c.N; ++k) {
     if (c.R[k] > 32 || c.R[k] * c.R[(k + 1) % c.N] > 512) return false;
+    if (c.variant == TRSGD_SCALED && c.R[k] * c.R[(k + 1) % c.N] > kGridScaledMaxQ) return false;
     if (c.I[k] > (1LL << 24)) return false;
   }
   return true;
@@ -546,22 +547,32 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
       Ri[k] = (int)c.R[k];
     }
     const int np = c.prec == TRSGD_BF16_MIXED ? 1 : 3;
-    grid_layout(Ii, Ri, c.N, (int)c.J, np, g);
+    const int scaled = c.variant == TRSGD_SCALED ? 1 : 0;
+    grid_layout(Ii, Ri, c.N, (int)c.J, np, scaled, (int)c.J_H, g);
     g.x_bf16 = h->xc_dtype == TRSGD_DTYPE_BF16 ? 1 : 0;
     g.w = (float)(1.0 / (double)c.J);
     const size_t bf = 2;
-    for (int p = 0; p < np && e == cudaSuccess; ++p) {
-      if ((e = h->buf.alloc((void **)&g.Gp[p], (size_t)g.Ip * g.ldg * bf)) != cudaSuccess ||
-          (e = h->buf.alloc((void **)&g.Zp[p], (size_t)g.Jp * g.ldz * bf)) != cudaSuccess ||
-          (e = h->buf.alloc((void **)&g.ZTp[p], (size_t)g.QTp * g.ldzt * bf)) != cudaSuccess ||
-          (e = h->buf.alloc((void **)&g.Ep[p], (size_t)g.Ip * g.lde * bf)) != cudaSuccess)
+    for (int p = 0; p < 3; ++p) g.Gp[p] = g.Zp[p] = g.ZTp[p] = g.Ep[p] = nullptr;
+    for (int p = 0; p < g.npz && e == cudaSuccess; ++p) {
+      if ((e = h->buf.alloc((void **)&g.Zp[p], (size_t)g.Jp * g.ldz * bf)) != cudaSuccess ||
+          (e = h->buf.alloc((void **)&g.ZTp[p], (size_t)g.QTp * g.ldzt * bf)) != cudaSuccess)
         break;
       cudaMemsetAsync(g.Zp[p], 0, (size_t)g.Jp * g.ldz * bf, h->stream);
       cudaMemsetAsync(g.ZTp[p], 0, (size_t)g.QTp * g.ldzt * bf, h->stream);
+      if (p < np && ((e = h->buf.alloc((void **)&g.Gp[p], (size_t)g.Ip * g.ldg * bf)) != cudaSuccess ||
+                     (e = h->buf.alloc((void **)&g.Ep[p], (size_t)g.Ip * g.lde * bf)) != cudaSuccess))
+        break;
     }
-    for (int p = np; p < 3; ++p) g.Gp[p] = g.Zp[p] = g.ZTp[p] = g.Ep[p] = nullptr;
     if (e == cudaSuccess) e = h->buf.alloc((void **)&g.gpart, g.gpart_elems * 4);
     if (e == cudaSuccess) e = h->buf.alloc((void **)&g.col, (size_t)c.J * 8);
+    if (e == cudaSuccess && scaled) {
+      int qmax = 1;
+      for (int k = 0; k < c.N; ++k) qmax = std::max(qmax, Ri[k] * Ri[(k + 1) % c.N]);
+      if ((e = h->buf.alloc((void **)&g.hpart, g.hpart_elems * 4)) == cudaSuccess &&
+          (e = h->buf.alloc((void **)&g.Lfac, grid_scaled_factor_floats(qmax) * 4)) == cudaSuccess &&
+          (e = h->buf.alloc((void **)&g.fac_ok, 16)) == cudaSuccess)
+        e = grid_scaled_prepare();
+    }
     if (e == cudaSuccess) e = grid_prepare_gemm();
     if (e == cudaSuccess) e = grid_tensor_maps(Ri, c.N, g);
     if (e != cudaSuccess) return fail(from_cuda(e));
@@ -595,7 +606,9 @@ static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
       const int n = draw_mode(D.seed, t, D.N);
       cudaError_t e = launch_grid_step(h->gp, D, n, t, h->dbg ? 1 : 0, h->stream);
       if (e != cudaSuccess) return from_cuda(e);
-      h->launches += 5;
+      // prepare, samples, transpose(s), residual, gradient, update; scaled:
+      // (H samples and transposes,) Gram, factor and direction instead of the update
+      h->launches += 4 + h->gp.npz + (h->gp.scaled ? (h->gp.JH > 0 ? 3 + h->gp.npz : 2) : 1);
     }
     return TRSGD_OK;
   }
@@ -785,6 +798,15 @@ trsgd_status trsgd_set_debug(trsgd_handle *h, int32_t on) {
   return from_cuda(e);
 }
 
+trsgd_status trsgd_set_wait_limit(trsgd_handle *h, int64_t polls) {
+  if (!h) return TRSGD_EINVAL;
+  for (auto &D : h->hdesc) D.wait_limit = polls;
+  cudaError_t e = cudaMemcpyAsync(h->ddesc, h->hdesc.data(), sizeof(ProbDesc) * h->nprob, cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return from_cuda(e);
+}
+
 trsgd_status trsgd_get_debug(trsgd_handle *h, int32_t item, void *out_host, size_t bytes, size_t *written) {
   if (!h || item < 0 || item > 7 || !out_host) return TRSGD_EINVAL;
   if (!h->dbg_ptr[item]) return TRSGD_EINVAL;
@@ -933,6 +955,85 @@ trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial) {
 }
 
 int64_t trsgd_launch_count(const trsgd_handle *h) { return h ? h->launches : -1; }
+
+trsgd_status trsgd_shard_plan(trsgd_handle *h, int64_t t, int32_t rank, int32_t world, trsgd_shard *out) {
+  if (!h || !out || t < 0 || world < 1 || rank < 0 || rank >= world) return TRSGD_EINVAL;
+  if (!h->grid) return TRSGD_EUNSUPPORTED;
+  const ProbDesc &D = h->hdesc[0];
+  const GridPath &g = h->gp;
+  const int n = draw_mode(D.seed, t, D.N);
+  const long long Q = (long long)D.R[n] * D.R[(n + 1) % D.N];
+  trsgd_shard sh = {};
+  sh.mode = n;
+  auto deal = [&](long long total, long long unit, int64_t &a, int64_t &b, int64_t &cnt, int64_t &mx) {
+    const long long U = (total + unit - 1) / unit;
+    const long long u0 = U * rank / world, u1 = U * (rank + 1) / world;
+    a = std::min<long long>(u0 * unit, total);
+    b = std::min<long long>(u1 * unit, total);
+    cnt = u1 - u0;
+    mx = (U + world - 1) / world;
+  };
+  sh.gunit = grid_split_unit(g, D, n, D.J);
+  deal(D.J, sh.gunit, sh.j0, sh.j1, sh.gsplits, sh.gsplits_max);
+  sh.gelems = (long long)D.I[n] * Q;
+  if (g.scaled) {
+    const long long JH = g.JH > 0 ? g.JH : D.J;
+    sh.hunit = grid_split_unit(g, D, n, JH);
+    if (g.JH > 0) {
+      deal(JH, sh.hunit, sh.h0, sh.h1, sh.hsplits, sh.hsplits_max);
+    } else {   // H = F: the Gram over this rank's F samples, in the same units
+      sh.h0 = sh.j0;
+      sh.h1 = sh.j1;
+      sh.hsplits = sh.gsplits;
+      sh.hsplits_max = sh.gsplits_max;
+    }
+    sh.helems = Q * Q;
+  }
+  *out = sh;
+  return TRSGD_OK;
+}
+
+trsgd_status trsgd_step_partial(trsgd_handle *h, int64_t t, const trsgd_shard *plan, float *gpart_dev,
+                                float *hpart_dev) {
+  if (!h || !plan || t < 0 || !gpart_dev) return TRSGD_EINVAL;
+  if (!h->grid) return TRSGD_EUNSUPPORTED;
+  const ProbDesc &D = h->hdesc[0];
+  const GridPath &g = h->gp;
+  const int n = draw_mode(D.seed, t, D.N);
+  if (plan->mode != n || (g.scaled && !hpart_dev)) return TRSGD_EINVAL;
+  if (plan->gsplits > plan->gsplits_max || plan->hsplits > plan->hsplits_max) return TRSGD_EINVAL;
+  cudaError_t e = launch_grid_partial(g, D, n, t, plan->j0, plan->j1, g.JH > 0 ? plan->h0 : 0,
+                                      g.JH > 0 ? plan->h1 : 0, h->dbg ? 1 : 0, gpart_dev, hpart_dev, h->stream);
+  if (e == cudaErrorInvalidValue) return TRSGD_EINVAL;
+  // zero partials up to the common count, so that a gather of every rank's
+  // buffer sums to the same values
+  if (e == cudaSuccess && plan->gsplits_max > plan->gsplits)
+    e = cudaMemsetAsync(gpart_dev + plan->gsplits * plan->gelems, 0,
+                        (size_t)(plan->gsplits_max - plan->gsplits) * plan->gelems * sizeof(float), h->stream);
+  if (e == cudaSuccess && g.scaled && plan->hsplits_max > plan->hsplits)
+    e = cudaMemsetAsync(hpart_dev + plan->hsplits * plan->helems, 0,
+                        (size_t)(plan->hsplits_max - plan->hsplits) * plan->helems * sizeof(float), h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  // prepare, samples, transposes, residual, gradient (+ H samples and transposes), Gram
+  h->launches += 4 + g.npz + (g.scaled ? (g.JH > 0 ? 2 + g.npz : 1) : 0);
+  return TRSGD_OK;
+}
+
+trsgd_status trsgd_step_apply(trsgd_handle *h, int64_t t, const float *gparts_dev, int64_t gsplits,
+                              const float *hparts_dev, int64_t hsplits) {
+  if (!h || t < 0 || !gparts_dev || gsplits < 1 || gsplits > (1 << 20)) return TRSGD_EINVAL;
+  if (!h->grid) return TRSGD_EUNSUPPORTED;
+  const GridPath &g = h->gp;
+  if (g.scaled && (!hparts_dev || hsplits < 1 || hsplits > (1 << 20))) return TRSGD_EINVAL;
+  const ProbDesc &D = h->hdesc[0];
+  const int n = draw_mode(D.seed, t, D.N);
+  cudaError_t e = launch_grid_apply(g, D, n, gparts_dev, (int)gsplits, hparts_dev, (int)hsplits, h->dbg ? 1 : 0,
+                                    h->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  h->launches += g.scaled ? 2 : 1;
+  h->t_next = t + 1;
+  return TRSGD_OK;
+}
 
 trsgd_status trsgd_gd_step(trsgd_handle *h, int32_t scaled, double alpha, double damping) {
   if (!h || (scaled != 0 && scaled != 1) || !std::isfinite(alpha) || !std::isfinite(damping) || damping < 0)

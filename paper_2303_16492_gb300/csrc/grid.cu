@@ -73,6 +73,8 @@ __global__ void grid_prepare_kernel(const float *__restrict__ G, int In, int Q, 
 // ---- 2. samples and sampled subchain rows ---------------------------------
 struct GridSampleArgs {
   int N, n, J, Q, Qp, np, rec;
+  int j0, j1;                           // sample range of this launch
+  int stream;                           // Philox stream: F (fibers drawn) or H (Hessian batch)
   int I[kMaxOrder], R[kMaxOrder];
   unsigned long long seed;
   long long t;
@@ -99,18 +101,18 @@ __global__ void __launch_bounds__(32 * kGridWarps) grid_samples_kernel(GridSampl
   for (int s = 0; s < kMaxOrder; ++s) order[s] = (s < L) ? (n + 1 + s) % N : 0;
   if (a.rec && blockIdx.x == 0 && threadIdx.x == 0) *a.dbg_n = n;
   const int Rn = a.R[n], Rn1 = a.R[(n + 1) % N];
-  for (int j = blockIdx.x * kGridWarps + warp; j < a.J; j += gridDim.x * kGridWarps) {
+  for (int j = a.j0 + blockIdx.x * kGridWarps + warp; j < a.j1; j += gridDim.x * kGridWarps) {
     // slice indices of the L cores in ring order, one lane per core
     int myi = 0;
     if (lane < L) {
       const int k = order[lane];
-      const uint64_t u = draw_u64(a.seed, a.t, kStreamF, k, (uint32_t)j);
+      const uint64_t u = draw_u64(a.seed, a.t, a.stream, k, (uint32_t)j);
       myi = (int)mulhi64(u, (uint64_t)a.I[k]);
     }
     int idx[kMaxOrder];
 #pragma unroll
     for (int s = 0; s < kMaxOrder; ++s) idx[s] = __shfl_sync(0xffffffffu, myi, s);
-    if (lane == 0) {
+    if (lane == 0 && a.col) {
       long long col = 0, st = 1;
       for (int s = 0; s < L; ++s) {
         col += (long long)idx[s] * st;
@@ -205,7 +207,9 @@ struct __align__(64) GridGemmArgs {
   CUtensorMap tmA[3];
   CUtensorMap tmB[3];
   int npa, npb, maxord;
-  int kchunks, kper;       // chunks of 64 along K in total / per split (blockIdx.z)
+  int kchunks, kper;       // chunks of 64 along K in this launch / per split (blockIdx.z)
+  int kbase;               // first chunk of K (sample range of the launch)
+  int nbase;               // first output column (residual: first sample of the range)
   int NT, S;               // N tile (multiple of 16, <= 256), pipeline stages (2..4)
   int xpre;                // residual: gather the X tile at kernel start into its own region after the stages
   int mode;                // 0: FP32 partials C[z][m][n]; 1: residual epilogue
@@ -288,8 +292,8 @@ __global__ void __launch_bounds__(kGemmThreads) grid_gemm_kernel(const __grid_co
   // the 128-byte swizzle repeats every 1024 bytes: align the stage ring to it
   unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.x * 128, n0 = blockIdx.y * NT;
-  const int kbeg = blockIdx.z * a.kper, kend = min(kbeg + a.kper, a.kchunks);
+  const int m0 = blockIdx.x * 128, n0 = a.nbase + blockIdx.y * NT;
+  const int kbeg = a.kbase + blockIdx.z * a.kper, kend = min(kbeg + a.kper, a.kbase + a.kchunks);
   const int nck = max(0, kend - kbeg);
   const size_t stage = grid_gemm_stage_bytes(npa, npb, NT);
   const int S = a.S;
@@ -485,10 +489,10 @@ __global__ void __launch_bounds__(kGemmThreads) grid_gemm_kernel(const __grid_co
 }
 
 // ---- Z^T from Z (32 x 32 tiles through shared memory) ------------------------
-__global__ void grid_transpose_kernel(const __nv_bfloat16 *__restrict__ Z, long long ldz, int rows, int cols,
-                                      __nv_bfloat16 *__restrict__ ZT, long long ldzt) {
+__global__ void grid_transpose_kernel(const __nv_bfloat16 *__restrict__ Z, long long ldz, int row0, int rows,
+                                      int cols, __nv_bfloat16 *__restrict__ ZT, long long ldzt) {
   __shared__ unsigned short tile[32][34];
-  const int j0 = blockIdx.x * 32, q0 = blockIdx.y * 32;
+  const int j0 = row0 + blockIdx.x * 32, q0 = blockIdx.y * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const unsigned short *z = reinterpret_cast<const unsigned short *>(Z);
   unsigned short *zt = reinterpret_cast<unsigned short *>(ZT);
@@ -497,9 +501,12 @@ __global__ void grid_transpose_kernel(const __nv_bfloat16 *__restrict__ Z, long 
     tile[r][tx] = (j < rows && q < cols) ? z[(size_t)j * ldz + q] : (unsigned short)0;
   }
   __syncthreads();
+  // rows past the batch end up to the next 64-sample chunk are written as
+  // zeros: a contraction over the batch reads whole chunks
+  const int rows_pad = (rows + 63) / 64 * 64;
   for (int r = ty; r < 32; r += 8) {
     const int q = q0 + r, j = j0 + tx;
-    if (q < cols && j < rows) zt[(size_t)q * ldzt + j] = tile[tx][r];
+    if (q < cols && j < rows_pad) zt[(size_t)q * ldzt + j] = tile[tx][r];
   }
 }
 
@@ -574,12 +581,120 @@ cudaError_t grid_prepare_gemm() {
   return cudaFuncSetAttribute(grid_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
 }
 
-// one iteration t of the grid path on mode n
-cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long long t, int rec, cudaStream_t s) {
+// Split-K unit of a contraction over nsamples samples with `tiles` output
+// tiles: at most one wave of CTAs (the stages fill most of shared memory),
+// at most max_splits partials, in chunks of 64 samples rounded to a multiple
+// of 256 samples so that sample ranges on unit boundaries align with every
+// N tile of the residual GEMM.
+static long long split_unit(const GridPath &g, long long nsamples, int tiles) {
+  const long long kch = (nsamples + 255) / 256 * 4;
+  const long long splits = std::max<long long>(1, std::min<long long>(std::min<long long>(g.max_splits, kch),
+                                                                      g.sms / std::max(tiles, 1)));
+  long long kper = (kch + splits - 1) / splits;
+  kper = (kper + 3) / 4 * 4;
+  return kper * 64;
+}
+
+// N tiling over the Q columns of the gradient and the Gram: with the scaled
+// variant both read Z^T through the same tensor maps, so both take the
+// three-piece tile width
+static int gemm_ntiles(const GridPath &g, int Q, int &NT) { return grid_ntiles(Q, g.scaled ? 3 : g.np, NT); }
+
+long long grid_split_unit(const GridPath &g, const ProbDesc &D, int n, long long nsamples) {
+  const int N = D.N, In = D.I[n], Q = D.R[n] * D.R[(n + 1) % N];
+  int NT = 0;
+  const int ntile = gemm_ntiles(g, Q, NT);
+  return split_unit(g, nsamples, ((In + 127) / 128) * ntile);
+}
+
+static int nsplits(long long j0, long long j1, long long unit) { return (int)((j1 - j0 + unit - 1) / unit); }
+
+// Z (and Z^T) of the samples [j0, j1) on Philox stream `stream`; fiber
+// columns only for the F batch
+static cudaError_t launch_samples(const GridPath &g, const ProbDesc &D, int n, long long t, long long j0,
+                                  long long j1, int stream, int rec, cudaStream_t s) {
+  const int N = D.N, Q = D.R[n] * D.R[(n + 1) % N];
+  const int Qp = (Q + 63) / 64 * 64;
+  GridSampleArgs sa = {};
+  sa.N = N;
+  sa.n = n;
+  sa.J = D.J;
+  sa.Q = Q;
+  sa.Qp = Qp;
+  sa.np = g.npz;
+  sa.rec = rec;
+  sa.j0 = (int)j0;
+  sa.j1 = (int)j1;
+  sa.stream = stream;
+  for (int k = 0; k < N; ++k) {
+    sa.I[k] = D.I[k];
+    sa.R[k] = D.R[k];
+    sa.cores[k] = static_cast<const float *>(D.cores[k]);
+  }
+  sa.seed = D.seed;
+  sa.t = t;
+  sa.col = stream == kStreamF ? g.col : nullptr;
+  for (int p = 0; p < 3; ++p) sa.Z[p] = g.Zp[p];
+  sa.ldz = g.ldz;
+  sa.dbg_idx = D.dbg_idx;
+  sa.dbg_pf = D.dbg_pf;
+  sa.dbg_z = static_cast<float *>(D.dbg_z);
+  sa.dbg_n = D.dbg_n;
+  const int blocks = (int)std::max<long long>(1, std::min<long long>((j1 - j0 + kGridWarps - 1) / kGridWarps,
+                                                                     8 * (long long)g.sms));
+  grid_samples_kernel<<<blocks, 32 * kGridWarps, 0, s>>>(sa);
+  cudaError_t e = cudaGetLastError();
+  // Z^T for the gradient's K-major B operand (and both Gram operands)
+  for (int p = 0; p < g.npz && e == cudaSuccess; ++p) {
+    dim3 grid((unsigned)(((j1 + 63) / 64 * 64 - j0 + 31) / 32), (Q + 31) / 32);
+    grid_transpose_kernel<<<grid, 256, 0, s>>>(g.Zp[p], g.ldz, (int)j0, (int)j1, Q, g.ZTp[p], g.ldzt);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+// Z^T Z over the samples [j0, j1) held in Z^T, one FP32 partial per unit
+static cudaError_t launch_gram(const GridPath &g, int Q, long long j0, long long j1, long long unit, int n,
+                               float *hout, int *status, cudaStream_t s) {
+  int NT = 0;
+  const int ntile = grid_ntiles(Q, 3, NT);
+  GridGemmArgs ga = {};
+  for (int p = 0; p < 3; ++p) {
+    ga.tmA[p] = g.tmZTa[p];
+    ga.tmB[p] = g.tmZT[n][p];
+  }
+  ga.npa = ga.npb = 3;
+  ga.maxord = 2;
+  ga.kbase = (int)(j0 / 64);
+  ga.kchunks = (int)((j1 - j0 + 63) / 64);
+  ga.kper = (int)(unit / 64);
+  ga.nbase = 0;
+  ga.NT = NT;
+  ga.S = grid_stages(3, 3, NT);
+  if (ga.S < 2) return cudaErrorInvalidConfiguration;
+  ga.mode = 0;
+  ga.C = hout;
+  ga.ldc = Q;
+  ga.cstride = (long long)Q * Q;
+  ga.Mv = Q;
+  ga.Nv = Q;
+  ga.status = status;
+  dim3 grid((unsigned)((Q + 127) / 128), ntile, nsplits(j0, j1, unit));
+  grid_gemm_kernel<<<grid, kGemmThreads, grid_gemm_smem(3, 3, NT, ga.S), s>>>(ga);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, long long t, long long j0,
+                                long long j1, long long h0, long long h1, int rec, float *gout, float *hout,
+                                cudaStream_t s) {
   const int N = D.N, In = D.I[n], Q = D.R[n] * D.R[(n + 1) % N];
   const int Ip = (In + 127) / 128 * 128, Qp = (Q + 63) / 64 * 64;
   const int np = g.np;
   cudaError_t e;
+  const long long unit = grid_split_unit(g, D, n, D.J);
+  if (j0 < 0 || j1 > D.J || j0 > j1 || (j0 % unit) != 0 || ((j1 % unit) != 0 && j1 != D.J))
+    return cudaErrorInvalidValue;
+  if (j1 == j0) return cudaSuccess;
   // 1. operand pieces of G_n
   {
     const long long total = (long long)Ip * Qp;
@@ -588,38 +703,10 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
                                                g.Gp[0], g.Gp[1], g.Gp[2]);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // 2. samples and Z
-  {
-    GridSampleArgs sa = {};
-    sa.N = N;
-    sa.n = n;
-    sa.J = D.J;
-    sa.Q = Q;
-    sa.Qp = Qp;
-    sa.np = np;
-    sa.rec = rec;
-    for (int k = 0; k < N; ++k) {
-      sa.I[k] = D.I[k];
-      sa.R[k] = D.R[k];
-      sa.cores[k] = static_cast<const float *>(D.cores[k]);
-    }
-    sa.seed = D.seed;
-    sa.t = t;
-    sa.col = g.col;
-    for (int p = 0; p < 3; ++p) {
-      sa.Z[p] = g.Zp[p];
-    }
-    sa.ldz = g.ldz;
-    sa.dbg_idx = D.dbg_idx;
-    sa.dbg_pf = D.dbg_pf;
-    sa.dbg_z = static_cast<float *>(D.dbg_z);
-    sa.dbg_n = D.dbg_n;
-    const int blocks = (int)std::min<long long>((D.J + kGridWarps - 1) / kGridWarps, 8 * grid_sm_count());
-    grid_samples_kernel<<<blocks, 32 * kGridWarps, 0, s>>>(sa);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
+  // 2. samples of F and Z (and Z^T)
+  if ((e = launch_samples(g, D, n, t, j0, j1, kStreamF, rec, s)) != cudaSuccess) return e;
   const int maxord = np == 1 ? 0 : 2;
-  // 3. residual: E = G_n Z^T - X_S (M = Ip, N = Jp, K = Qp), weighted, as pieces
+  // 3. residual: E = G_n Z^T - X_S (M = Ip, N = the samples of the range, K = Qp), weighted, as pieces
   {
     GridGemmArgs ga = {};
     for (int p = 0; p < 3; ++p) ga.E[p] = g.Ep[p];
@@ -629,9 +716,11 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     }
     ga.npa = ga.npb = np;
     ga.maxord = maxord;
+    ga.kbase = 0;
     ga.kchunks = Qp / 64;
     ga.kper = ga.kchunks;
     ga.NT = g.nt_res;
+    ga.nbase = (int)j0;
     {   // X tile in its own region when at least three stages still fit beside it
       const size_t xb = (size_t)ga.NT * 128 * (g.x_bf16 ? 2 : 4);
       const int sx3 = grid_stages_budget(np, np, ga.NT, xb);
@@ -641,7 +730,7 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     if (ga.S < 2) return cudaErrorInvalidConfiguration;
     ga.mode = 1;
     ga.Mv = In;
-    ga.Nv = D.J;
+    ga.Nv = (int)j1;
     ga.xmode = D.xmode[n];
     ga.ldx = D.ldx[n];
     ga.x_bf16 = g.x_bf16;
@@ -651,26 +740,14 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     ga.npe = np;
     ga.dbg_e = rec ? static_cast<float *>(D.dbg_e) : nullptr;
     ga.status = D.status;
-    dim3 grid(Ip / 128, g.Jp / ga.NT, 1);
+    dim3 grid(Ip / 128, (unsigned)((j1 - j0 + ga.NT - 1) / ga.NT), 1);
     grid_gemm_kernel<<<grid, kGemmThreads, grid_gemm_smem(np, np, ga.NT, ga.S) + (ga.xpre ? (size_t)ga.NT * 128 * (g.x_bf16 ? 2 : 4) : 0), s>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // Z^T for the gradient's K-major B operand
-  for (int p = 0; p < np; ++p) {
-    dim3 grid(g.Jp / 32, (Q + 31) / 32);
-    grid_transpose_kernel<<<grid, 256, 0, s>>>(g.Zp[p], g.ldz, g.Jp, Q, g.ZTp[p], g.ldzt);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  // 4. partial gradients: (E D) Z over slices of the samples (M = Ip, N = Q, K = Jp)
-  int NT = 0;
-  const int ntile = grid_ntiles(Q, np, NT);
-  int splits = 1;
+  // 4. partial gradients: (E D) Z over the units of the range (M = Ip, N = Q, K = samples)
   {
-    const int tiles = (Ip / 128) * ntile, kch = g.Jp / 64;
-    // one wave: at most one CTA per SM (the stages fill most of shared memory)
-    splits = std::max(1, std::min(std::min(g.max_splits, kch), grid_sm_count() / tiles));
-    const int kper = (kch + splits - 1) / splits;
-    splits = (kch + kper - 1) / kper;
+    int NT = 0;
+    const int ntile = gemm_ntiles(g, Q, NT);
     GridGemmArgs ga = {};
     for (int p = 0; p < np; ++p) {
       ga.tmA[p] = g.tmE[p];
@@ -678,47 +755,102 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     }
     ga.npa = ga.npb = np;
     ga.maxord = maxord;
-    ga.kchunks = kch;
-    ga.kper = kper;
+    ga.kbase = (int)(j0 / 64);
+    ga.kchunks = (int)((j1 - j0 + 63) / 64);
+    ga.kper = (int)(unit / 64);
+    ga.nbase = 0;
     ga.NT = NT;
     ga.S = grid_stages(np, np, NT);
     if (ga.S < 2) return cudaErrorInvalidConfiguration;
     ga.mode = 0;
-    ga.C = g.gpart;
+    ga.C = gout;
     ga.ldc = Q;
     ga.cstride = (long long)In * Q;
     ga.Mv = In;
     ga.Nv = Q;
     ga.status = D.status;
-    dim3 grid(Ip / 128, ntile, splits);
+    dim3 grid(Ip / 128, ntile, nsplits(j0, j1, unit));
     grid_gemm_kernel<<<grid, kGemmThreads, grid_gemm_smem(np, np, NT, ga.S), s>>>(ga);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  // 5. update
-  {
-    GridUpdateArgs ua = {};
-    ua.gpart = g.gpart;
-    ua.cstride = (long long)In * Q;
-    ua.splits = splits;
-    ua.In = In;
-    ua.Q = Q;
-    ua.rule = D.rule;
-    ua.rec = rec;
-    ua.alpha = (float)D.alpha;
-    ua.eta = (float)D.eta;
-    ua.b = (float)D.b;
-    ua.eps = D.eps;
-    ua.G = static_cast<float *>(D.cores[n]);
-    ua.acc = static_cast<float *>(D.acc[n]);
-    ua.dbg_g = static_cast<float *>(D.dbg_g);
-    ua.dbg_p = static_cast<float *>(D.dbg_p);
-    ua.status = D.status;
-    const long long total = (long long)In * Q;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
-    grid_update_kernel<<<blocks, 256, 0, s>>>(ua);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // 5. scaled variant: partial Grams of the Hessian batch (H = F: the same samples)
+  if (g.scaled) {
+    if (g.JH > 0) {
+      const long long uh = grid_split_unit(g, D, n, g.JH);
+      if (h0 < 0 || h1 > g.JH || h0 > h1 || (h0 % uh) != 0 || ((h1 % uh) != 0 && h1 != g.JH))
+        return cudaErrorInvalidValue;
+      if (h1 > h0) {
+        if ((e = launch_samples(g, D, n, t, h0, h1, kStreamH, 0, s)) != cudaSuccess) return e;
+        if ((e = launch_gram(g, Q, h0, h1, uh, n, hout, D.status, s)) != cudaSuccess) return e;
+      }
+    } else if ((e = launch_gram(g, Q, j0, j1, unit, n, hout, D.status, s)) != cudaSuccess) {
+      return e;
+    }
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_grid_apply(const GridPath &g, const ProbDesc &D, int n, const float *gparts, int gsplits,
+                              const float *hparts, int hsplits, int rec, cudaStream_t s) {
+  const int N = D.N, In = D.I[n], Q = D.R[n] * D.R[(n + 1) % N];
+  if (g.scaled) {
+    GridScaledArgs sa = {};
+    sa.hpart = hparts;
+    sa.hstride = (long long)Q * Q;
+    sa.hsplits = hsplits;
+    sa.gpart = gparts;
+    sa.gstride = (long long)In * Q;
+    sa.gsplits = gsplits;
+    sa.In = In;
+    sa.Q = Q;
+    sa.hscale = 1.0 / (double)(g.JH > 0 ? g.JH : D.J);
+    sa.damping = D.damping;
+    sa.Lfac = g.Lfac;
+    sa.ok = g.fac_ok;
+    sa.rule = D.rule;
+    sa.alpha = (float)D.alpha;
+    sa.eta = (float)D.eta;
+    sa.b = (float)D.b;
+    sa.eps = D.eps;
+    sa.G = static_cast<float *>(D.cores[n]);
+    sa.acc = static_cast<float *>(D.acc[n]);
+    sa.dbg_g = rec ? static_cast<float *>(D.dbg_g) : nullptr;
+    sa.dbg_p = rec ? static_cast<float *>(D.dbg_p) : nullptr;
+    sa.dbg_h = rec ? D.dbg_h : nullptr;
+    sa.status = D.status;
+    return launch_grid_scaled(sa, s);
+  }
+  GridUpdateArgs ua = {};
+  ua.gpart = gparts;
+  ua.cstride = (long long)In * Q;
+  ua.splits = gsplits;
+  ua.In = In;
+  ua.Q = Q;
+  ua.rule = D.rule;
+  ua.rec = rec;
+  ua.alpha = (float)D.alpha;
+  ua.eta = (float)D.eta;
+  ua.b = (float)D.b;
+  ua.eps = D.eps;
+  ua.G = static_cast<float *>(D.cores[n]);
+  ua.acc = static_cast<float *>(D.acc[n]);
+  ua.dbg_g = static_cast<float *>(D.dbg_g);
+  ua.dbg_p = static_cast<float *>(D.dbg_p);
+  ua.status = D.status;
+  const long long total = (long long)In * Q;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+  grid_update_kernel<<<blocks, 256, 0, s>>>(ua);
+  return cudaGetLastError();
+}
+
+// one iteration t of the grid path on mode n: every sample on this GPU
+cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long long t, int rec, cudaStream_t s) {
+  const long long JH = g.JH > 0 ? g.JH : D.J;
+  const int gs = nsplits(0, D.J, grid_split_unit(g, D, n, D.J));
+  const int hs = g.scaled ? nsplits(0, JH, grid_split_unit(g, D, n, JH)) : 0;
+  cudaError_t e = launch_grid_partial(g, D, n, t, 0, D.J, 0, g.JH, rec, g.gpart, g.hpart, s);
+  if (e == cudaSuccess) e = launch_grid_apply(g, D, n, g.gpart, gs, g.hpart, hs, rec, s);
+  return e;
 }
 
 // N tiling of the gradient GEMM over the Q columns: the number of tiles and
@@ -731,7 +863,7 @@ int grid_ntiles(int Q, int np, int &NT) {
 }
 
 // buffer sizes of the grid path for problem c; fills the layout fields of g
-void grid_layout(const int *I, const int *R, int N, int J, int np, GridPath &g) {
+void grid_layout(const int *I, const int *R, int N, int J, int np, int scaled, int JH, GridPath &g) {
   int Imax = 1, Qmax = 1;
   long long zcols = 1;   // columns of Z any tile reads: the K padding of the residual, the N tiles of the gradient
   for (int k = 0; k < N; ++k) {
@@ -743,8 +875,11 @@ void grid_layout(const int *I, const int *R, int N, int J, int np, GridPath &g) 
     zcols = std::max<long long>(zcols, std::max<long long>((Q + 63) / 64 * 64, (long long)ntile * NT));
   }
   g.np = np;
+  g.npz = scaled ? 3 : np;
+  g.scaled = scaled;
+  g.JH = scaled ? JH : 0;
   g.nt_res = grid_nt_max(np);
-  g.Jp = (J + 255) / 256 * 256;
+  g.Jp = (std::max(J, g.JH) + 255) / 256 * 256;
   g.Ip = (Imax + 127) / 128 * 128;
   g.Qp = (Qmax + 63) / 64 * 64;
   g.QTp = g.Qp;
@@ -754,7 +889,10 @@ void grid_layout(const int *I, const int *R, int N, int J, int np, GridPath &g) 
   g.lde = g.Jp;
   (void)zcols;
   g.max_splits = 16;
-  g.gpart_elems = (size_t)g.max_splits * Imax * Qmax;
+  g.sms = grid_sm_count();
+  // a range of samples yields at most max_splits + 1 partials (unit rounding)
+  g.gpart_elems = (size_t)(g.max_splits + 1) * Imax * Qmax;
+  g.hpart_elems = scaled ? (size_t)(g.max_splits + 1) * Qmax * Qmax : 0;
 }
 
 }  // namespace trsgd
@@ -789,11 +927,16 @@ cudaError_t grid_tensor_maps(const int *R, int N, GridPath &g) {
     if ((e = encode_map(fn, &g.tmG[p], g.Gp[p], g.Ip, g.ldg, 128)) != cudaSuccess) break;
     if ((e = encode_map(fn, &g.tmZ[p], g.Zp[p], g.Jp, g.ldz, g.nt_res)) != cudaSuccess) break;
     if ((e = encode_map(fn, &g.tmE[p], g.Ep[p], g.Ip, g.lde, 128)) != cudaSuccess) break;
+  }
+  // Z^T: every kept piece, as the B operand of mode n's gradient (and Gram)
+  // and as the A operand of the Gram
+  for (int p = 0; p < g.npz && e == cudaSuccess; ++p) {
     for (int n = 0; n < N && e == cudaSuccess; ++n) {
       int NT = 0;
-      grid_ntiles(R[n] * R[(n + 1) % N], g.np, NT);
+      grid_ntiles(R[n] * R[(n + 1) % N], g.scaled ? 3 : g.np, NT);
       e = encode_map(fn, &g.tmZT[n][p], g.ZTp[p], g.QTp, g.ldzt, NT);
     }
+    if (e == cudaSuccess && g.scaled) e = encode_map(fn, &g.tmZTa[p], g.ZTp[p], g.QTp, g.ldzt, 128);
   }
   return e;
 }

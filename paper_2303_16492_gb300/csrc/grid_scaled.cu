@@ -1,0 +1,512 @@
+// Scaled variant on the whole-GPU path (Sec. 3.3): the damped preconditioner
+// h = Z_H^T D_H Z_H / (|H| J_n) + eta^t I for R_n R_{n+1} up to 512, its
+// factorisation and the direction p = -g h^{-1} (Eq. scaledsg_direction),
+// followed by the step rule and the update of G_n.
+//
+// The Gram matrix itself is a tcgen05 GEMM of the grid path (three BF16 pieces
+// of Z, FP32 partial sums over slices of the samples); everything after it is
+// double-float arithmetic (df64.cuh, about 44-48 significant bits on the FP32
+// pipes, where native FP64 runs ~60x slower on this GPU):
+//
+//   grid_gram_factor_kernel   one cluster of 16 CTAs.  The fixed-order sum of
+//       the partial Grams, scaled by 1/|H|, plus the damping, is cut into
+//       32 x 32 blocks (the last block row padded with the identity), spread
+//       over the CTAs' shared memory in column-major block order, and
+//       factored h = L L^T by right-looking block elimination: per block
+//       column k (1) the owner of the diagonal block eliminates it (LDL^T
+//       with the row operations also applied to an identity, giving
+//       L_kk^{-1} = D^{-1/2} U^{-1}); (2) every CTA holding a block of the
+//       panel forms L_ik = A_ik L_kk^{-T}; (3) every trailing block takes
+//       A_ij -= L_ik L_jk^T with the panel blocks copied in from their
+//       owners through distributed shared memory.  A non-positive or
+//       non-finite pivot restarts the whole factorisation with the damping
+//       grown by 1e-12 tr(h)/Q * 10^m, m = 0..6 (then TRSGD_ENUMERIC).
+//       Output: every block of L below the diagonal and the inverted
+//       diagonal blocks, each stored as-is and transposed.
+//   grid_scaled_apply_kernel  one warp per row of g (8 rows per CTA, the
+//       blocks of L staged once per CTA in shared memory, double-buffered):
+//       the fixed-order sum of the partial gradients, then u L^T = -g by
+//       blocked forward substitution and p L = u by blocked backward
+//       substitution, each 32 x 32 diagonal step a product with the inverted
+//       block; then fixed alpha or AdaGrad and the update, exactly as the
+//       plain update kernel does with p = -g.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "df64.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace trsgd {
+
+namespace {
+
+constexpr int kGfB = 32;                                   // block size
+constexpr int kGfC = 16;                                   // CTAs of the cluster
+constexpr int kGfT = 512;                                  // threads per CTA
+constexpr int kGfMaxNb = kGridScaledMaxQ / kGfB;           // 16 block rows
+constexpr int kGfSlots = (kGfMaxNb * (kGfMaxNb + 1) / 2 + kGfC - 1) / kGfC;   // blocks per CTA
+constexpr int kGfPitchT = 33;                              // transposed staging pitch (conflict-free)
+constexpr int kGfPlaneT = kGfB * kGfPitchT;                // floats per transposed plane
+constexpr int kBlkF = 4 * kGfB * kGfB;                     // floats per output block: X hi, X lo, X^T hi, X^T lo
+
+// shared memory of the factor kernel (floats): local blocks (hi plane, lo
+// plane), the transposed panel staging, the row-major L_kk^{-1} / U^{-1}
+// buffer, and its transposed copy
+constexpr size_t kGfSlotF = 2 * kGfB * kGfB;
+constexpr size_t kGfSmemFloats = kGfSlots * kGfSlotF + kGfMaxNb * 2 * kGfPlaneT + kGfSlotF + 2 * kGfPlaneT;
+
+__device__ __forceinline__ df64 lds(const float *b, int e) { return df64{b[e], b[e + kGfB * kGfB]}; }
+__device__ __forceinline__ void sts(float *b, int e, df64 v) {
+  b[e] = v.hi;
+  b[e + kGfB * kGfB] = v.lo;
+}
+__device__ __forceinline__ df64 ldt(const float *b, int e) { return df64{b[e], b[e + kGfPlaneT]}; }
+__device__ __forceinline__ void stt(float *b, int e, df64 v) {
+  b[e] = v.hi;
+  b[e + kGfPlaneT] = v.lo;
+}
+// c + a b in double-float (the fused form of df64.cuh, c - (-a) b)
+__device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c) { return df_fnms_fast(df_neg(a), b, c); }
+
+// column-major packed position of block (i, j), i >= j, of an nb x nb block triangle
+__device__ __forceinline__ int blk_cm(int i, int j, int nb) { return j * nb - j * (j - 1) / 2 + (i - j); }
+// row-major packed position (output layout)
+__host__ __device__ __forceinline__ int blk_rm(int i, int j) { return i * (i + 1) / 2 + j; }
+
+}  // namespace
+
+struct GramFactorArgs {
+  const float *hpart;     // [splits][Q][Q] partial Grams (FP32, row-major)
+  long long pstride;      // elements between consecutive partials
+  int splits, Q, nb;
+  double scale;           // 1 / |H|
+  double damping;         // eta^t
+  float *Lout;            // [nb (nb + 1) / 2][kBlkF] blocks of the factor (row-major packed)
+  double *dbg_h;          // [Q][Q] the damped h actually factored (FP64), or null
+  int *ok;                // 1: factored; 0: every rung of the ladder failed
+  int *status;
+};
+
+__global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_constant__ GramFactorArgs a) {
+  cg::cluster_group cluster = cg::this_cluster();
+  const int cta = (int)cluster.block_rank();
+  extern __shared__ __align__(16) float gfs[];
+  float *slots = gfs;                                     // [kGfSlots][2][32 * 32]
+  float *panelT = slots + kGfSlots * kGfSlotF;            // [kGfMaxNb][2][32 * 33], block (i, k) transposed
+  float *W = panelT + (size_t)kGfMaxNb * 2 * kGfPlaneT;   // [2][32 * 32] U^{-1}, then L_kk^{-1} (owner)
+  float *linvT = W + kGfSlotF;                            // [2][32 * 33] L_kk^{-1} transposed (every CTA)
+  __shared__ int blk_i[kGfSlots], blk_j[kGfSlots], nslots_s, fail_s;
+  __shared__ double diag_s[kGridScaledMaxQ];
+  const int tid = threadIdx.x, cc = tid & 31, r0 = tid >> 5;
+  const int nb = a.nb, Q = a.Q, nblk = nb * (nb + 1) / 2;
+  if (tid == 0) {
+    int n = 0;
+    for (int idx = cta; idx < nblk; idx += kGfC) {
+      int j = 0;
+      while (blk_cm(nb - 1, j, nb) < idx) ++j;   // last position of column j >= idx
+      blk_i[n] = j + (idx - blk_cm(j, j, nb));
+      blk_j[n] = j;
+      ++n;
+    }
+    nslots_s = n;
+  }
+  __syncthreads();
+  const int nslots = nslots_s;
+  const df64 scale = df_from_double(a.scale);
+
+  // h(ga, gb) as double-float: the partials summed in increasing order
+  auto gram_entry = [&](int ga, int gb) {
+    df64 v = df64{0.f, 0.f};
+    for (int z = 0; z < a.splits; ++z) v = df_add(v, df64{__ldcg(a.hpart + z * a.pstride + (long long)ga * Q + gb), 0.f});
+    return df_mul(v, scale);
+  };
+
+  bool ok = false;
+  double extra = 0.0, tr = -1.0;
+  for (int m = -1; m < 7 && !ok; ++m) {
+    if (m >= 0) {
+      if (tr < 0.0) {   // trace of the undamped h, same fixed order in every CTA
+        for (int q = tid; q < Q; q += kGfT) diag_s[q] = df_to_double(gram_entry(q, q));
+        __syncthreads();
+        if (tid == 0) {
+          double s = 0.0;
+          for (int q = 0; q < Q; ++q) s += diag_s[q];
+          diag_s[0] = s;
+        }
+        __syncthreads();
+        tr = diag_s[0];
+        __syncthreads();
+      }
+      extra = 1e-12 * tr / Q * pow(10.0, (double)m);
+    }
+    const df64 damp = df_from_double(a.damping + extra);
+    // load: this CTA's blocks of the damped h (identity on the padding)
+    for (int s = 0; s < nslots; ++s) {
+      float *A = slots + s * kGfSlotF;
+      for (int e = tid; e < kGfB * kGfB; e += kGfT) {
+        const int ga = blk_i[s] * kGfB + (e >> 5), gb = blk_j[s] * kGfB + (e & 31);
+        df64 v;
+        if (ga < Q && gb < Q) {
+          v = gram_entry(ga, gb);
+          if (ga == gb) v = df_add(v, damp);
+        } else {
+          v = df64{ga == gb ? 1.f : 0.f, 0.f};
+        }
+        sts(A, e, v);
+      }
+    }
+    if (tid == 0) fail_s = 0;
+    cluster.sync();
+    bool failed = false;
+    for (int k = 0; k < nb && !failed; ++k) {
+      const int own_kk = blk_cm(k, k, nb) % kGfC;
+      // (1) diagonal block: LDL^T with the row operations applied to an identity
+      if (cta == own_kk) {
+        float *A = slots + (blk_cm(k, k, nb) / kGfC) * kGfSlotF;
+        for (int e = tid; e < kGfB * kGfB; e += kGfT) sts(W, e, df64{(e >> 5) == (e & 31) ? 1.f : 0.f, 0.f});
+        __syncthreads();
+        bool bad = false;
+        for (int j = 0; j < kGfB; ++j) {
+          const df64 d = lds(A, j * kGfB + j);
+          if (!(d.hi > 0.f) || !isfinite(d.hi)) {
+            bad = true;
+            break;
+          }
+          const df64 invd = df_rcp(d);
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = r0 + 16 * h;
+            if (r > j) {
+              const df64 l = df_mul(lds(A, r * kGfB + j), invd);
+              if (cc > j) sts(A, r * kGfB + cc, df_fnms_fast(l, lds(A, j * kGfB + cc), lds(A, r * kGfB + cc)));
+              else sts(W, r * kGfB + cc, df_fnms_fast(l, lds(W, j * kGfB + cc), lds(W, r * kGfB + cc)));
+            }
+          }
+          __syncthreads();
+        }
+        if (!bad) {   // L_kk^{-1} = D^{-1/2} U^{-1}, in place in W
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = r0 + 16 * h;
+            const df64 qr = df_rcp(df_sqrt(lds(A, r * kGfB + r)));
+            const df64 v = cc <= r ? df_mul(lds(W, r * kGfB + cc), qr) : df64{0.f, 0.f};
+            sts(W, r * kGfB + cc, v);
+            float *o = a.Lout + (size_t)blk_rm(k, k) * kBlkF;
+            o[r * kGfB + cc] = v.hi;
+            o[kGfB * kGfB + r * kGfB + cc] = v.lo;
+            o[2 * kGfB * kGfB + cc * kGfB + r] = v.hi;
+            o[3 * kGfB * kGfB + cc * kGfB + r] = v.lo;
+          }
+        }
+        if (tid == 0) fail_s = bad ? 1 : 0;
+      }
+      cluster.sync();
+      failed = *cluster.map_shared_rank(&fail_s, own_kk) != 0;
+      if (failed) break;
+      // (2) panel: L_ik = A_ik L_kk^{-T} for the blocks (i, k), i > k, held here
+      bool have_panel = false;
+      for (int s = 0; s < nslots; ++s) have_panel |= (blk_j[s] == k && blk_i[s] > k);
+      if (have_panel) {
+        const float *Wk = cluster.map_shared_rank(W, own_kk);
+        for (int e = tid; e < kGfB * kGfB; e += kGfT) {
+          const int r = e >> 5, c = e & 31;
+          stt(linvT, c * kGfPitchT + r, lds(Wk, e));
+        }
+        __syncthreads();
+        for (int s = 0; s < nslots; ++s) {
+          if (blk_j[s] != k || blk_i[s] <= k) continue;
+          float *A = slots + s * kGfSlotF;
+          df64 out[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = r0 + 16 * h;
+            df64 acc = df64{0.f, 0.f};
+            for (int t = 0; t <= cc; ++t) acc = df_fma(lds(A, r * kGfB + t), ldt(linvT, t * kGfPitchT + cc), acc);
+            out[h] = acc;
+          }
+          __syncthreads();
+          float *o = a.Lout + (size_t)blk_rm(blk_i[s], k) * kBlkF;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int r = r0 + 16 * h;
+            sts(A, r * kGfB + cc, out[h]);
+            o[r * kGfB + cc] = out[h].hi;
+            o[kGfB * kGfB + r * kGfB + cc] = out[h].lo;
+            o[2 * kGfB * kGfB + cc * kGfB + r] = out[h].hi;
+            o[3 * kGfB * kGfB + cc * kGfB + r] = out[h].lo;
+          }
+        }
+      }
+      cluster.sync();
+      // (3) trailing update A_ij -= L_ik L_jk^T, k < j <= i, of the blocks held here
+      unsigned need = 0u;
+      for (int s = 0; s < nslots; ++s)
+        if (blk_j[s] > k) need |= (1u << blk_i[s]) | (1u << blk_j[s]);
+      for (int i = k + 1; i < nb; ++i) {
+        if (!((need >> i) & 1u)) continue;
+        const int pos = blk_cm(i, k, nb);
+        const float *src = cluster.map_shared_rank(slots + (pos / kGfC) * kGfSlotF, pos % kGfC);
+        float *dst = panelT + (size_t)i * 2 * kGfPlaneT;
+        for (int e = tid; e < kGfB * kGfB; e += kGfT) stt(dst, (e & 31) * kGfPitchT + (e >> 5), lds(src, e));
+      }
+      __syncthreads();
+      for (int s = 0; s < nslots; ++s) {
+        if (blk_j[s] <= k) continue;
+        float *A = slots + s * kGfSlotF;
+        const float *Pi = panelT + (size_t)blk_i[s] * 2 * kGfPlaneT;
+        const float *Pj = panelT + (size_t)blk_j[s] * 2 * kGfPlaneT;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int r = r0 + 16 * h;
+          df64 acc = lds(A, r * kGfB + cc);
+#pragma unroll 8
+          for (int t = 0; t < kGfB; ++t) acc = df_fnms_fast(ldt(Pi, t * kGfPitchT + r), ldt(Pj, t * kGfPitchT + cc), acc);
+          sts(A, r * kGfB + cc, acc);
+        }
+      }
+      // the panel staging and the blocks are read again only after the next
+      // step's first cluster barrier
+      __syncthreads();
+    }
+    ok = !failed;
+    cluster.sync();   // every CTA done with the others' shared memory before a restart reloads it
+  }
+  if (cta == 0 && tid == 0) {
+    *a.ok = ok ? 1 : 0;
+    if (!ok) latch_status(a.status, kStatusNumeric);
+  }
+  if (ok && a.dbg_h) {   // the damped h that was factored, for the record
+    const double dtot = a.damping + extra;
+    for (long long e = (long long)cta * kGfT + tid; e < (long long)Q * Q; e += (long long)kGfC * kGfT) {
+      const int ga = (int)(e / Q), gb = (int)(e % Q);
+      a.dbg_h[e] = df_to_double(gram_entry(ga, gb)) + (ga == gb ? dtot : 0.0);
+    }
+  }
+}
+
+// ---- direction, step rule and update ---------------------------------------
+struct ScaledApplyArgs {
+  const float *gpart;     // [splits][In][Q] partial gradients
+  long long cstride;
+  int splits, In, Q, nb;
+  const float *Lblk;      // blocks written by grid_gram_factor_kernel
+  const int *ok;
+  int rule;
+  float alpha, eta, b;
+  double eps;
+  float *G, *acc;
+  float *dbg_g, *dbg_p;
+  int *status;
+};
+
+constexpr int kApRows = 8;   // rows of g per CTA (one warp each)
+
+__global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const __grid_constant__ ScaledApplyArgs a) {
+  if (!*a.ok) return;   // no factor: the status is latched, G_n stays as it is
+  extern __shared__ __align__(16) float aps[];
+  const int nb = a.nb, Q = a.Q, Qp = nb * kGfB;
+  float(*stage)[2 * kGfB * kGfB] = reinterpret_cast<float(*)[2 * kGfB * kGfB]>(aps);   // [2] plane pairs (hi, lo)
+  df64 *vecb = reinterpret_cast<df64 *>(aps + 2 * 2 * kGfB * kGfB);                     // [kApRows][Qp]: -g, u, p
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  df64 *vrow = vecb + (size_t)warp * Qp;
+#define vec_w(i) vrow[i]
+  const int row = blockIdx.x * kApRows + warp;
+  const bool live = row < a.In;
+  // -g of this warp's row (the plain update's fixed-order sum of the partials)
+  for (int q = lane; q < Qp; q += 32) {
+    float g = 0.f;
+    if (live && q < Q)
+      for (int z = 0; z < a.splits; ++z) g += __ldcg(a.gpart + z * a.cstride + (long long)row * Q + q);
+    vec_w(q) = df64{-g, 0.f};
+    if (live && q < Q && a.dbg_g) a.dbg_g[(long long)row * Q + q] = g;
+  }
+  // the sequence of staged blocks: forward (b, m < b) as C^T then (b, b) as
+  // L_bb^{-T}; backward (m > b, b) as C then (b, b) as L_bb^{-1}
+  const int nfw = nb * (nb + 1) / 2, S = 2 * nfw;
+  auto stage_src = [&](int s) -> const float * {
+    int bi, bj, tr;
+    if (s < nfw) {   // forward: block row b, m = 0..b
+      int b = 0;
+      while ((b + 1) * (b + 2) / 2 <= s) ++b;
+      bi = b;
+      bj = s - b * (b + 1) / 2;
+      tr = 1;
+    } else {         // backward: block column b = nb-1..0, m = nb-1..b
+      int u = s - nfw, b = nb - 1;
+      while (u >= nb - b) {
+        u -= nb - b;
+        --b;
+      }
+      bi = nb - 1 - u;
+      bj = b;
+      tr = 0;
+    }
+    return a.Lblk + (size_t)blk_rm(bi, bj) * kBlkF + (tr ? 2 * kGfB * kGfB : 0);
+  };
+  auto issue = [&](int s) {
+    const float *src = stage_src(s);
+    float *dst = stage[s & 1];
+    for (int e = tid; e < 2 * kGfB * kGfB / 4; e += 32 * kApRows) cp_async16(dst + 4 * e, src + 4 * e);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  issue(0);
+  if (S > 1) issue(1);
+  __syncwarp();
+  df64 acc = df64{0.f, 0.f};
+  int s = 0;
+  auto wait_stage = [&]() {
+    if (s + 1 < S) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+  };
+  auto release = [&]() {
+    __syncthreads();
+    if (s + 2 < S) issue(s + 2);
+    ++s;
+  };
+  // forward: u L^T = -g
+  for (int b = 0; b < nb; ++b) {
+    acc = vec_w(b * kGfB + lane);
+    for (int m = 0; m < b; ++m) {   // acc[c] -= sum_t C_bm[c][t] u_m[t]
+      wait_stage();
+      const float *X = stage[s & 1];
+#pragma unroll 8
+      for (int t = 0; t < kGfB; ++t)
+        acc = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t), acc);
+      release();
+    }
+    vec_w(b * kGfB + lane) = acc;
+    __syncwarp();
+    wait_stage();
+    {   // u_b[c] = sum_{t <= c} L_bb^{-1}[c][t] r[t]
+      const float *X = stage[s & 1];
+      df64 u = df64{0.f, 0.f};
+      for (int t = 0; t <= lane; ++t)
+        u = df_fma(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(b * kGfB + t), u);
+      __syncwarp();
+      vec_w(b * kGfB + lane) = u;
+      __syncwarp();
+    }
+    release();
+  }
+  // backward: p L = u
+  for (int b = nb - 1; b >= 0; --b) {
+    acc = vec_w(b * kGfB + lane);
+    for (int m = nb - 1; m > b; --m) {   // acc[c] -= sum_t C_mb[t][c] p_m[t]
+      wait_stage();
+      const float *X = stage[s & 1];
+#pragma unroll 8
+      for (int t = 0; t < kGfB; ++t)
+        acc = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t), acc);
+      release();
+    }
+    vec_w(b * kGfB + lane) = acc;
+    __syncwarp();
+    wait_stage();
+    {   // p_b[c] = sum_{t >= c} L_bb^{-1}[t][c] s[t]
+      const float *X = stage[s & 1];
+      df64 p = df64{0.f, 0.f};
+      for (int t = lane; t < kGfB; ++t)
+        p = df_fma(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(b * kGfB + t), p);
+      __syncwarp();
+      vec_w(b * kGfB + lane) = p;
+      __syncwarp();
+    }
+    release();
+  }
+  if (!live) return;
+  // step rule and update (as the plain update kernel, with this p)
+  for (int q = lane; q < Q; q += 32) {
+    const df64 pd = vec_w(q);
+    const float p = pd.hi + pd.lo;
+    const long long e = (long long)row * Q + q;
+    float d;
+    if (a.rule == 0) {
+      d = a.alpha * p;
+    } else {
+      const float sacc = __ldcg(a.acc + e) + p * p;
+      a.acc[e] = sacc;
+      const float base = a.b + sacc;
+      d = !(base > 0.f) ? 0.f
+                        : ((a.eps == 0.0) ? a.eta / sqrtf(base) : a.eta * powf(base, (float)(-(0.5 + a.eps)))) * p;
+    }
+    const float nv = __ldcg(a.G + e) + d;
+    if (!isfinite(nv)) latch_status(a.status, kStatusNumeric);
+    a.G[e] = nv;
+    if (a.dbg_p) a.dbg_p[e] = p;
+  }
+}
+
+#undef vec_w
+
+// ---- host side ----------------------------------------------------------------
+size_t grid_scaled_factor_floats(int Q) {
+  const int nb = (Q + kGfB - 1) / kGfB;
+  return (size_t)(nb * (nb + 1) / 2) * kBlkF;
+}
+
+cudaError_t grid_scaled_prepare() {
+  const int smem = (int)(kGfSmemFloats * sizeof(float));
+  cudaError_t e = cudaFuncSetAttribute(grid_gram_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(grid_gram_factor_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return e;
+}
+
+cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
+  const int nb = (s.Q + kGfB - 1) / kGfB;
+  if (s.Q < 1 || s.Q > kGridScaledMaxQ) return cudaErrorInvalidValue;
+  {
+    GramFactorArgs fa = {};
+    fa.hpart = s.hpart;
+    fa.pstride = s.hstride;
+    fa.splits = s.hsplits;
+    fa.Q = s.Q;
+    fa.nb = nb;
+    fa.scale = s.hscale;
+    fa.damping = s.damping;
+    fa.Lout = s.Lfac;
+    fa.dbg_h = s.dbg_h;
+    fa.ok = s.ok;
+    fa.status = s.status;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kGfC, 1, 1);
+    cfg.blockDim = dim3(kGfT, 1, 1);
+    cfg.dynamicSmemBytes = kGfSmemFloats * sizeof(float);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kGfC;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, grid_gram_factor_kernel, fa);
+    if (e != cudaSuccess) return e;
+  }
+  ScaledApplyArgs aa = {};
+  aa.gpart = s.gpart;
+  aa.cstride = s.gstride;
+  aa.splits = s.gsplits;
+  aa.In = s.In;
+  aa.Q = s.Q;
+  aa.nb = nb;
+  aa.Lblk = s.Lfac;
+  aa.ok = s.ok;
+  aa.rule = s.rule;
+  aa.alpha = s.alpha;
+  aa.eta = s.eta;
+  aa.b = s.b;
+  aa.eps = s.eps;
+  aa.G = s.G;
+  aa.acc = s.acc;
+  aa.dbg_g = s.dbg_g;
+  aa.dbg_p = s.dbg_p;
+  aa.status = s.status;
+  const size_t smem = (size_t)2 * 2 * kGfB * kGfB * sizeof(float) + (size_t)kApRows * nb * kGfB * sizeof(df64);
+  grid_scaled_apply_kernel<<<(s.In + kApRows - 1) / kApRows, 32 * kApRows, smem, st>>>(aa);
+  return cudaGetLastError();
+}
+
+}  // namespace trsgd

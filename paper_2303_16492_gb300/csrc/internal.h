@@ -28,6 +28,10 @@ struct ProbDesc {
                                   // the Q reciprocal pivots, in the Gram-solve scalar (8 bytes each)
   const int *ext_idx;             // optimal distribution: this step's indices [J][N] and p_F [J]
   const double *ext_pf;
+  // polls of a bounded mbarrier wait before it latches TRSGD_ETIMEOUT (0: the
+  // default 2^22; negative: none, every first try times out); the timed-out
+  // operation is then drained by a second wait of the default length
+  long long wait_limit;
   // recording of intermediates (problem 0 only)
   int dbg;
   int *dbg_n, *dbg_idx;
@@ -91,28 +95,76 @@ struct OptBuffers {
 // map (boxes of 64 K-elements, 128-byte swizzle); Z^T's box height depends on
 // the mode, so it has one map per mode.
 struct GridPath {
-  int np;                  // BF16 pieces per operand (1 or 3)
+  int np;                  // BF16 pieces per operand of the residual and gradient GEMMs (1 or 3)
+  int npz;                 // pieces of Z kept (3 for the scaled variant: its Gram is formed from three)
+  int scaled;              // scaled variant (Sec. 3.3)
+  int JH;                  // |H| of an independent Hessian batch (0: H = F)
   int nt_res;              // N tile of the residual GEMM
-  int Jp, Ip, Qp, QTp;     // padded J (256), I (128), Q (64)
+  int Jp, Ip, Qp, QTp;     // padded J (256; the larger of |F| and |H|), I (128), Q (64)
   long long ldg, ldz, ldzt, lde;
   int max_splits;
-  size_t gpart_elems;
+  int sms;                 // SMs of the device (split-K sizing)
+  size_t gpart_elems, hpart_elems;
   int x_bf16;              // mode-major copies of X in BF16 (else FP32)
   float w;                 // uniform sampling: every weight 1/|F|
   __nv_bfloat16 *Gp[3], *Zp[3], *ZTp[3], *Ep[3];
-  float *gpart;
+  float *gpart;            // [splits][I_n][Q] partial gradients
+  float *hpart;            // [splits][Q][Q] partial Grams (scaled)
+  float *Lfac;             // blocks of the Gram factor (scaled)
+  int *fac_ok;             // 1 when the last factorisation succeeded
   long long *col;
   CUtensorMap tmG[3], tmZ[3], tmE[3];
-  CUtensorMap tmZT[8][3];
+  CUtensorMap tmZT[8][3];  // Z^T as the B operand (box height of mode n's N tile)
+  CUtensorMap tmZTa[3];    // Z^T as the A operand of the Gram (box height 128)
 };
 
+// Largest R_n R_{n+1} of the scaled variant on the whole-GPU path.
+constexpr int kGridScaledMaxQ = 512;
+
+// Arguments of the scaled variant's factorisation and direction (grid_scaled.cu).
+struct GridScaledArgs {
+  const float *hpart;      // partial Grams [hsplits][Q][Q]
+  long long hstride;
+  int hsplits;
+  const float *gpart;      // partial gradients [gsplits][In][Q]
+  long long gstride;
+  int gsplits;
+  int In, Q;
+  double hscale;           // 1 / |H|
+  double damping;
+  float *Lfac;
+  int *ok;
+  int rule;
+  float alpha, eta, b;
+  double eps;
+  float *G, *acc;
+  float *dbg_g, *dbg_p;
+  double *dbg_h;
+  int *status;
+};
+size_t grid_scaled_factor_floats(int Q);
+cudaError_t grid_scaled_prepare();
+cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st);
+
 // kernel launchers (defined in the .cu files)
-void grid_layout(const int *I, const int *R, int N, int J, int np, GridPath &g);
+void grid_layout(const int *I, const int *R, int N, int J, int np, int scaled, int JH, GridPath &g);
 cudaError_t grid_tensor_maps(const int *R, int N, GridPath &g);
 int grid_nt_max(int np);
 int grid_ntiles(int Q, int np, int &NT);
 cudaError_t grid_prepare_gemm();
 cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long long t, int rec, cudaStream_t s);
+// Split-K unit of mode n (samples per partial, a multiple of 256) and the
+// number of partials a sample range [j0, j1) produces.
+long long grid_split_unit(const GridPath &g, const ProbDesc &D, int n, long long nsamples);
+// The two halves of an iteration: the partial gradient (and partial Gram)
+// over the sample ranges [j0, j1) of F and [h0, h1) of H, written as one
+// FP32 partial per split unit; then the fixed-order sum of gsplits (hsplits)
+// partials, the direction, the step rule and the update of G_n.
+cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, long long t, long long j0,
+                                long long j1, long long h0, long long h1, int rec, float *gout, float *hout,
+                                cudaStream_t s);
+cudaError_t launch_grid_apply(const GridPath &g, const ProbDesc &D, int n, const float *gparts, int gsplits,
+                              const float *hparts, int hsplits, int rec, cudaStream_t s);
 cudaError_t launch_optimal_sampling(int core_dtype, int x_dtype, int N, int n, const int *I, const int *R,
                                     const void *const *cores, const void *xmode, long long ldx,
                                     unsigned long long seed, long long t, int J, OptBuffers &b, cudaStream_t s);

@@ -294,6 +294,9 @@ __global__ void __launch_bounds__(kMaxThreads)
   const int *I = D.I, *R = D.R;
   const bool scaled = SC && D.variant == 1;   // SC false: the scaled variant is compiled out
   const bool rec = D.dbg && pidx == 0;
+  // first try of every bounded wait; a timeout is latched, then the operation
+  // is drained by a second wait of the default length
+  const long long wlim = D.wait_limit == 0 ? kWaitLimit : (D.wait_limit < 0 ? 0 : D.wait_limit);
   int ru = R[0];   // the common rank when all ranks are equal, else 0
   for (int k = 1; k < N; ++k)
     if (R[k] != ru) ru = 0;
@@ -599,7 +602,10 @@ __global__ void __launch_bounds__(kMaxThreads)
         }
         umma_commit(bar_mma);
       }
-      if (!mbar_wait_bounded(bar_mma, mphase, kWaitLimit)) latch_status(D.status, kStatusTimeout);
+      if (!mbar_wait_bounded(bar_mma, mphase, wlim)) {
+        latch_status(D.status, kStatusTimeout);
+        mbar_wait_bounded(bar_mma, mphase, kWaitLimit);
+      }
       mphase ^= 1u;
       tc_fence_after();
       const int warp = tid >> 5, lane = tid & 31, qd = warp & 3, wg = warp >> 2, nwg = NT >> 7;
@@ -652,7 +658,10 @@ __global__ void __launch_bounds__(kMaxThreads)
         }
         umma_commit(bar_mma);
       }
-      if (!mbar_wait_bounded(bar_mma, mphase, kWaitLimit)) latch_status(D.status, kStatusTimeout);
+      if (!mbar_wait_bounded(bar_mma, mphase, wlim)) {
+        latch_status(D.status, kStatusTimeout);
+        mbar_wait_bounded(bar_mma, mphase, kWaitLimit);
+      }
       mphase ^= 1u;
       tc_fence_after();
       for (int c16 = wg; c16 < NP / 16; c16 += nwg) {   // NP: multiple of 16
@@ -809,7 +818,7 @@ __global__ void __launch_bounds__(kMaxThreads)
     // the fibers (A3)
     cp_async_wait_all();
     if (fiber_tma && jb > 0) {
-      if (!mbar_wait_bounded(bar, phase, kWaitLimit)) {
+      if (!mbar_wait_bounded(bar, phase, wlim)) {
         latch_status(D.status, kStatusTimeout);
         mbar_wait_bounded(bar, phase, kWaitLimit);
       }

@@ -101,7 +101,11 @@ def test_unsupported_shapes_reported(lib):
     assert _init(lib, c)[0] == _abi.EUNSUPPORTED
     c = _cfg(variant=_abi.SCALED)
     for k in range(3):
-        c.R[k] = 12                      # Q = 144 > scaled limit of the fused kernel
+        c.R[k] = 23                      # Q = 529 > the scaled limits of both paths (128, 512)
+    assert _init(lib, c)[0] == _abi.EUNSUPPORTED
+    c = _cfg(variant=_abi.SCALED, prec=_abi.FP64, x_dtype=_abi.DTYPE_F64)
+    for k in range(3):
+        c.R[k] = 12                      # Q = 144: the whole-GPU path has no FP64 mode
     assert _init(lib, c)[0] == _abi.EUNSUPPORTED
     c = _cfg(path=_abi.PATH_GRID, prec=_abi.FP64, x_dtype=_abi.DTYPE_F64)
     assert _init(lib, c)[0] == _abi.EUNSUPPORTED
@@ -123,6 +127,10 @@ def test_null_handle_calls(lib):
     assert lib.trsgd_launch_count(None) == -1
     assert lib.trsgd_tensor_pieces(None) == -1
     assert lib.trsgd_gd_step(None, 0, 0.1, 0.0) == _abi.EINVAL
+    sh = _abi.Shard()
+    assert lib.trsgd_shard_plan(None, 0, 0, 1, ctypes.byref(sh)) == _abi.EINVAL
+    assert lib.trsgd_step_partial(None, 0, ctypes.byref(sh), ctypes.c_void_p(16), None) == _abi.EINVAL
+    assert lib.trsgd_step_apply(None, 0, ctypes.c_void_p(16), 1, None, 0) == _abi.EINVAL
     lib.trsgd_destroy(None)
 
 

@@ -11,6 +11,7 @@ import pytest
 import torch
 
 from tests.gpu_helpers import Case, cuda
+from tests.gpu_helpers import api as api_mod
 
 pytestmark = [pytest.mark.gpu, cuda]
 
@@ -126,3 +127,39 @@ def test_pipelined_launch_equals_single_steps(threads, prec):
     _same(ca, cb)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,dims", [(1, [12, 9, 10, 7]), (1, [300, 20, 25]), (0, [300, 20, 25])],
+                         ids=["fp32_pieces", "fp32_bulk_fibers", "fp64_bulk_fibers"])
+def test_forced_wait_timeout_is_reported_and_drained(prec, dims):
+    """Bounded waits on the failure path: with trsgd_set_wait_limit(-1) the
+    first try of every mbarrier wait (tensor-core completion; bulk copies of
+    fibers of 1 KB or more, mode 1 of the 300-row shapes) times out at once,
+    latches TRSGD_ETIMEOUT, and a second wait of the default length drains
+    the operation, so the launch still completes: the next synchronising
+    call reports the timeout, the cores are finite and equal to those of a
+    run without the forced timeouts, and limit 0 restores normal operation."""
+    A = api_mod()
+    ranks = [3, 4, 2, 3][:len(dims)]
+    c = Case(dims, ranks, 40, seed=5, prec=prec, alpha=0.05)
+    start = [t.clone() for t in c.cores_d]
+    c.solver.close()
+    ref, ref_cores = _fresh(c, cores=start)
+    s, cores = _fresh(c, cores=start)
+    ref.run(0, 12)
+    s.set_wait_limit(-1)
+    for t in range(12):
+        s.step(t)
+    with pytest.raises(A._abi.TrsgdError) as ei:
+        s.rel_error(0)
+    assert ei.value.status == A._abi.ETIMEOUT
+    torch.cuda.synchronize()
+    for x, y in zip(cores, ref_cores):
+        assert torch.isfinite(x).all()
+    _same(cores, ref_cores)
+    s.set_wait_limit(0)
+    ref.run(12, 4)
+    s.run(12, 4)   # synchronising: no status latched any more
+    _same(cores, ref_cores)
+    ref.close()
+    s.close()

@@ -501,3 +501,55 @@ def test_optimal_distribution_fp32_draws_valid():
             assert lo - tol <= target < int(cdf[col]) + tol
             assert abs(d["pF"][j] - q[col]) <= 1e-4 * q[col]
         ob.step(case.state, case.X, case.ocfg, t)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_scaled_damping_ladder_first_rung(prec):
+    """A zero column in every slice of the core before n in the ring zeroes
+    columns of Z, so h has exact zero rows: the undamped factorisation fails
+    and the first rung of the ladder (damping 1e-12 tr(h)/Q) factors it, on
+    both sides.  The recorded h carries that damping on its diagonal."""
+    case = Case(dims=[12, 11, 10], ranks=[3, 2, 4], J=60, prec=prec, alpha=0.2, variant=ob.VARIANT_SCALED)
+    case.solver.set_debug(True)
+    t = 0
+    n = ob.draw_mode(case.ocfg.seed, t, 3)
+    k = (n + 2) % 3
+    Rk = case.ranks[k]
+    case.cores_d[k].view(case.dims[k], -1)[:, :Rk] = 0   # column 0 of every slice G_k(i)
+    case.resync()
+    rec = ob.step(case.state, case.X, case.ocfg, t)
+    case.solver.step(t)
+    d = case.debug(rec["n"])
+    h_or = rec["h"]
+    Q = h_or.shape[0]
+    zero = [q for q in range(Q) if q % case.ranks[n] == 0]
+    used = h_or[zero[0], zero[0]]
+    assert used > 0 and np.allclose(np.diag(h_or)[zero], used)
+    tr_h = np.trace(h_or) - Q * used
+    assert used == pytest.approx(1e-12 * tr_h / Q, rel=1e-10)
+    assert_close(np.diag(d["h"])[zero], np.diag(h_or)[zero], 1e-5, "damped zero pivots")
+    assert_close(d["h"], h_or, 1e-11 if prec == 0 else 2e-5, "h")
+    case.assert_cores(1e-10 if prec == 0 else 1e-4)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_scaled_zero_subchain_is_a_numerical_error(prec):
+    """Every core but G_n zero: Z = 0, h = 0, no rung of the ladder factors
+    it (the oracle raises); the kernel latches TRSGD_ENUMERIC, reported at the
+    next synchronising call, and the cores stay as they were."""
+    A = api()
+    case = Case(dims=[12, 11, 10], ranks=[3, 2, 4], J=60, prec=prec, alpha=0.2, variant=ob.VARIANT_SCALED)
+    t = 0
+    n = ob.draw_mode(case.ocfg.seed, t, 3)
+    for k, c in enumerate(case.cores_d):
+        if k != n:
+            c.zero_()
+    before = [c.clone() for c in case.cores_d]
+    with pytest.raises(ob.NumericError):
+        ob.step(ob.State.new(case.device_cores()), case.X, case.ocfg, t)
+    case.solver.step(t)
+    with pytest.raises(A._abi.TrsgdError) as ei:
+        case.solver.rel_error(0)
+    assert ei.value.status == A._abi.ENUMERIC
+    for c, b in zip(case.cores_d, before):
+        assert torch.equal(c, b)
