@@ -39,6 +39,7 @@ WORKLOAD_DESC = {
     "c5": "N=3 1000^3, R=20, ill-conditioned planted cores, noise 1e-3, |F|=4096, BF16 operands, AdaGrad, "
           "whole-GPU path",
     "c5p": "profiling size of c5: 1000x400x400, R=20, |F|=4096, BF16 operands, AdaGrad, whole-GPU path",
+    "c5ps": "profiling size of c5, scaled variant: 1000x400x400, R=20, |F|=4096, BF16 operands, AdaGrad",
 }
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16 operands, f32 accumulate"}
 UNIT = "steps/s"
@@ -51,11 +52,6 @@ def peaks():
         d = json.load(open(p))
         return d, "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
-
-
-def fp32_alu_peak_tflops(sm_mhz: float) -> float:
-    """FP32 FMA peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop x clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -131,23 +127,43 @@ def device_problem(w, device, seed_offset=0):
 # dram__bytes_read.sum + dram__bytes_write.sum per step of the c2 step kernel,
 # from one ncu capture of 200 steps (101.38 MB); a kernel changed since its
 # capture has no entry (traffic null)
-MEASURED_TRAFFIC_PER_STEP = {("c2", "step_cluster_kernel<float,float,12,3,false>"): 506913}
+MEASURED_TRAFFIC_PER_STEP = {}
 
 
 def algorithmic_per_step(w):
-    """Algorithmic bytes and flops of one iteration averaged over the modes
-    (uniform mode draw): fibers J*I_n*4 B, G_n read+write, the N-1 sampled
-    slices per sample (J*(N-1)*R^2*4 B); flops 2*J*(N-2)*R^3 (chain) +
-    2*I_n*Q*J (residual) + 2*I_n*Q*J (gradient)."""
+    """HBM bytes and flops of one iteration averaged over the modes (uniform
+    mode draw): the J sampled fibers (J I_n bytes of X), G_n read and written
+    (2 I_n Q, 4 B each) and the other N-1 cores read once (their sampled
+    slices come from them); flops 2 J (N-2) R^3 (chain) + 2 I_n Q J (residual)
+    + 2 I_n Q J (gradient)."""
     N = len(w.dims)
+    sx = 8 if w.prec == 0 else (2 if w.prec == 2 else 4)
+    sc = 8 if w.prec == 0 else 4
     by, fl = 0.0, 0.0
     for n in range(N):
         In = w.dims[n]
         Q = w.ranks[n] * w.ranks[(n + 1) % N]
         R = w.ranks[0]
-        by += w.J * In * 4 + 2 * In * Q * 4 + w.J * (N - 1) * R * R * 4
+        others = sum(w.dims[k] * w.ranks[k] * w.ranks[(k + 1) % N] for k in range(N) if k != n)
+        by += w.J * In * sx + 2 * In * Q * sc + others * sc
         fl += 2 * w.J * (N - 2) * R ** 3 + 4 * In * Q * w.J
     return by / N, fl / N
+
+
+def method_flops_per_step(w):
+    """The residual and gradient contractions of one iteration, 4 I_n Q J flop,
+    averaged over the modes."""
+    N = len(w.dims)
+    return sum(4.0 * w.dims[n] * w.ranks[n] * w.ranks[(n + 1) % N] * w.J for n in range(N)) / N
+
+
+def measured_fp32_peak():
+    """FP32 FMA flop/s of this device, measured now (trsgd_probe_peak)."""
+    try:
+        from paper_2303_16492_gb300 import api
+        return max(api.probe_peak(0, 2048) for _ in range(2))
+    except Exception:
+        return None
 
 
 def max_over_ranks(ms, device):
@@ -182,8 +198,13 @@ def run_ours(args):
     device = torch.device("cuda", local)
     w = synth.workload(args.workload)
     X, Xtrue, init = device_problem(w, device, seed_offset=rank)
-    pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=w.prec, alpha=w.alpha, rule=w.rule, eta=w.eta,
-                           seed=w.seed + 3)
+    if w.prec == 2:   # BF16-mixed workloads store X in BF16
+        X = X.to(torch.bfloat16)
+    from paper_2303_16492_gb300 import _abi
+    pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=w.prec, alpha=w.alpha, rule=w.rule,
+                           eta=w.extra.get("eta_scaled", w.eta) if w.variant else w.eta, variant=w.variant,
+                           J_H=w.JH, damping=w.damping, seed=w.seed + 3,
+                           x_dtype=_abi.DTYPE_BF16 if w.prec == 2 else None)
     stream = torch.cuda.current_stream()
     solver = api.Solver([pc], [X], [init], stream=stream)
     if args.autotune:
@@ -214,41 +235,45 @@ def run_ours(args):
     ms_per_step = ms / args.steps
 
     # roofline of the dominant kernel: the fused step kernel (the only launch in the timed
-    # region) on the cluster path, the tcgen05 GEMMs on the whole-GPU path
+    # region) on the cluster path; on the whole-GPU path the iteration's contractions
     pk, pk_kind = peaks()
     by, fl = algorithmic_per_step(w)
-    sm_mhz = pk.get("sm_max_mhz", 2070.0)
     if cluster == 0:
-        npieces = 1 if w.prec == 2 else 6
-        gemm_fl = sum(4.0 * w.dims[n] * w.ranks[n] * w.ranks[(n + 1) % len(w.dims)] * w.J
-                      for n in range(len(w.dims))) / len(w.dims) * npieces
+        Nw = len(w.dims)
+        gemm_fl = method_flops_per_step(w) + (sum(2.0 * (w.JH or w.J) * (w.ranks[n] * w.ranks[(n + 1) % Nw]) ** 2
+                                                  for n in range(Nw)) / Nw if w.variant else 0.0)
         achieved = gemm_fl / (ms_per_step * 1e-3) / 1e12
-        roofline = {"bound": "tensor", "achieved": round(achieved, 3), "peak": pk.get("bf16_tflops", 1899.3),
-                    "unit": "TFLOP/s", "frac": round(achieved / pk.get("bf16_tflops", 1899.3), 5), "traffic": None,
-                    "kernel": "grid_gemm_kernel (residual + gradient), whole iteration time",
-                    "peak_note": f"dense BF16, {pk_kind} burst", "algorithmic_flops_per_step": int(gemm_fl)}
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
+        roofline = {"bound": "tensor", "achieved": round(achieved, 3), "peak": peak,
+                    "unit": "TFLOP/s", "frac": round(achieved / peak, 5), "traffic": None,
+                    "kernel": "whole iteration (samples, tcgen05 contractions, update) over its time",
+                    "peak_note": f"dense BF16, {pk_kind} sustained (a kernel sequence inside a long run); "
+                                 "flops are the method's 4 I_n Q |F| per iteration"
+                                 + ("; FP32 runs them as 6 BF16 piece products" if w.prec == 1 else ""),
+                    "algorithmic_flops_per_step": int(gemm_fl)}
     else:
-        alu_peak = fp32_alu_peak_tflops(sm_mhz)
-        achieved_tflops = fl / (ms_per_step * 1e-3) / 1e12
         rmax = next(r for r in (4, 8, 12, 16) if r >= max(w.ranks))
         pieces = solver.tensor_pieces()
         kernel = f"step_cluster_kernel<float,float,{rmax},{pieces},false>"   # plain variant: scaled code compiled out
         # DRAM read+write per step of this kernel on this workload, from one ncu capture
-        # (a 200-step launch; the per-step figure is scaled to the timed launch)
+        # (scaled to the timed launch); null when the kernel changed since the capture
         traffic_step = MEASURED_TRAFFIC_PER_STEP.get((args.workload, kernel))
-        roofline = {"bound": "alu", "achieved": round(achieved_tflops, 4), "peak": round(alu_peak, 2),
-                    "unit": "TFLOP/s", "frac": round(achieved_tflops / alu_peak, 5),
+        achieved = by / (ms_per_step * 1e-3) / 1e9
+        peak = pk.get("hbm_gbs", 6800.0)
+        fp32_peak = measured_fp32_peak()
+        roofline = {"bound": "hbm", "achieved": round(achieved, 3), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 6),
                     "traffic": None if traffic_step is None else int(traffic_step * args.steps),
                     "traffic_per_step": traffic_step,
                     "kernel": kernel,
-                    "peak_note": f"FP32 FMA unit count x {sm_mhz:.0f} MHz (derived; {pk_kind} clock)"
-                                 + ("; the two contractions run on the tensor cores as three BF16 pieces per "
-                                    "operand, the rest of the step on the FP32 pipes" if pieces == 3 else ""),
-                    "hbm_frac": round(by / (ms_per_step * 1e-3) / 1e9 / pk.get("hbm_gbs", 6652.0), 5),
-                    # one problem occupies one cluster: its SMs' share of the same peak
-                    "sms_used": cluster,
-                    "frac_of_sms_used": round(achieved_tflops / (alu_peak * cluster / 152.0), 4),
-                    "algorithmic_bytes_per_step": int(by), "algorithmic_flops_per_step": int(fl)}
+                    "peak_note": f"HBM copy bandwidth, {pk_kind}; algorithmic bytes per step = the sampled "
+                                 "fibers + G_n read and written + the other N-1 cores read once; one problem "
+                                 f"runs on one cluster of {cluster} of the GPU's SMs, latency-bound",
+                    "algorithmic_bytes_per_step": int(by), "algorithmic_flops_per_step": int(fl),
+                    "fp32_fma": None if fp32_peak is None else {
+                        "achieved_tflops": round(fl / (ms_per_step * 1e-3) / 1e12, 4),
+                        "peak_tflops_measured": round(fp32_peak / 1e12, 2),
+                        "frac": round(fl / (ms_per_step * 1e-3) / fp32_peak, 5)}}
 
     e2e = run_e2e(args, w, solver, X, init, device) if rank == 0 and not args.no_e2e else None
     ttr = time_to_rse(args, w, device, ms_per_step) if rank == 0 and args.time_to_rse else None
@@ -562,55 +587,73 @@ def run_c3(args, device):
 
 
 def run_large(args, device, target=1e-2, check=100, max_steps=4000, timed_steps=500):
-    """The large workload (N=3, 1000^3, R=20, J=4096, AdaGrad eta=0.01) on the
-    whole-GPU path: BF16 operands, and FP32 as three BF16 pieces.  Steps/s over
-    `timed_steps` iterations, then iterations and device seconds until RSE
-    (against the noiseless tensor) <= target, checked every `check`
-    iterations (evaluations not timed); effective tensor rate = the two
-    contractions' flops (2 x 2 I Q J per iteration, times 6 piece products for
-    FP32) over the iteration time."""
+    """The large workload (N=3, 1000^3, R=20, |F|=4096, AdaGrad) on the
+    whole-GPU path as its recipe states it: the scaled variant (Sec. 3.3) with
+    the adaptive step, BF16 tensor-core contractions with X stored in BF16
+    (2 GB) against the FP32 path (X in FP32, three BF16 pieces per operand);
+    the plain direction beside it.  Steps/s and iterations / device seconds
+    until RSE (against the noiseless tensor) <= target, checked every `check`
+    iterations (evaluations not timed).  Tensor rate: the method's flops,
+    4 I_n Q |F| per iteration (plus 2 |H| Q^2 for the scaled variant's Gram),
+    over the iteration time, against the measured sustained BF16 peak."""
     import torch
 
     from paper_2303_16492_gb300 import _abi, api, synth
     w = synth.workload("c5")
     X, Xtrue, init = device_problem(w, device)
-    pk, _ = peaks()
+    Xb = X.to(torch.bfloat16)
+    pk, pk_kind = peaks()
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1700.0))
     out = {}
-    gemm_flops = 2 * 2.0 * w.dims[0] * w.ranks[0] * w.ranks[1] * w.J
-    for label, prec, npieces in (("bf16", _abi.BF16_MIXED, 1), ("fp32x3", _abi.FP32, 6)):
+    N = len(w.dims)
+    gemm_flops = method_flops_per_step(w)
+    gram_flops = sum(2.0 * w.J * (w.ranks[n] * w.ranks[(n + 1) % N]) ** 2 for n in range(N)) / N
+    for label, prec, variant in (("bf16_scaled", _abi.BF16_MIXED, 1), ("fp32_scaled", _abi.FP32, 1),
+                                 ("bf16_plain", _abi.BF16_MIXED, 0), ("fp32_plain", _abi.FP32, 0)):
+        bf = prec == _abi.BF16_MIXED
         cores = [c.clone() for c in init]
-        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=prec, x_dtype=_abi.DTYPE_F32, rule=w.rule,
-                               eta=w.eta, seed=w.seed + 3)
-        s = api.Solver([pc], [X], [cores])
+        pc = api.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=prec,
+                               x_dtype=_abi.DTYPE_BF16 if bf else _abi.DTYPE_F32, rule=w.rule,
+                               eta=w.extra.get("eta_scaled", w.eta) if variant else w.eta, variant=variant,
+                               seed=w.seed + 3)
+        s = api.Solver([pc], [Xb if bf else X], [cores])
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         ms_total, it, rse, reached = 0.0, 0, None, False
-        while it < max_steps:
+        try:
+            while it < max_steps:
+                a.record()
+                s.run(it, check)
+                b.record()
+                torch.cuda.synchronize()
+                ms_total += a.elapsed_time(b)
+                it += check
+                rse = s.rel_error(0, Xtrue)
+                if rse <= target:
+                    reached = True
+                    break
             a.record()
-            s.run(it, check)
+            s.run(it, timed_steps)
             b.record()
             torch.cuda.synchronize()
-            ms_total += a.elapsed_time(b)
-            it += check
-            rse = s.rel_error(0, Xtrue)
-            if rse <= target:
-                reached = True
-                break
-        a.record()
-        s.run(it, timed_steps)
-        b.record()
-        torch.cuda.synchronize()
+        except Exception as ex:   # a numerical failure of the run is reported, not hidden
+            out[f"c5_{label}"] = {"error": str(ex), "iterations": it}
+            s.close()
+            continue
         ms = a.elapsed_time(b) / timed_steps
         s.close()
+        fl = gemm_flops + (gram_flops if variant else 0.0)
         out[f"c5_{label}"] = {
             "steps_per_s": round(1e3 / ms, 1), "us_per_step": round(ms * 1e3, 2),
             "time_to_rse": {"target": target, "iterations": it, "reached": reached, "rse": rse,
                             "seconds": round(ms_total * 1e-3, 4)},
-            "effective_tensor_tflops": round(gemm_flops * npieces / (ms * 1e-3) / 1e12, 2),
-            "frac_of_bf16_peak": round(gemm_flops * npieces / (ms * 1e-3) / 1e12 / pk.get("bf16_tflops", 1899.3), 4)}
-    out["c5_config"] = {"dims": w.dims, "ranks": w.ranks, "J": w.J, "rule": "AdaGrad", "eta": w.eta,
-                        "path": "grid (whole GPU, tcgen05 GEMMs)", "x_storage": "bf16 copies for bf16; fp32 for fp32x3"}
-    del X, Xtrue
+            "method_tflops": round(fl / (ms * 1e-3) / 1e12, 2),
+            "frac_of_bf16_sustained": round(fl / (ms * 1e-3) / 1e12 / peak, 4)}
+    out["c5_config"] = {"dims": w.dims, "ranks": w.ranks, "J": w.J, "rule": "AdaGrad", "eta_plain": w.eta,
+                        "eta_scaled": w.extra.get("eta_scaled", w.eta), "path": "grid (whole GPU)",
+                        "x_storage": "BF16 (2 GB) for the BF16 runs; FP32 (4 GB) for the FP32 runs",
+                        "peak": f"{peak} TFLOP/s dense BF16, {pk_kind} sustained"}
+    del X, Xb, Xtrue
     return out
 
 
@@ -671,10 +714,49 @@ def run_batched(args, device, steps=2000):
     steps = reps * chunk
     rse = [s.rel_error(p, Xts[p]) for p in range(0, len(ws), 16)]
     s.close()
+    # HBM bytes of one round (every problem one iteration), as for one problem
+    round_bytes = sum(algorithmic_per_step(w)[0] for w in ws)
+    pk, pk_kind = peaks()
+    gbs = round_bytes * steps / sec / 1e9
+    # time to RSE 1e-3 (against each problem's noiseless tensor) of the batched form: fresh
+    # cores, graph replays of 250 iterations until every problem is there (evaluations untimed)
+    cores = [[c.clone() for c in cs] for cs in inits]
+    s = api.Solver(pcs, Xs, cores, stream=side)
+    s.launch_shape(*shape)
+    torch.cuda.synchronize()
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=side):
+        s.step_counter(chunk)
+    s.set_counter(0)
+    torch.cuda.synchronize()
+    done, ms_total, it, todo = [False] * len(ws), 0.0, 0, set(range(len(ws)))
+    first = [None] * len(ws)
+    while todo and it < 40 * chunk:
+        with torch.cuda.stream(side):
+            a.record(side)
+            g2.replay()
+            b.record(side)
+        torch.cuda.synchronize()
+        ms_total += a.elapsed_time(b)
+        it += chunk
+        for p in sorted(todo):
+            if s.rel_error(p, Xts[p]) <= 1e-3:
+                first[p] = it
+                todo.discard(p)
+    s.close()
     return {"c4_batched_problem_steps_per_s": round(len(ws) * steps / sec, 1),
             "c4_batched_rounds_per_s": round(steps / sec, 1), "c4_launch_shape": list(shape),
             "c4_execution": "autotuned shape; one persistent launch of 250 iterations of all problems per CUDA-graph replay",
-            "c4_rse_sample": [float(f"{r:.3e}") for r in rse]}
+            "c4_rse_sample": [float(f"{r:.3e}") for r in rse],
+            "c4_roofline": {"bound": "hbm", "achieved": round(gbs, 2), "peak": pk.get("hbm_gbs", 6800.0),
+                            "unit": "GB/s", "frac": round(gbs / pk.get("hbm_gbs", 6800.0), 5),
+                            "algorithmic_bytes_per_round": int(round_bytes),
+                            "note": f"fibers + G_n read and written + the other cores, every problem; {pk_kind} peak"},
+            "c4_time_to_rse_1e-3": {"all_reached": not todo, "iterations_all": it if not todo else None,
+                                    "device_seconds": round(ms_total * 1e-3, 4),
+                                    "reached": len(ws) - len(todo), "problems": len(ws),
+                                    "median_iterations": sorted(x for x in first if x is not None)[
+                                        (len(ws) - len(todo)) // 2] if len(ws) > len(todo) else None}}
 
 
 def cpu_baseline(args, w, budget_s=None):

@@ -187,8 +187,10 @@ trsgd_status trsgd_step_counter(trsgd_handle *h, int64_t T);
 trsgd_status trsgd_set_counter(trsgd_handle *h, int64_t t);
 
 /* RSE = ||TR(G) - X_ref||_F / ||X_ref||_F (Sec. 4) of problem `problem`,
- * reduced in FP64.  Xref_dev: NULL for the X given to init, else a tensor of
- * the problem's dims and x_dtype.  Synchronising; *out receives the value. */
+ * reduced in FP64.  Xref_dev: a tensor of the problem's dims in the cores'
+ * dtype (double for TRSGD_FP64, float otherwise), or NULL for the X given to
+ * init when that X has the cores' dtype (TRSGD_EUNSUPPORTED for a BF16 X).
+ * Synchronising; *out receives the value. */
 trsgd_status trsgd_rel_error(trsgd_handle *h, int32_t problem,
                              const void *Xref_dev, double *out);
 
@@ -320,8 +322,10 @@ trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial);
  *                       step rule and update of G_n.  Pass the ranks'
  *                       buffers gathered in rank order (an all-gather): the
  *                       zero padding leaves every sum unchanged, so the
- *                       result is bit-identical to trsgd_step(t) on one
- *                       device, and identical on every rank.  Async.
+ *                       result is bit-identical for every world size (and to
+ *                       trsgd_step(t) on one device, except where that runs
+ *                       the fused BF16 kernel, whose sums take another
+ *                       order), and identical on every rank.  Async.
  * The buffers are caller device memory of gsplits_max * gelems (per rank) or
  * world * gsplits_max * gelems (gathered) floats. */
 typedef struct {
@@ -345,7 +349,9 @@ trsgd_status trsgd_step_apply(trsgd_handle *h, int64_t t, const float *gparts_de
  * path launches per iteration: G_n's pieces, the samples, one transpose per
  * kept piece of Z, the residual, the gradient and the update; the scaled
  * variant replaces the update by the Gram, its factorisation and the
- * direction, plus the H batch's samples and transposes when J_H > 0). */
+ * direction, plus the H batch's samples and transposes when J_H > 0; BF16
+ * operands with the plain direction and R_n R_{n+1} <= 448: G_n's pieces,
+ * the samples and one fused kernel). */
 int64_t trsgd_launch_count(const trsgd_handle *h);
 
 /* One iteration of the full-gradient methods the paper compares against
@@ -372,6 +378,15 @@ trsgd_status trsgd_gd_step(trsgd_handle *h, int32_t scaled, double alpha, double
  * BF16-mixed mode, 1 = the whole-GPU path's BF16-mixed mode.  -1 for a null
  * handle.  Pure host query. */
 int32_t trsgd_tensor_pieces(const trsgd_handle *h);
+
+/* Measured arithmetic peak of one unit of the current device, for the
+ * roofline fractions of kernels that run on it.  The paper has no
+ * counterpart.  unit 0: FP32 fused multiply-add, 1: FP64 fused multiply-add.
+ * A warm-up launch, then a timed launch (CUDA events on `stream`) of 8
+ * independent FMA chains per thread, 8 CTAs of 256 threads per SM, `iters`
+ * rounds of 16 FMAs per chain; *flops_per_s receives 2 flop per FMA over the
+ * timed launch.  Synchronising. */
+trsgd_status trsgd_probe_peak(int32_t unit, int64_t iters, void *stream, double *flops_per_s);
 
 void trsgd_destroy(trsgd_handle *h);
 const char *trsgd_status_string(trsgd_status s);

@@ -105,6 +105,8 @@ _SIGNATURES = {
     "trsgd_step_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.c_int64]),
     "trsgd_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "trsgd_probe_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
+                                        ctypes.POINTER(ctypes.c_double)]),
     "trsgd_destroy": (None, [ctypes.c_void_p]),
     "trsgd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

@@ -197,6 +197,14 @@ class Solver:
             pass
 
 
+def probe_peak(unit: int, iters: int = 4096, stream=None) -> float:
+    """trsgd_probe_peak: measured flop/s of the FP32 (unit 0) or FP64 (unit 1) FMA units."""
+    out = ctypes.c_double()
+    check(_abi.lib().trsgd_probe_peak(int(unit), int(iters), _stream_ptr(stream), ctypes.byref(out)),
+          "trsgd_probe_peak")
+    return out.value
+
+
 def reconstruct(cores, dims, ranks, out=None, stream=None):
     """trsgd_reconstruct: X = TR({G_n}) as a flat device tensor (i_1 fastest)."""
     dt = cores[0].dtype

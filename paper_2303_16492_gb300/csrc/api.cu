@@ -575,6 +575,9 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
     }
     if (e == cudaSuccess) e = grid_prepare_gemm();
     if (e == cudaSuccess) e = grid_tensor_maps(Ri, c.N, g);
+    // the fused BF16 kernel for the modes it takes, its cluster size per mode
+    for (int k = 0; k < c.N; ++k)
+      g.fz_S[k] = (np == 1 && !scaled && g.x_bf16) ? grid_fused_cluster(Ii[k], Ri[k] * Ri[(k + 1) % c.N], (int)c.J) : 0;
     if (e != cudaSuccess) return fail(from_cuda(e));
   }
   h->threads = 512;
@@ -606,9 +609,7 @@ static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
       const int n = draw_mode(D.seed, t, D.N);
       cudaError_t e = launch_grid_step(h->gp, D, n, t, h->dbg ? 1 : 0, h->stream);
       if (e != cudaSuccess) return from_cuda(e);
-      // prepare, samples, transpose(s), residual, gradient, update; scaled:
-      // (H samples and transposes,) Gram, factor and direction instead of the update
-      h->launches += 4 + h->gp.npz + (h->gp.scaled ? (h->gp.JH > 0 ? 3 + h->gp.npz : 2) : 1);
+      h->launches += grid_step_kernels(h->gp, D, n);
     }
     return TRSGD_OK;
   }
@@ -669,7 +670,8 @@ trsgd_status trsgd_rel_error(trsgd_handle *h, int32_t problem, const void *Xref_
   if (!h || !out || problem < 0 || problem >= h->nprob) return TRSGD_EINVAL;
   const trsgd_config &c = h->cfg[problem];
   const ProbDesc &D = h->hdesc[problem];
-  if (c.x_dtype != TRSGD_DTYPE_F64 && c.x_dtype != TRSGD_DTYPE_F32) return TRSGD_EUNSUPPORTED;
+  // the reference is read in the cores' dtype: the caller's own X only when it has that dtype
+  if (!Xref_dev && c.x_dtype != (h->core_dtype == 0 ? TRSGD_DTYPE_F64 : TRSGD_DTYPE_F32)) return TRSGD_EUNSUPPORTED;
   const void *ref = Xref_dev ? Xref_dev : h->X[problem];
   const long long np = reconstruct_partials(h->core_dtype, c.N, D.I, D.R);
   cudaError_t e = cudaSuccess;

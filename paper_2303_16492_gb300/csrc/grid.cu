@@ -89,106 +89,120 @@ struct GridSampleArgs {
 };
 
 constexpr int kGridRmax = 32;
-constexpr int kGridWarps = 4;
-constexpr int kPld = kGridRmax + 4;   // row stride of P (multiple of 4: float4 row reads)
+constexpr int kSpc = 8;             // samples per CTA
+constexpr int kSmpThreads = 256;
 
-__global__ void __launch_bounds__(32 * kGridWarps) grid_samples_kernel(GridSampleArgs a) {
-  __shared__ __align__(16) float Pbuf[kGridWarps][2][kGridRmax][kPld];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int N = a.N, n = a.n, L = N - 1;
-  int order[kMaxOrder];
-#pragma unroll
-  for (int s = 0; s < kMaxOrder; ++s) order[s] = (s < L) ? (n + 1 + s) % N : 0;
-  if (a.rec && blockIdx.x == 0 && threadIdx.x == 0) *a.dbg_n = n;
-  const int Rn = a.R[n], Rn1 = a.R[(n + 1) % N];
-  for (int j = a.j0 + blockIdx.x * kGridWarps + warp; j < a.j1; j += gridDim.x * kGridWarps) {
-    // slice indices of the L cores in ring order, one lane per core
-    int myi = 0;
-    if (lane < L) {
-      const int k = order[lane];
-      const uint64_t u = draw_u64(a.seed, a.t, a.stream, k, (uint32_t)j);
-      myi = (int)mulhi64(u, (uint64_t)a.I[k]);
-    }
-    int idx[kMaxOrder];
-#pragma unroll
-    for (int s = 0; s < kMaxOrder; ++s) idx[s] = __shfl_sync(0xffffffffu, myi, s);
-    if (lane == 0 && a.col) {
+// pitch of the staged matrices: odd, so that a column walk and a row walk are
+// both free of bank conflicts
+__host__ __device__ inline int smp_pitch(int rmax) { return rmax | 1; }
+size_t grid_samples_smem(int rmax) { return (size_t)3 * kSpc * rmax * smp_pitch(rmax) * sizeof(float); }
+
+// n / d for n d < 2^32 as the high word of n * ceil(2^32 / d) (division by an
+// invariant integer, Granlund and Montgomery, PLDI 1994): one multiply instead
+// of a division in the per-element index arithmetic
+struct FastDiv {
+  unsigned d, m;
+  __device__ explicit FastDiv(unsigned dv) : d(dv), m(0xFFFFFFFFu / dv + 1u) {}
+  __device__ __forceinline__ unsigned div(unsigned n) const { return d == 1u ? n : __umulhi(n, m); }
+};
+
+// kSpc samples per CTA: the L = N - 1 slice indices of each sample (one
+// thread per (sample, factor) draw), its fiber column, then the subchain row
+// P = G_{n+1}(i) G_{n+2}(i) ... G_{n-1}(i) (R_{n+1} x R_n) by L - 1 products
+// of matrices staged in shared memory (one thread per output entry, the
+// inner index in increasing order), and Z(j, r + r' R_n) = P(r', r) written
+// as np BF16 pieces, row-major [j][q], zero in the padding [Q, Qp).
+__global__ void __launch_bounds__(kSmpThreads) grid_samples_kernel(GridSampleArgs a) {
+  extern __shared__ float smp[];
+  __shared__ int idx_s[kSpc][kMaxOrder];
+  const int N = a.N, n = a.n, L = N - 1, tid = threadIdx.x;
+  const int jbase = a.j0 + blockIdx.x * kSpc;
+  const int nj = min(kSpc, a.j1 - jbase);
+  if (nj <= 0) return;
+  int rmax = 1;
+  for (int k = 0; k < N; ++k) rmax = max(rmax, a.R[k]);
+  const int pt = smp_pitch(rmax), mat = rmax * pt;
+  float *P = smp, *Pn = smp + kSpc * mat, *Sg = smp + 2 * kSpc * mat;
+  for (int e = tid; e < nj * L; e += kSmpThreads) {
+    const int jl = e / L, sf = e - jl * L, k = (n + 1 + sf) % N;
+    const uint64_t u = draw_u64(a.seed, a.t, a.stream, k, (uint32_t)(jbase + jl));
+    idx_s[jl][sf] = (int)mulhi64(u, (uint64_t)a.I[k]);
+  }
+  __syncthreads();
+  if (a.col || a.rec) {
+    for (int jl = tid; jl < nj; jl += kSmpThreads) {
+      const int j = jbase + jl;
       long long col = 0, st = 1;
-      for (int s = 0; s < L; ++s) {
-        col += (long long)idx[s] * st;
-        st *= a.I[order[s]];
+      for (int sf = 0; sf < L; ++sf) {
+        const int k = (n + 1 + sf) % N;
+        col += (long long)idx_s[jl][sf] * st;
+        st *= a.I[k];
       }
-      a.col[j] = col;
+      if (a.col) a.col[j] = col;
       if (a.rec) {   // p_F in ring order (FP64), only for the record
         double pf = 1.0;
-        for (int s = 0; s < L; ++s) pf = __dmul_rn(pf, __ddiv_rn(1.0, (double)a.I[order[s]]));
+        for (int sf = 0; sf < L; ++sf) pf = __dmul_rn(pf, __ddiv_rn(1.0, (double)a.I[(n + 1 + sf) % N]));
         a.dbg_pf[j] = pf;
         for (int k = 0; k < N; ++k) a.dbg_idx[(size_t)j * N + k] = -1;
-        for (int s = 0; s < L; ++s) a.dbg_idx[(size_t)j * N + order[s]] = idx[s];
+        for (int sf = 0; sf < L; ++sf) a.dbg_idx[(size_t)j * N + (n + 1 + sf) % N] = idx_s[jl][sf];
       }
     }
-    // P = G_{n+1}(i) ... G_{n-1}(i) (R_{n+1} x R_n) in shared memory, row-major
-    float(*P)[kPld] = Pbuf[warp][0];
-    float(*Pn)[kPld] = Pbuf[warp][1];
-    {
-      const int k = order[0], Ra = a.R[k], Rb = a.R[(k + 1) % N];
-      const float *g = a.cores[k] + (size_t)idx[0] * Ra * Rb;
-      for (int e = lane; e < Ra * Rb; e += 32) P[e % Ra][e / Ra] = __ldcg(g + e);   // (a, b) at a + b Ra
+  }
+  if (a.rec && blockIdx.x == 0 && tid == 0) *a.dbg_n = n;
+  // stage slice sf of every sample as a row-major [c][b] matrix (c < R_k,
+  // b < R_{k+1}) from its column-major slice (c + b R_k): 4-byte asynchronous
+  // copies (L2), coalesced reads, all in flight together
+  auto stage = [&](int sf, float *dst) {
+    const int k = (n + 1 + sf) % N, Ra = a.R[k], Rb = a.R[(k + 1) % N], sz = Ra * Rb;
+    const FastDiv dsz((unsigned)sz), dra((unsigned)Ra);
+    for (int e = tid; e < nj * sz; e += kSmpThreads) {
+      const int jl = (int)dsz.div((unsigned)e), el = e - jl * sz, b = (int)dra.div((unsigned)el), c = el - b * Ra;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst + jl * mat + c * pt + b)),
+                   "l"(a.cores[k] + (size_t)idx_s[jl][sf] * sz + el)
+                   : "memory");
     }
-    for (int s = 1; s < L; ++s) {
-      const int k = order[s], Ra = a.R[k], Rb = a.R[(k + 1) % N];
-      const float *g = a.cores[k] + (size_t)idx[s] * Ra * Rb;
-      // lane b keeps column b of G_k(i) in registers; rows of P are read as
-      // broadcast float4 (padded with zeros past Ra)
-      float col[kGridRmax];
-#pragma unroll
-      for (int c = 0; c < kGridRmax; ++c) col[c] = (lane < Rb && c < Ra) ? __ldcg(g + c + lane * Ra) : 0.f;
-      __syncwarp();
-      for (int r = lane; r < Rn1; r += 32)
-        for (int c = Ra; c < ((Ra + 3) & ~3); ++c) P[r][c] = 0.f;
-      __syncwarp();
-      const int Ra4 = (Ra + 3) >> 2;
-      for (int r = 0; r < Rn1; ++r) {
-        const float4 *pr = reinterpret_cast<const float4 *>(P[r]);
-        float acc = 0.f;
-#pragma unroll
-        for (int c4 = 0; c4 < kGridRmax / 4; ++c4) {
-          if (c4 >= Ra4) break;
-          const float4 pv = pr[c4];
-          acc = fmaf(pv.x, col[4 * c4], acc);
-          acc = fmaf(pv.y, col[4 * c4 + 1], acc);
-          acc = fmaf(pv.z, col[4 * c4 + 2], acc);
-          acc = fmaf(pv.w, col[4 * c4 + 3], acc);
-        }
-        if (lane < Rb) Pn[r][lane] = acc;
-      }
-      __syncwarp();
-      float(*tmp)[kPld] = P;
-      P = Pn;
-      Pn = tmp;
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  stage(0, P);
+  if (L > 1) stage(1, Sg);
+  int rc = a.R[(n + 2) % N];   // columns of P
+  const int Rn1 = a.R[(n + 1) % N];
+  for (int sf = 1; sf < L; ++sf) {
+    if (sf > 1) stage(sf, Sg);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    const int k = (n + 1 + sf) % N, Rb = a.R[(k + 1) % N];
+    const FastDiv dout((unsigned)(Rn1 * Rb)), drb((unsigned)Rb);
+    for (int e = tid; e < nj * Rn1 * Rb; e += kSmpThreads) {
+      const int jl = (int)dout.div((unsigned)e), el = e - jl * (Rn1 * Rb), rp = (int)drb.div((unsigned)el),
+                b = el - rp * Rb;
+      const float *pr = P + jl * mat + rp * pt, *sc = Sg + jl * mat + b;
+      float acc = 0.f;
+      for (int c = 0; c < rc; ++c) acc = fmaf(pr[c], sc[c * pt], acc);
+      Pn[jl * mat + rp * pt + b] = acc;
     }
-    __syncwarp();
-    // Z(j, r + r' R_n) = P(r', r); zero the padding columns [Q, Qp)
-    int rp = lane / Rn, r = lane - (lane / Rn) * Rn;
-    for (int q = lane; q < a.Qp; q += 32) {
-      float v = 0.f;
-      if (q < a.Q) {
-        v = P[rp][r];
-        if (a.rec) a.dbg_z[(size_t)j * a.Q + q] = v;
-      }
-      if (a.np == 1) {
-        a.Z[0][(size_t)j * a.ldz + q] = __float2bfloat16_rn(v);
-      } else {
-        __nv_bfloat16 p[3];
-        bf16_pieces(v, a.np, p);
-        for (int pc = 0; pc < a.np; ++pc) a.Z[pc][(size_t)j * a.ldz + q] = p[pc];
-      }
-      r += 32;
-      while (r >= Rn) {
-        r -= Rn;
-        ++rp;
-      }
+    __syncthreads();
+    float *tmp = P;
+    P = Pn;
+    Pn = tmp;
+    rc = Rb;
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");   // L = 1: the only slice
+  __syncthreads();
+  // Z(j, r + r' R_n) = P(r', r), as pieces; padding columns [Q, Qp) zero
+  const int Rn = a.R[n];
+  const FastDiv dqp((unsigned)a.Qp), drn((unsigned)Rn);
+  for (int e = tid; e < nj * a.Qp; e += kSmpThreads) {
+    const int jl = (int)dqp.div((unsigned)e), q = e - jl * a.Qp, j = jbase + jl;
+    float v = 0.f;
+    if (q < a.Q) {
+      const int rp = (int)drn.div((unsigned)q);
+      v = P[jl * mat + rp * pt + (q - rp * Rn)];
+      if (a.rec) a.dbg_z[(size_t)j * a.Q + q] = v;
     }
+    __nv_bfloat16 pc[3];
+    bf16_pieces(v, a.np, pc);
+    for (int p = 0; p < a.np; ++p) a.Z[p][(size_t)j * a.ldz + q] = pc[p];
   }
 }
 
@@ -578,7 +592,12 @@ static int grid_stages(int npa, int npb, int NT) {
 }
 
 cudaError_t grid_prepare_gemm() {
-  return cudaFuncSetAttribute(grid_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  cudaError_t e = cudaFuncSetAttribute(grid_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(grid_samples_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)grid_samples_smem(kGridRmax));
+  if (e == cudaSuccess) e = grid_fused_prepare();
+  return e;
 }
 
 // Split-K unit of a contraction over nsamples samples with `tiles` output
@@ -612,7 +631,7 @@ static int nsplits(long long j0, long long j1, long long unit) { return (int)((j
 // Z (and Z^T) of the samples [j0, j1) on Philox stream `stream`; fiber
 // columns only for the F batch
 static cudaError_t launch_samples(const GridPath &g, const ProbDesc &D, int n, long long t, long long j0,
-                                  long long j1, int stream, int rec, cudaStream_t s) {
+                                  long long j1, int stream, int rec, cudaStream_t s, bool transpose = true) {
   const int N = D.N, Q = D.R[n] * D.R[(n + 1) % N];
   const int Qp = (Q + 63) / 64 * 64;
   GridSampleArgs sa = {};
@@ -640,10 +659,12 @@ static cudaError_t launch_samples(const GridPath &g, const ProbDesc &D, int n, l
   sa.dbg_pf = D.dbg_pf;
   sa.dbg_z = static_cast<float *>(D.dbg_z);
   sa.dbg_n = D.dbg_n;
-  const int blocks = (int)std::max<long long>(1, std::min<long long>((j1 - j0 + kGridWarps - 1) / kGridWarps,
-                                                                     8 * (long long)g.sms));
-  grid_samples_kernel<<<blocks, 32 * kGridWarps, 0, s>>>(sa);
+  int rmax = 1;
+  for (int k = 0; k < N; ++k) rmax = std::max(rmax, D.R[k]);
+  const int blocks = (int)((j1 - j0 + kSpc - 1) / kSpc);
+  grid_samples_kernel<<<blocks, kSmpThreads, grid_samples_smem(rmax), s>>>(sa);
   cudaError_t e = cudaGetLastError();
+  if (!transpose) return e;
   // Z^T for the gradient's K-major B operand (and both Gram operands)
   for (int p = 0; p < g.npz && e == cudaSuccess; ++p) {
     dim3 grid((unsigned)(((j1 + 63) / 64 * 64 - j0 + 31) / 32), (Q + 31) / 32);
@@ -694,9 +715,9 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
   const long long unit = grid_split_unit(g, D, n, D.J);
   if (j0 < 0 || j1 > D.J || j0 > j1 || (j0 % unit) != 0 || ((j1 % unit) != 0 && j1 != D.J))
     return cudaErrorInvalidValue;
-  if (j1 == j0) return cudaSuccess;
+  const bool fpart = j1 > j0;   // a rank may hold no sample of F but some of H
   // 1. operand pieces of G_n
-  {
+  if (fpart) {
     const long long total = (long long)Ip * Qp;
     const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
     grid_prepare_kernel<<<blocks, 256, 0, s>>>(static_cast<const float *>(D.cores[n]), In, Q, Ip, Qp, g.ldg, np,
@@ -704,10 +725,10 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // 2. samples of F and Z (and Z^T)
-  if ((e = launch_samples(g, D, n, t, j0, j1, kStreamF, rec, s)) != cudaSuccess) return e;
+  if (fpart && (e = launch_samples(g, D, n, t, j0, j1, kStreamF, rec, s)) != cudaSuccess) return e;
   const int maxord = np == 1 ? 0 : 2;
   // 3. residual: E = G_n Z^T - X_S (M = Ip, N = the samples of the range, K = Qp), weighted, as pieces
-  {
+  if (fpart) {
     GridGemmArgs ga = {};
     for (int p = 0; p < 3; ++p) ga.E[p] = g.Ep[p];
     for (int p = 0; p < np; ++p) {
@@ -745,7 +766,7 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   // 4. partial gradients: (E D) Z over the units of the range (M = Ip, N = Q, K = samples)
-  {
+  if (fpart) {
     int NT = 0;
     const int ntile = gemm_ntiles(g, Q, NT);
     GridGemmArgs ga = {};
@@ -783,7 +804,7 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
         if ((e = launch_samples(g, D, n, t, h0, h1, kStreamH, 0, s)) != cudaSuccess) return e;
         if ((e = launch_gram(g, Q, h0, h1, uh, n, hout, D.status, s)) != cudaSuccess) return e;
       }
-    } else if ((e = launch_gram(g, Q, j0, j1, unit, n, hout, D.status, s)) != cudaSuccess) {
+    } else if (fpart && (e = launch_gram(g, Q, j0, j1, unit, n, hout, D.status, s)) != cudaSuccess) {
       return e;
     }
   }
@@ -843,8 +864,30 @@ cudaError_t launch_grid_apply(const GridPath &g, const ProbDesc &D, int n, const
   return cudaGetLastError();
 }
 
-// one iteration t of the grid path on mode n: every sample on this GPU
+// kernels one iteration of mode n launches (the handle's launch count)
+int grid_step_kernels(const GridPath &g, const ProbDesc &D, int n) {
+  if (g.fz_S[n] > 0) return 3;   // G_n's pieces, the samples, the fused kernel
+  // prepare, samples, transposes, residual, gradient, update; scaled: (H samples
+  // and transposes,) Gram, factor and direction instead of the update
+  return 4 + g.npz + (g.scaled ? (g.JH > 0 ? 3 + g.npz : 2) : 1);
+}
+
+// one iteration t of the grid path on mode n: every sample on this GPU.  BF16
+// operands, plain direction, Q <= 448: G_n's pieces, the samples and one fused
+// kernel (residual, gradient, cluster sum, update); otherwise partial + apply.
 cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long long t, int rec, cudaStream_t s) {
+  const int S = g.fz_S[n];
+  if (S > 0) {
+    const int In = D.I[n], Q = D.R[n] * D.R[(n + 1) % D.N];
+    const int Ip = (In + 127) / 128 * 128, Qp = (Q + 63) / 64 * 64;
+    const long long total = (long long)Ip * Qp;
+    grid_prepare_kernel<<<(int)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(
+        static_cast<const float *>(D.cores[n]), In, Q, Ip, Qp, g.ldg, 1, g.Gp[0], g.Gp[1], g.Gp[2]);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_samples(g, D, n, t, 0, D.J, kStreamF, rec, s, false);
+    if (e == cudaSuccess) e = launch_grid_fused(g.tmZc, g.tmG[0], g.gpart, D, n, g.col, g.w, S, rec, s);
+    return e;
+  }
   const long long JH = g.JH > 0 ? g.JH : D.J;
   const int gs = nsplits(0, D.J, grid_split_unit(g, D, n, D.J));
   const int hs = g.scaled ? nsplits(0, JH, grid_split_unit(g, D, n, JH)) : 0;
@@ -891,7 +934,8 @@ void grid_layout(const int *I, const int *R, int N, int J, int np, int scaled, i
   g.max_splits = 16;
   g.sms = grid_sm_count();
   // a range of samples yields at most max_splits + 1 partials (unit rounding)
-  g.gpart_elems = (size_t)(g.max_splits + 1) * Imax * Qmax;
+  // (and the fused BF16 kernel's 16 slots of rows padded to a multiple of 4 columns)
+  g.gpart_elems = std::max((size_t)(g.max_splits + 1) * Imax * Qmax, (size_t)16 * Imax * ((Qmax + 3) & ~3));
   g.hpart_elems = scaled ? (size_t)(g.max_splits + 1) * Qmax * Qmax : 0;
 }
 
@@ -926,6 +970,7 @@ cudaError_t grid_tensor_maps(const int *R, int N, GridPath &g) {
   for (int p = 0; p < g.np && e == cudaSuccess; ++p) {
     if ((e = encode_map(fn, &g.tmG[p], g.Gp[p], g.Ip, g.ldg, 128)) != cudaSuccess) break;
     if ((e = encode_map(fn, &g.tmZ[p], g.Zp[p], g.Jp, g.ldz, g.nt_res)) != cudaSuccess) break;
+    if (p == 0 && (e = encode_map(fn, &g.tmZc, g.Zp[0], g.Jp, g.ldz, 64)) != cudaSuccess) break;
     if ((e = encode_map(fn, &g.tmE[p], g.Ep[p], g.Ip, g.lde, 128)) != cudaSuccess) break;
   }
   // Z^T: every kept piece, as the B operand of mode n's gradient (and Gram)

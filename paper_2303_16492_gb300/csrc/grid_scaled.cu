@@ -145,11 +145,29 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
     // load: this CTA's blocks of the damped h (identity on the padding)
     for (int s = 0; s < nslots; ++s) {
       float *A = slots + s * kGfSlotF;
-      for (int e = tid; e < kGfB * kGfB; e += kGfT) {
+      // the two entries of this thread: every partial loaded before the sums
+      float part[2][16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = tid + h * kGfT;
+        const int ga = blk_i[s] * kGfB + (e >> 5), gb = blk_j[s] * kGfB + (e & 31);
+#pragma unroll
+        for (int z = 0; z < 16; ++z)
+          part[h][z] = (z < a.splits && ga < Q && gb < Q) ? __ldcg(a.hpart + z * a.pstride + (long long)ga * Q + gb) : 0.f;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int e = tid + h * kGfT;
         const int ga = blk_i[s] * kGfB + (e >> 5), gb = blk_j[s] * kGfB + (e & 31);
         df64 v;
         if (ga < Q && gb < Q) {
-          v = gram_entry(ga, gb);
+          v = df64{0.f, 0.f};
+#pragma unroll
+          for (int z = 0; z < 16; ++z)
+            if (z < a.splits) v = df_add(v, df64{part[h][z], 0.f});
+          for (int z = 16; z < a.splits; ++z)
+            v = df_add(v, df64{__ldcg(a.hpart + z * a.pstride + (long long)ga * Q + gb), 0.f});
+          v = df_mul(v, scale);
           if (ga == gb) v = df_add(v, damp);
         } else {
           v = df64{ga == gb ? 1.f : 0.f, 0.f};
@@ -222,9 +240,12 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
             const int r = r0 + 16 * h;
-            df64 acc = df64{0.f, 0.f};
-            for (int t = 0; t <= cc; ++t) acc = df_fma(lds(A, r * kGfB + t), ldt(linvT, t * kGfPitchT + cc), acc);
-            out[h] = acc;
+            // four independent partial sums (t mod 4): four chains in flight
+            df64 acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 8
+            for (int t = 0; t < kGfB; ++t)
+              if (t <= cc) acc[t & 3] = df_fma(lds(A, r * kGfB + t), ldt(linvT, t * kGfPitchT + cc), acc[t & 3]);
+            out[h] = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
           }
           __syncthreads();
           float *o = a.Lout + (size_t)blk_rm(blk_i[s], k) * kBlkF;
@@ -260,10 +281,11 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int r = r0 + 16 * h;
-          df64 acc = lds(A, r * kGfB + cc);
+          df64 acc[4] = {lds(A, r * kGfB + cc), {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll 8
-          for (int t = 0; t < kGfB; ++t) acc = df_fnms_fast(ldt(Pi, t * kGfPitchT + r), ldt(Pj, t * kGfPitchT + cc), acc);
-          sts(A, r * kGfB + cc, acc);
+          for (int t = 0; t < kGfB; ++t)
+            acc[t & 3] = df_fnms_fast(ldt(Pi, t * kGfPitchT + r), ldt(Pj, t * kGfPitchT + cc), acc[t & 3]);
+          sts(A, r * kGfB + cc, df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3])));
         }
       }
       // the panel staging and the blocks are read again only after the next
@@ -354,7 +376,6 @@ __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const _
   issue(0);
   if (S > 1) issue(1);
   __syncwarp();
-  df64 acc = df64{0.f, 0.f};
   int s = 0;
   auto wait_stage = [&]() {
     if (s + 1 < S) asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -366,25 +387,36 @@ __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const _
     if (s + 2 < S) issue(s + 2);
     ++s;
   };
+  // four independent partial sums per lane (t mod 4): four dependency chains in flight
+  df64 pa[4];
+  auto reset = [&](df64 first) {
+    pa[0] = first;
+    pa[1] = pa[2] = pa[3] = df64{0.f, 0.f};
+  };
+  auto total = [&]() { return df_add(df_add(pa[0], pa[1]), df_add(pa[2], pa[3])); };
   // forward: u L^T = -g
   for (int b = 0; b < nb; ++b) {
-    acc = vec_w(b * kGfB + lane);
+    reset(vec_w(b * kGfB + lane));
     for (int m = 0; m < b; ++m) {   // acc[c] -= sum_t C_bm[c][t] u_m[t]
       wait_stage();
       const float *X = stage[s & 1];
 #pragma unroll 8
       for (int t = 0; t < kGfB; ++t)
-        acc = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t), acc);
+        pa[t & 3] = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t),
+                                 pa[t & 3]);
       release();
     }
-    vec_w(b * kGfB + lane) = acc;
+    vec_w(b * kGfB + lane) = total();
     __syncwarp();
     wait_stage();
     {   // u_b[c] = sum_{t <= c} L_bb^{-1}[c][t] r[t]
       const float *X = stage[s & 1];
-      df64 u = df64{0.f, 0.f};
-      for (int t = 0; t <= lane; ++t)
-        u = df_fma(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(b * kGfB + t), u);
+      reset(df64{0.f, 0.f});
+#pragma unroll 8
+      for (int t = 0; t < kGfB; ++t)
+        if (t <= lane)
+          pa[t & 3] = df_fma(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(b * kGfB + t), pa[t & 3]);
+      const df64 u = total();
       __syncwarp();
       vec_w(b * kGfB + lane) = u;
       __syncwarp();
@@ -393,23 +425,27 @@ __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const _
   }
   // backward: p L = u
   for (int b = nb - 1; b >= 0; --b) {
-    acc = vec_w(b * kGfB + lane);
+    reset(vec_w(b * kGfB + lane));
     for (int m = nb - 1; m > b; --m) {   // acc[c] -= sum_t C_mb[t][c] p_m[t]
       wait_stage();
       const float *X = stage[s & 1];
 #pragma unroll 8
       for (int t = 0; t < kGfB; ++t)
-        acc = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t), acc);
+        pa[t & 3] = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t),
+                                 pa[t & 3]);
       release();
     }
-    vec_w(b * kGfB + lane) = acc;
+    vec_w(b * kGfB + lane) = total();
     __syncwarp();
     wait_stage();
     {   // p_b[c] = sum_{t >= c} L_bb^{-1}[t][c] s[t]
       const float *X = stage[s & 1];
-      df64 p = df64{0.f, 0.f};
-      for (int t = lane; t < kGfB; ++t)
-        p = df_fma(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(b * kGfB + t), p);
+      reset(df64{0.f, 0.f});
+#pragma unroll 8
+      for (int t = 0; t < kGfB; ++t)
+        if (t >= lane)
+          pa[t & 3] = df_fma(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(b * kGfB + t), pa[t & 3]);
+      const df64 p = total();
       __syncwarp();
       vec_w(b * kGfB + lane) = p;
       __syncwarp();

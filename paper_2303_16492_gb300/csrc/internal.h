@@ -116,7 +116,17 @@ struct GridPath {
   CUtensorMap tmG[3], tmZ[3], tmE[3];
   CUtensorMap tmZT[8][3];  // Z^T as the B operand (box height of mode n's N tile)
   CUtensorMap tmZTa[3];    // Z^T as the A operand of the Gram (box height 128)
+  CUtensorMap tmZc;        // Z (first piece) in boxes of 64 samples (fused BF16 kernel)
+  int fz_S[8];             // cluster size of the fused BF16 kernel per mode (0: not used)
 };
+
+// Fused BF16 iteration body (grid_fused.cu): cluster size for a mode (0: not
+// applicable), set-up and launch.
+int grid_fused_cluster(int In, int Q, int J);
+int grid_step_kernels(const GridPath &g, const ProbDesc &D, int n);
+cudaError_t grid_fused_prepare();
+cudaError_t launch_grid_fused(const CUtensorMap &tmZ, const CUtensorMap &tmG, float *gpart, const ProbDesc &D,
+                              int n, const long long *col, float w, int S, int rec, cudaStream_t st);
 
 // Largest R_n R_{n+1} of the scaled variant on the whole-GPU path.
 constexpr int kGridScaledMaxQ = 512;

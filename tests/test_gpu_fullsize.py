@@ -154,6 +154,92 @@ def test_large_size_grid_path_steps(bf16):
     s.close()
 
 
+@pytest.mark.parametrize("bf16", [False, True], ids=["fp32x3", "bf16_x_stored_bf16"])
+def test_large_size_scaled_steps(bf16):
+    """The large workload as its recipe states it: the scaled variant (Sec.
+    3.3, Q = R^2 = 400) with AdaGrad on the whole-GPU path, X stored in BF16
+    (2 GB) for the BF16 run.  Two full-size iterations against the oracle:
+    indices bit-exact; Z, E, g element by element; h from three BF16 pieces
+    of Z (FP32 accuracy in both modes) within 2e-5; the direction against an
+    FP64 Cholesky solve of the device's own h and g (1e-6: the double-float
+    factorisation and solves), and against the oracle's direction within the
+    direction's FP32/BF16 bound amplified by cond(h); the core update."""
+    from paper_2303_16492_gb300 import synth
+    A = api()
+    w = synth.workload("c5")
+    eta = w.extra.get("eta_scaled", w.eta)
+    planted = synth.planted_cores(w)
+    P = to_oracle_cores(planted, w.ranks)
+    rng = np.random.default_rng(0)
+    ent = [tr.tr_entry(P, [int(rng.integers(0, d)) for d in w.dims]) for _ in range(2000)]
+    sigma = w.noise_rel * float(np.sqrt(np.mean(np.square(ent))))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(w.seed + 1)
+    numel = int(np.prod(w.dims))
+    noise_d = torch.randn(numel, generator=gen, device="cuda", dtype=torch.float32)
+    lazy = LazyTensor(P, w.dims, lambda pos: noise_d[torch.from_numpy(pos).cuda()].double().cpu().numpy(), sigma)
+    if bf16:   # the oracle's fibers rounded as the stored X is (FP32, then BF16)
+        class _Rounded:
+            shape, ndim = lazy.shape, lazy.ndim
+
+            def __getitem__(self, key):
+                f = torch.from_numpy(lazy[key].astype(np.float32))
+                return f.to(torch.bfloat16).double().numpy()
+        Xo = _Rounded()
+    else:
+        Xo = lazy
+    planted_d = [torch.from_numpy(G).to("cuda", torch.float32) for G in planted]
+    Xd = A.reconstruct(planted_d, w.dims, w.ranks)
+    Xd.add_(noise_d, alpha=sigma)
+    init = synth.initial_cores(w, float(torch.linalg.vector_norm(Xd.double()) ** 2))
+    init = [G.astype(np.float32) for G in init]
+    if bf16:
+        Xd = Xd.to(torch.bfloat16)
+    cores_d = [torch.from_numpy(G).cuda() for G in init]
+    pc = A.ProblemConfig(dims=w.dims, ranks=w.ranks, J=w.J, prec=A._abi.BF16_MIXED if bf16 else A._abi.FP32,
+                         x_dtype=A._abi.DTYPE_BF16 if bf16 else A._abi.DTYPE_F32, rule=w.rule, eta=eta,
+                         variant=1, seed=w.seed + 3)
+    s = A.Solver([pc], [Xd], [cores_d])
+    assert s.launch_shape() == (0, 256)
+    s.set_debug(True)
+    st = ob.State.new(to_oracle_cores([G.astype(np.float64) for G in init], w.ranks))
+    cfg = ob.Config(J=w.J, seed=w.seed + 3, rule=w.rule, eta=eta, variant=1)
+    tol_e, tol_g = (1e-2, 2e-2) if bf16 else (2e-5, 2e-5)
+    N, J, Q = 3, w.J, w.ranks[0] * w.ranks[1]
+    for t in range(2):
+        for k in range(N):
+            st.cores[k] = tr.fold2(cores_d[k].double().cpu().numpy(), w.ranks[k], w.ranks[(k + 1) % N])
+            acc = np.empty(w.dims[k] * Q, dtype=np.float32)
+            s.adagrad_state(0, k, acc)
+            st.acc[k] = acc.reshape(w.dims[k], Q).astype(np.float64)
+        before = [cores_d[k].double().cpu().numpy() for k in range(N)]
+        rec = ob.step(st, Xo, cfg, t)
+        s.step(t)
+        n, In = rec["n"], w.dims[rec["n"]]
+        assert int(s.get_debug(A._abi.DBG_MODE, np.int32, 1)[0]) == n
+        np.testing.assert_array_equal(s.get_debug(A._abi.DBG_IDX, np.int32, J * N).reshape(J, N), rec["idx"])
+        assert_close(s.get_debug(A._abi.DBG_Z, np.float32, J * Q).reshape(J, Q), rec["Z"], 2e-5, "Z")
+        assert_close(s.get_debug(A._abi.DBG_E, np.float32, J * In).reshape(J, In).T, rec["E"], tol_e, "E")
+        g_dev = s.get_debug(A._abi.DBG_G, np.float32, In * Q).reshape(In, Q).astype(np.float64)
+        assert_close(g_dev, rec["g"], tol_g, "g")
+        h_dev = s.get_debug(A._abi.DBG_H, np.float64, Q * Q).reshape(Q, Q)
+        assert_close(h_dev, rec["h"], 2e-5, "h")
+        p_dev = s.get_debug(A._abi.DBG_P, np.float32, In * Q).reshape(In, Q)
+        L = np.linalg.cholesky(h_dev)
+        assert_close(p_dev, -np.linalg.solve(L.T, np.linalg.solve(L, g_dev.T)).T, 1e-6, "p vs FP64 solve")
+        kappa = np.linalg.cond(rec["h"])
+        tol_p = tol_g + 2e-7 * kappa
+        assert_close(p_dev, rec["p"], tol_p, f"p (cond {kappa:.1e})")
+        # the update from the device's own direction (AdaGrad of Sec. 3.1's remark, FP32)
+        dev = cores_d[n].double().cpu().numpy()
+        acc = np.empty(In * Q, dtype=np.float32)
+        s.adagrad_state(0, n, acc)
+        A32 = acc.reshape(In, Q).astype(np.float64)
+        want = before[n] + np.where(A32 > 0, eta / np.sqrt(np.maximum(A32, 1e-300)), 0.0) * p_dev
+        assert_close(dev - before[n], want - before[n], 1e-5, "update from the device's p")
+    s.close()
+
+
 def _problem(A, name):
     """A named workload from the synth module: device X by the library's
     reconstruction plus seeded device noise (noise_rel of the rms of X_true,

@@ -28,6 +28,21 @@ def _pair(bf16, **cfg):
     return A, A.Solver([pc], [case.Xd], [ca]), ca, A.Solver([pc], [case.Xd], [cb]), cb
 
 
+def _sharded_step(sh, t, world):
+    """One iteration as `world` ranks would run it, emulated one rank after
+    the other: each rank's partials into its slot of the gathered buffer,
+    then the apply over all of them."""
+    plans = [sh.shard_plan(t, r, world) for r in range(world)]
+    g = torch.empty(world * plans[0].gsplits_max * plans[0].gelems, device="cuda")
+    h = torch.empty(world * plans[0].hsplits_max * plans[0].helems, device="cuda") if plans[0].helems else None
+    for r, p in enumerate(plans):
+        gs = g[r * p.gsplits_max * p.gelems:(r + 1) * p.gsplits_max * p.gelems]
+        hs = h[r * p.hsplits_max * p.helems:(r + 1) * p.hsplits_max * p.helems] if h is not None else None
+        sh.step_partial(t, p, gs, hs)
+    sh.step_apply(t, g, world * plans[0].gsplits_max, h, world * plans[0].hsplits_max if h is not None else 0)
+    return plans
+
+
 @pytest.mark.parametrize("world", [2, 3, 8])
 @pytest.mark.parametrize("cfg", [dict(), dict(variant=ob.VARIANT_SCALED, damping=1e-3),
                                  dict(variant=ob.VARIANT_SCALED, J_H=700, damping=1e-3),
@@ -35,10 +50,17 @@ def _pair(bf16, **cfg):
                          ids=["plain", "scaled", "scaled_H", "adagrad"])
 @pytest.mark.parametrize("bf16", [False, True], ids=["fp32x3", "bf16"])
 def test_sharded_steps_equal_single_device_steps(world, cfg, bf16):
+    """Against trsgd_step where it runs the same kernels (FP32 pieces, the
+    scaled variant), and against the one-rank plan where trsgd_step takes the
+    fused BF16 kernel (plain direction), whose sums run in another order."""
     from paper_2303_16492_gb300.shard import unit_ranges
     A, ref, ref_cores, sh, sh_cores = _pair(bf16, **cfg)
+    fused = bf16 and cfg.get("variant", 0) == 0
     for t in range(4):
-        ref.step(t)
+        if fused:
+            _sharded_step(ref, t, 1)
+        else:
+            ref.step(t)
         plans = [sh.shard_plan(t, r, world) for r in range(world)]
         # the plan follows the documented dealing rule and covers every sample once
         for r, p in enumerate(plans):
@@ -48,13 +70,7 @@ def test_sharded_steps_equal_single_device_steps(world, cfg, bf16):
         assert all(plans[r].j1 == plans[r + 1].j0 for r in range(world - 1))
         if world == 8:
             assert any(p.gsplits == 0 for p in plans)   # a rank without samples
-        g = torch.empty(world * plans[0].gsplits_max * plans[0].gelems, device="cuda")
-        h = torch.empty(world * plans[0].hsplits_max * plans[0].helems, device="cuda") if plans[0].helems else None
-        for r, p in enumerate(plans):   # each rank's partials into its slot of the gathered buffer
-            gs = g[r * p.gsplits_max * p.gelems:(r + 1) * p.gsplits_max * p.gelems]
-            hs = h[r * p.hsplits_max * p.helems:(r + 1) * p.hsplits_max * p.helems] if h is not None else None
-            sh.step_partial(t, p, gs, hs)
-        sh.step_apply(t, g, world * plans[0].gsplits_max, h, world * plans[0].hsplits_max if h is not None else 0)
+        _sharded_step(sh, t, world)
         torch.cuda.synchronize()
         for a, b in zip(sh_cores, ref_cores):
             assert torch.equal(a, b), t
