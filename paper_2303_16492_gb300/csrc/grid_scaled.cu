@@ -324,13 +324,14 @@ struct ScaledApplyArgs {
 };
 
 constexpr int kApRows = 8;   // rows of g per CTA (one warp each)
+constexpr int kApDepth = 6;  // staged blocks in flight: a stage's arithmetic is far shorter than an L2 round trip
 
 __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const __grid_constant__ ScaledApplyArgs a) {
   if (!*a.ok) return;   // no factor: the status is latched, G_n stays as it is
   extern __shared__ __align__(16) float aps[];
   const int nb = a.nb, Q = a.Q, Qp = nb * kGfB;
-  float(*stage)[2 * kGfB * kGfB] = reinterpret_cast<float(*)[2 * kGfB * kGfB]>(aps);   // [2] plane pairs (hi, lo)
-  df64 *vecb = reinterpret_cast<df64 *>(aps + 2 * 2 * kGfB * kGfB);                     // [kApRows][Qp]: -g, u, p
+  float(*stage)[2 * kGfB * kGfB] = reinterpret_cast<float(*)[2 * kGfB * kGfB]>(aps);   // ring of plane pairs (hi, lo)
+  df64 *vecb = reinterpret_cast<df64 *>(aps + kApDepth * 2 * kGfB * kGfB);              // [kApRows][Qp]: -g, u, p
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   df64 *vrow = vecb + (size_t)warp * Qp;
 #define vec_w(i) vrow[i]
@@ -367,24 +368,26 @@ __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const _
     }
     return a.Lblk + (size_t)blk_rm(bi, bj) * kBlkF + (tr ? 2 * kGfB * kGfB : 0);
   };
+  // one commit group per stage slot (empty past the end), so that "all but the
+  // newest kApDepth - 1 groups complete" always means "stage s arrived"
   auto issue = [&](int s) {
-    const float *src = stage_src(s);
-    float *dst = stage[s & 1];
-    for (int e = tid; e < 2 * kGfB * kGfB / 4; e += 32 * kApRows) cp_async16(dst + 4 * e, src + 4 * e);
+    if (s < S) {
+      const float *src = stage_src(s);
+      float *dst = stage[s % kApDepth];
+      for (int e = tid; e < 2 * kGfB * kGfB / 4; e += 32 * kApRows) cp_async16(dst + 4 * e, src + 4 * e);
+    }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  issue(0);
-  if (S > 1) issue(1);
+  for (int k = 0; k < kApDepth; ++k) issue(k);
   __syncwarp();
   int s = 0;
   auto wait_stage = [&]() {
-    if (s + 1 < S) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 0;" ::: "memory");
+    asm volatile("cp.async.wait_group %0;" ::"n"(kApDepth - 1) : "memory");
     __syncthreads();
   };
   auto release = [&]() {
     __syncthreads();
-    if (s + 2 < S) issue(s + 2);
+    issue(s + kApDepth);
     ++s;
   };
   // four independent partial sums per lane (t mod 4): four dependency chains in flight
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const _
     reset(vec_w(b * kGfB + lane));
     for (int m = 0; m < b; ++m) {   // acc[c] -= sum_t C_bm[c][t] u_m[t]
       wait_stage();
-      const float *X = stage[s & 1];
+      const float *X = stage[s % kApDepth];
 #pragma unroll 8
       for (int t = 0; t < kGfB; ++t)
         pa[t & 3] = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t),
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const _
     __syncwarp();
     wait_stage();
     {   // u_b[c] = sum_{t <= c} L_bb^{-1}[c][t] r[t]
-      const float *X = stage[s & 1];
+      const float *X = stage[s % kApDepth];
       reset(df64{0.f, 0.f});
 #pragma unroll 8
       for (int t = 0; t < kGfB; ++t)
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const _
     reset(vec_w(b * kGfB + lane));
     for (int m = nb - 1; m > b; --m) {   // acc[c] -= sum_t C_mb[t][c] p_m[t]
       wait_stage();
-      const float *X = stage[s & 1];
+      const float *X = stage[s % kApDepth];
 #pragma unroll 8
       for (int t = 0; t < kGfB; ++t)
         pa[t & 3] = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t),
@@ -439,7 +442,7 @@ __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const _
     __syncwarp();
     wait_stage();
     {   // p_b[c] = sum_{t >= c} L_bb^{-1}[t][c] s[t]
-      const float *X = stage[s & 1];
+      const float *X = stage[s % kApDepth];
       reset(df64{0.f, 0.f});
 #pragma unroll 8
       for (int t = 0; t < kGfB; ++t)
@@ -487,6 +490,10 @@ cudaError_t grid_scaled_prepare() {
   const int smem = (int)(kGfSmemFloats * sizeof(float));
   cudaError_t e = cudaFuncSetAttribute(grid_gram_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(grid_gram_factor_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(grid_scaled_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)kApDepth * 2 * kGfB * kGfB * sizeof(float) +
+                                   (size_t)kApRows * kGridScaledMaxQ * sizeof(df64)));
   return e;
 }
 
@@ -540,7 +547,7 @@ cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
   aa.dbg_g = s.dbg_g;
   aa.dbg_p = s.dbg_p;
   aa.status = s.status;
-  const size_t smem = (size_t)2 * 2 * kGfB * kGfB * sizeof(float) + (size_t)kApRows * nb * kGfB * sizeof(df64);
+  const size_t smem = (size_t)kApDepth * 2 * kGfB * kGfB * sizeof(float) + (size_t)kApRows * nb * kGfB * sizeof(df64);
   grid_scaled_apply_kernel<<<(s.In + kApRows - 1) / kApRows, 32 * kApRows, smem, st>>>(aa);
   return cudaGetLastError();
 }
