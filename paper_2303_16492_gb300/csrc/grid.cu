@@ -89,40 +89,50 @@ struct GridSampleArgs {
 };
 
 constexpr int kGridRmax = 32;
-constexpr int kSpc = 8;             // samples per CTA
-constexpr int kSmpThreads = 256;
+constexpr int kSpc = 8;             // samples per CTA, one warp each
+constexpr int kSmpThreads = 32 * kSpc;
 
-// pitch of the staged matrices: odd, so that a column walk and a row walk are
-// both free of bank conflicts
+// odd pitch of a staged slice column: lane b reads column b, so a step along
+// the column is free of bank conflicts across the warp
 __host__ __device__ inline int smp_pitch(int rmax) { return rmax | 1; }
-size_t grid_samples_smem(int rmax) { return (size_t)3 * kSpc * rmax * smp_pitch(rmax) * sizeof(float); }
+// row pitch of a subchain row P: a multiple of 4 (rows read as float4)
+__host__ __device__ inline int smp_pld(int rmax) { return (rmax + 3) & ~3; }
+// two staging buffers (this factor, the next) of kSpc slices, and two P
+// buffers per warp
+size_t grid_samples_smem(int rmax) {
+  return ((size_t)2 * kSpc * rmax * smp_pitch(rmax) + (size_t)2 * kSpc * rmax * smp_pld(rmax)) * sizeof(float);
+}
 
 // n / d for n d < 2^32 as the high word of n * ceil(2^32 / d) (division by an
-// invariant integer, Granlund and Montgomery, PLDI 1994): one multiply instead
-// of a division in the per-element index arithmetic
+// invariant integer, Granlund and Montgomery, PLDI 1994)
 struct FastDiv {
   unsigned d, m;
   __device__ explicit FastDiv(unsigned dv) : d(dv), m(0xFFFFFFFFu / dv + 1u) {}
   __device__ __forceinline__ unsigned div(unsigned n) const { return d == 1u ? n : __umulhi(n, m); }
 };
 
-// kSpc samples per CTA: the L = N - 1 slice indices of each sample (one
-// thread per (sample, factor) draw), its fiber column, then the subchain row
-// P = G_{n+1}(i) G_{n+2}(i) ... G_{n-1}(i) (R_{n+1} x R_n) by L - 1 products
-// of matrices staged in shared memory (one thread per output entry, the
-// inner index in increasing order), and Z(j, r + r' R_n) = P(r', r) written
-// as np BF16 pieces, row-major [j][q], zero in the padding [Q, Qp).
+// kSpc samples per CTA, one warp per sample: the L = N - 1 slice indices of
+// each sample (one thread per (sample, factor) draw) and its fiber column;
+// the slices of every sample staged by asynchronous copies, factor by factor
+// (the next factor's copies in flight while this one is multiplied), each
+// slice column-major at an odd pitch; the subchain row
+// P = G_{n+1}(i) G_{n+2}(i) ... G_{n-1}(i) (R_{n+1} x R_n) by L - 1 products in
+// which lane b keeps column b of the factor in registers and reads the rows
+// of P as float4 broadcasts (the inner index in increasing order); then
+// Z(j, r + r' R_n) = P(r', r) as np BF16 pieces, row-major [j][q], zero in the
+// padding [Q, Qp).
 __global__ void __launch_bounds__(kSmpThreads) grid_samples_kernel(GridSampleArgs a) {
-  extern __shared__ float smp[];
+  extern __shared__ __align__(16) float smp[];
   __shared__ int idx_s[kSpc][kMaxOrder];
-  const int N = a.N, n = a.n, L = N - 1, tid = threadIdx.x;
+  const int N = a.N, n = a.n, L = N - 1, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int jbase = a.j0 + blockIdx.x * kSpc;
   const int nj = min(kSpc, a.j1 - jbase);
   if (nj <= 0) return;
   int rmax = 1;
   for (int k = 0; k < N; ++k) rmax = max(rmax, a.R[k]);
-  const int pt = smp_pitch(rmax), mat = rmax * pt;
-  float *P = smp, *Pn = smp + kSpc * mat, *Sg = smp + 2 * kSpc * mat;
+  const int pt = smp_pitch(rmax), mat = rmax * pt, pld = smp_pld(rmax);
+  float *stg[2] = {smp, smp + kSpc * mat};
+  float *Pb = smp + 2 * kSpc * mat + (size_t)warp * 2 * rmax * pld;
   for (int e = tid; e < nj * L; e += kSmpThreads) {
     const int jl = e / L, sf = e - jl * L, k = (n + 1 + sf) % N;
     const uint64_t u = draw_u64(a.seed, a.t, a.stream, k, (uint32_t)(jbase + jl));
@@ -149,60 +159,98 @@ __global__ void __launch_bounds__(kSmpThreads) grid_samples_kernel(GridSampleArg
     }
   }
   if (a.rec && blockIdx.x == 0 && tid == 0) *a.dbg_n = n;
-  // stage slice sf of every sample as a row-major [c][b] matrix (c < R_k,
-  // b < R_{k+1}) from its column-major slice (c + b R_k): 4-byte asynchronous
-  // copies (L2), coalesced reads, all in flight together
+  // slice sf of every sample, column b at b * pt (c < R_k contiguous), from its
+  // column-major slice (c + b R_k): 4-byte asynchronous copies, coalesced reads
   auto stage = [&](int sf, float *dst) {
     const int k = (n + 1 + sf) % N, Ra = a.R[k], Rb = a.R[(k + 1) % N], sz = Ra * Rb;
     const FastDiv dsz((unsigned)sz), dra((unsigned)Ra);
     for (int e = tid; e < nj * sz; e += kSmpThreads) {
       const int jl = (int)dsz.div((unsigned)e), el = e - jl * sz, b = (int)dra.div((unsigned)el), c = el - b * Ra;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst + jl * mat + c * pt + b)),
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst + jl * mat + b * pt + c)),
                    "l"(a.cores[k] + (size_t)idx_s[jl][sf] * sz + el)
                    : "memory");
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
-  stage(0, P);
-  if (L > 1) stage(1, Sg);
+  stage(0, stg[0]);
+  stage(L > 1 ? 1 : 0, stg[1]);   // (N = 2: a repeated copy of the only factor, never read)
+  const int jl = warp;
+  const bool live = jl < nj;
+  const int Rn1 = a.R[(n + 1) % N], Rn = a.R[n];
+  float *P = Pb, *Pn = Pb + rmax * pld;
+  asm volatile("cp.async.wait_group 1;" ::: "memory");
+  __syncthreads();
   int rc = a.R[(n + 2) % N];   // columns of P
-  const int Rn1 = a.R[(n + 1) % N];
-  for (int sf = 1; sf < L; ++sf) {
-    if (sf > 1) stage(sf, Sg);
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
-    const int k = (n + 1 + sf) % N, Rb = a.R[(k + 1) % N];
-    const FastDiv dout((unsigned)(Rn1 * Rb)), drb((unsigned)Rb);
-    for (int e = tid; e < nj * Rn1 * Rb; e += kSmpThreads) {
-      const int jl = (int)dout.div((unsigned)e), el = e - jl * (Rn1 * Rb), rp = (int)drb.div((unsigned)el),
-                b = el - rp * Rb;
-      const float *pr = P + jl * mat + rp * pt, *sc = Sg + jl * mat + b;
-      float acc = 0.f;
-      for (int c = 0; c < rc; ++c) acc = fmaf(pr[c], sc[c * pt], acc);
-      Pn[jl * mat + rp * pt + b] = acc;
+  if (live) {                  // P = G_{n+1}(i), row-major [r'][b] from the staged columns
+    const float *S0 = stg[0] + jl * mat;
+    for (int e = lane; e < Rn1 * rc; e += 32) {
+      const int b = e / Rn1, rp = e - b * Rn1;
+      P[rp * pld + b] = S0[b * pt + rp];
     }
-    __syncthreads();
-    float *tmp = P;
-    P = Pn;
-    Pn = tmp;
+    for (int rp = lane; rp < Rn1; rp += 32)
+      for (int c = rc; c < ((rc + 3) & ~3); ++c) P[rp * pld + c] = 0.f;
+  }
+  for (int sf = 1; sf < L; ++sf) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();   // factor sf staged (and every warp done with the buffer the next copies go to)
+    if (sf + 1 < L) stage(sf + 1, stg[(sf + 1) & 1]);
+    const int k = (n + 1 + sf) % N, Ra = a.R[k], Rb = a.R[(k + 1) % N];
+    if (live) {
+      const float *Sc = stg[sf & 1] + jl * mat + lane * pt;
+      float col[kGridRmax];
+#pragma unroll
+      for (int c = 0; c < kGridRmax; ++c) col[c] = (lane < Rb && c < Ra) ? Sc[c] : 0.f;
+      __syncwarp();
+      const int Ra4 = (Ra + 3) >> 2;
+      for (int rp = 0; rp < Rn1; ++rp) {
+        const float4 *pr = reinterpret_cast<const float4 *>(P + rp * pld);
+        float acc = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < kGridRmax / 4; ++c4) {
+          if (c4 >= Ra4) break;
+          const float4 pv = pr[c4];
+          acc = fmaf(pv.x, col[4 * c4], acc);
+          acc = fmaf(pv.y, col[4 * c4 + 1], acc);
+          acc = fmaf(pv.z, col[4 * c4 + 2], acc);
+          acc = fmaf(pv.w, col[4 * c4 + 3], acc);
+        }
+        if (lane < Rb) Pn[rp * pld + lane] = acc;
+      }
+      for (int rp = lane; rp < Rn1; rp += 32)
+        for (int c = Rb; c < ((Rb + 3) & ~3); ++c) Pn[rp * pld + c] = 0.f;
+      __syncwarp();
+      float *tmp = P;
+      P = Pn;
+      Pn = tmp;
+    }
     rc = Rb;
   }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");   // L = 1: the only slice
-  __syncthreads();
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (!live) return;
+  __syncwarp();
   // Z(j, r + r' R_n) = P(r', r), as pieces; padding columns [Q, Qp) zero
-  const int Rn = a.R[n];
-  const FastDiv dqp((unsigned)a.Qp), drn((unsigned)Rn);
-  for (int e = tid; e < nj * a.Qp; e += kSmpThreads) {
-    const int jl = (int)dqp.div((unsigned)e), q = e - jl * a.Qp, j = jbase + jl;
+  const int j = jbase + jl;
+  int rp = lane / Rn, r = lane - rp * Rn;
+  for (int q = lane; q < a.Qp; q += 32) {
     float v = 0.f;
     if (q < a.Q) {
-      const int rp = (int)drn.div((unsigned)q);
-      v = P[jl * mat + rp * pt + (q - rp * Rn)];
+      v = P[rp * pld + r];
       if (a.rec) a.dbg_z[(size_t)j * a.Q + q] = v;
     }
-    __nv_bfloat16 pc[3];
-    bf16_pieces(v, a.np, pc);
-    for (int p = 0; p < a.np; ++p) a.Z[p][(size_t)j * a.ldz + q] = pc[p];
+    if (a.np == 1) {
+      a.Z[0][(size_t)j * a.ldz + q] = __float2bfloat16_rn(v);
+    } else {
+      __nv_bfloat16 pc[3];
+      bf16_pieces(v, 3, pc);
+      a.Z[0][(size_t)j * a.ldz + q] = pc[0];
+      a.Z[1][(size_t)j * a.ldz + q] = pc[1];
+      a.Z[2][(size_t)j * a.ldz + q] = pc[2];
+    }
+    r += 32;
+    while (r >= Rn) {
+      r -= Rn;
+      ++rp;
+    }
   }
 }
 
