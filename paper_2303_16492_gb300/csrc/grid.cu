@@ -92,15 +92,17 @@ constexpr int kGridRmax = 32;
 constexpr int kSpc = 8;             // samples per CTA, one warp each
 constexpr int kSmpThreads = 32 * kSpc;
 
-// odd pitch of a staged slice column: lane b reads column b, so a step along
-// the column is free of bank conflicts across the warp
-__host__ __device__ inline int smp_pitch(int rmax) { return rmax | 1; }
-// row pitch of a subchain row P: a multiple of 4 (rows read as float4)
-__host__ __device__ inline int smp_pld(int rmax) { return (rmax + 3) & ~3; }
-// two staging buffers (this factor, the next) of kSpc slices, and two P
-// buffers per warp
-size_t grid_samples_smem(int rmax) {
-  return ((size_t)2 * kSpc * rmax * smp_pitch(rmax) + (size_t)2 * kSpc * rmax * smp_pld(rmax)) * sizeof(float);
+// floats of one staged slice (column-major c + b R_k, as in memory), padded to
+// a multiple of 4 so that every staged slice starts on a 16-byte boundary
+__host__ __device__ inline int smp_mat(int rmax) { return (rmax * rmax + 3) & ~3; }
+constexpr int kProwPitch = kGridRmax + 1;   // a lane's row of P between two factors (odd pitch)
+// two staging buffers (this factor, the next) of kSpc slices, per warp np
+// rows of Z (BF16) assembled before the row is stored, and for chains of
+// more than two factors (N > 3) the lanes' rows of P between two factors
+__host__ __device__ inline size_t smp_pb_floats(int N) { return N > 3 ? (size_t)kSpc * 32 * kProwPitch : 0; }
+size_t grid_samples_smem(int rmax, int Qp, int np, int N) {
+  return (size_t)2 * kSpc * smp_mat(rmax) * sizeof(float) + (size_t)kSpc * np * Qp * sizeof(__nv_bfloat16) +
+         smp_pb_floats(N) * sizeof(float);
 }
 
 // n / d for n d < 2^32 as the high word of n * ceil(2^32 / d) (division by an
@@ -111,17 +113,56 @@ struct FastDiv {
   __device__ __forceinline__ unsigned div(unsigned n) const { return d == 1u ? n : __umulhi(n, m); }
 };
 
+// (row r' of P) S for a staged slice S (Ra x Rb, column-major): the lane's
+// row of P is in registers, the columns of S are read as broadcasts (16-byte
+// loads when Ra is a multiple of 4, i.e. when every column starts on a
+// 16-byte boundary), each output summed c = 0 .. Ra-1 in order and handed to
+// emit(r, value) as soon as it is formed.
+template <typename Emit>
+__device__ __forceinline__ void chain_row(const float (&prow)[kGridRmax], const float *S, int Ra, int Rb, Emit emit) {
+  if ((Ra & 3) == 0) {
+    const int Ra4 = Ra >> 2;
+#pragma unroll
+    for (int r = 0; r < kGridRmax; ++r)
+      if (r < Rb) {
+        const float4 *col = reinterpret_cast<const float4 *>(S + r * Ra);
+        float acc = 0.f;
+#pragma unroll
+        for (int c4 = 0; c4 < kGridRmax / 4; ++c4)
+          if (c4 < Ra4) {
+            const float4 sv = col[c4];
+            acc = fmaf(prow[4 * c4], sv.x, acc);
+            acc = fmaf(prow[4 * c4 + 1], sv.y, acc);
+            acc = fmaf(prow[4 * c4 + 2], sv.z, acc);
+            acc = fmaf(prow[4 * c4 + 3], sv.w, acc);
+          }
+        emit(r, acc);
+      }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kGridRmax; ++r)
+      if (r < Rb) {
+        const float *col = S + r * Ra;
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < kGridRmax; ++c)
+          if (c < Ra) acc = fmaf(prow[c], col[c], acc);
+        emit(r, acc);
+      }
+  }
+}
+
 // kSpc samples per CTA, one warp per sample: the L = N - 1 slice indices of
 // each sample (one thread per (sample, factor) draw) and its fiber column;
-// the slices of every sample staged by asynchronous copies, factor by factor
-// (the next factor's copies in flight while this one is multiplied), each
-// slice column-major at an odd pitch; the subchain row
-// P = G_{n+1}(i) G_{n+2}(i) ... G_{n-1}(i) (R_{n+1} x R_n) by L - 1 products in
-// which lane b keeps column b of the factor in registers and reads the rows
-// of P as float4 broadcasts (the inner index in increasing order); then
-// Z(j, r + r' R_n) = P(r', r) as np BF16 pieces, row-major [j][q], zero in the
-// padding [Q, Qp).
-__global__ void __launch_bounds__(kSmpThreads) grid_samples_kernel(GridSampleArgs a) {
+// the slices of every sample staged by asynchronous copies exactly as they
+// lie in memory, factor by factor (the next factor's copies in flight while
+// this one is multiplied); lane r' forms row r' of the subchain product
+// P = G_{n+1}(i) G_{n+2}(i) ... G_{n-1}(i) (R_{n+1} x R_n) in registers, by
+// L - 1 row-times-slice products (chain_row); then
+// Z(j, r + r' R_n) = P(r', r) as np BF16 pieces, assembled row by row in
+// shared memory (zero in the padding [Q, Qp)) and stored with 16-byte stores,
+// row-major [j][q].
+__global__ void __launch_bounds__(kSmpThreads, 3) grid_samples_kernel(GridSampleArgs a) {
   extern __shared__ __align__(16) float smp[];
   __shared__ int idx_s[kSpc][kMaxOrder];
   const int N = a.N, n = a.n, L = N - 1, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -130,9 +171,12 @@ __global__ void __launch_bounds__(kSmpThreads) grid_samples_kernel(GridSampleArg
   if (nj <= 0) return;
   int rmax = 1;
   for (int k = 0; k < N; ++k) rmax = max(rmax, a.R[k]);
-  const int pt = smp_pitch(rmax), mat = rmax * pt, pld = smp_pld(rmax);
+  const int mat = smp_mat(rmax), np = a.np, Qp = a.Qp, Q = a.Q;
   float *stg[2] = {smp, smp + kSpc * mat};
-  float *Pb = smp + 2 * kSpc * mat + (size_t)warp * 2 * rmax * pld;
+  __nv_bfloat16 *zrow = reinterpret_cast<__nv_bfloat16 *>(smp + 2 * kSpc * mat) + (size_t)warp * np * Qp;
+  // this lane's row of P between two factors (N > 3 only), after the Z rows
+  float *pb = reinterpret_cast<float *>(reinterpret_cast<__nv_bfloat16 *>(smp + 2 * kSpc * mat) + (size_t)kSpc * np * Qp) +
+              (size_t)(warp * 32 + lane) * kProwPitch;
   for (int e = tid; e < nj * L; e += kSmpThreads) {
     const int jl = e / L, sf = e - jl * L, k = (n + 1 + sf) % N;
     const uint64_t u = draw_u64(a.seed, a.t, a.stream, k, (uint32_t)(jbase + jl));
@@ -159,98 +203,93 @@ __global__ void __launch_bounds__(kSmpThreads) grid_samples_kernel(GridSampleArg
     }
   }
   if (a.rec && blockIdx.x == 0 && tid == 0) *a.dbg_n = n;
-  // slice sf of every sample, column b at b * pt (c < R_k contiguous), from its
-  // column-major slice (c + b R_k): 4-byte asynchronous copies, coalesced reads
+  // slice sf of every sample, as in memory: 16-byte asynchronous copies when
+  // the slices are a multiple of 4 floats long (each then starts on a 16-byte
+  // boundary), else 4-byte copies; one commit group per factor
   auto stage = [&](int sf, float *dst) {
-    const int k = (n + 1 + sf) % N, Ra = a.R[k], Rb = a.R[(k + 1) % N], sz = Ra * Rb;
-    const FastDiv dsz((unsigned)sz), dra((unsigned)Ra);
-    for (int e = tid; e < nj * sz; e += kSmpThreads) {
-      const int jl = (int)dsz.div((unsigned)e), el = e - jl * sz, b = (int)dra.div((unsigned)el), c = el - b * Ra;
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst + jl * mat + b * pt + c)),
-                   "l"(a.cores[k] + (size_t)idx_s[jl][sf] * sz + el)
-                   : "memory");
+    const int k = (n + 1 + sf) % N, sz = a.R[k] * a.R[(k + 1) % N];
+    const float *src = a.cores[k];
+    if ((sz & 3) == 0 && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+      const int q4 = sz >> 2;
+      const FastDiv dq((unsigned)q4);
+      for (int e = tid; e < nj * q4; e += kSmpThreads) {
+        const int jl = (int)dq.div((unsigned)e), el = e - jl * q4;
+        cp_async16(dst + jl * mat + 4 * el, src + (size_t)idx_s[jl][sf] * sz + 4 * el);
+      }
+    } else {
+      const FastDiv dsz((unsigned)sz);
+      for (int e = tid; e < nj * sz; e += kSmpThreads) {
+        const int jl = (int)dsz.div((unsigned)e), el = e - jl * sz;
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst + jl * mat + el)),
+                     "l"(src + (size_t)idx_s[jl][sf] * sz + el)
+                     : "memory");
+      }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   stage(0, stg[0]);
-  stage(L > 1 ? 1 : 0, stg[1]);   // (N = 2: a repeated copy of the only factor, never read)
+  if (L > 1) stage(1, stg[1]);
+  else asm volatile("cp.async.commit_group;" ::: "memory");   // an empty group keeps the count
   const int jl = warp;
   const bool live = jl < nj;
   const int Rn1 = a.R[(n + 1) % N], Rn = a.R[n];
-  float *P = Pb, *Pn = Pb + rmax * pld;
+  float prow[kGridRmax];
   asm volatile("cp.async.wait_group 1;" ::: "memory");
   __syncthreads();
-  int rc = a.R[(n + 2) % N];   // columns of P
-  if (live) {                  // P = G_{n+1}(i), row-major [r'][b] from the staged columns
+  {   // row r' = lane of the first slice G_{n+1}(i) (R_{n+1} x R_{n+2}, column-major)
+    const int rc = a.R[(n + 2) % N];
     const float *S0 = stg[0] + jl * mat;
-    for (int e = lane; e < Rn1 * rc; e += 32) {
-      const int b = e / Rn1, rp = e - b * Rn1;
-      P[rp * pld + b] = S0[b * pt + rp];
+#pragma unroll
+    for (int c = 0; c < kGridRmax; ++c) prow[c] = (live && lane < Rn1 && c < rc) ? S0[c * Rn1 + lane] : 0.f;
+  }
+  const int j = jbase + jl;
+  // Z(j, r + r' R_n) = P(r', r): lane r' fills R_n entries of the warp's row
+  // buffers as the last product forms them
+  auto emit_z = [&](int r, float v) {
+    const int q = lane * Rn + r;
+    if (a.rec) a.dbg_z[(size_t)j * Q + q] = v;
+    if (np == 1) {
+      zrow[q] = __float2bfloat16_rn(v);
+    } else {
+      __nv_bfloat16 pc[3];
+      bf16_pieces(v, 3, pc);
+      zrow[q] = pc[0];
+      zrow[Qp + q] = pc[1];
+      zrow[2 * Qp + q] = pc[2];
     }
-    for (int rp = lane; rp < Rn1; rp += 32)
-      for (int c = rc; c < ((rc + 3) & ~3); ++c) P[rp * pld + c] = 0.f;
+  };
+  if (live)
+    for (int q = Q + lane; q < Qp; q += 32)
+      for (int p = 0; p < np; ++p) zrow[p * Qp + q] = __float2bfloat16_rn(0.f);
+  if (L == 1 && live && lane < Rn1) {   // N = 2: P is the slice itself
+#pragma unroll
+    for (int r = 0; r < kGridRmax; ++r)
+      if (r < Rn) emit_z(r, prow[r]);
   }
   for (int sf = 1; sf < L; ++sf) {
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();   // factor sf staged (and every warp done with the buffer the next copies go to)
     if (sf + 1 < L) stage(sf + 1, stg[(sf + 1) & 1]);
-    const int k = (n + 1 + sf) % N, Ra = a.R[k], Rb = a.R[(k + 1) % N];
-    if (live) {
-      const float *Sc = stg[sf & 1] + jl * mat + lane * pt;
-      float col[kGridRmax];
+    if (live && lane < Rn1) {
+      const int k = (n + 1 + sf) % N, Ra = a.R[k], Rb = a.R[(k + 1) % N];
+      const float *S = stg[sf & 1] + jl * mat;
+      if (sf + 1 < L) {   // the next row of P through this lane's own buffer
+        chain_row(prow, S, Ra, Rb, [&](int r, float v) { pb[r] = v; });
 #pragma unroll
-      for (int c = 0; c < kGridRmax; ++c) col[c] = (lane < Rb && c < Ra) ? Sc[c] : 0.f;
-      __syncwarp();
-      const int Ra4 = (Ra + 3) >> 2;
-      for (int rp = 0; rp < Rn1; ++rp) {
-        const float4 *pr = reinterpret_cast<const float4 *>(P + rp * pld);
-        float acc = 0.f;
-#pragma unroll
-        for (int c4 = 0; c4 < kGridRmax / 4; ++c4) {
-          if (c4 >= Ra4) break;
-          const float4 pv = pr[c4];
-          acc = fmaf(pv.x, col[4 * c4], acc);
-          acc = fmaf(pv.y, col[4 * c4 + 1], acc);
-          acc = fmaf(pv.z, col[4 * c4 + 2], acc);
-          acc = fmaf(pv.w, col[4 * c4 + 3], acc);
-        }
-        if (lane < Rb) Pn[rp * pld + lane] = acc;
+        for (int c = 0; c < kGridRmax; ++c) prow[c] = c < Rb ? pb[c] : 0.f;
+      } else {
+        chain_row(prow, S, Ra, Rb, emit_z);
       }
-      for (int rp = lane; rp < Rn1; rp += 32)
-        for (int c = Rb; c < ((Rb + 3) & ~3); ++c) Pn[rp * pld + c] = 0.f;
-      __syncwarp();
-      float *tmp = P;
-      P = Pn;
-      Pn = tmp;
     }
-    rc = Rb;
   }
   asm volatile("cp.async.wait_group 0;" ::: "memory");
   if (!live) return;
   __syncwarp();
-  // Z(j, r + r' R_n) = P(r', r), as pieces; padding columns [Q, Qp) zero
-  const int j = jbase + jl;
-  int rp = lane / Rn, r = lane - rp * Rn;
-  for (int q = lane; q < a.Qp; q += 32) {
-    float v = 0.f;
-    if (q < a.Q) {
-      v = P[rp * pld + r];
-      if (a.rec) a.dbg_z[(size_t)j * a.Q + q] = v;
-    }
-    if (a.np == 1) {
-      a.Z[0][(size_t)j * a.ldz + q] = __float2bfloat16_rn(v);
-    } else {
-      __nv_bfloat16 pc[3];
-      bf16_pieces(v, 3, pc);
-      a.Z[0][(size_t)j * a.ldz + q] = pc[0];
-      a.Z[1][(size_t)j * a.ldz + q] = pc[1];
-      a.Z[2][(size_t)j * a.ldz + q] = pc[2];
-    }
-    r += 32;
-    while (r >= Rn) {
-      r -= Rn;
-      ++rp;
-    }
+  const int nvec = Qp / 8;   // 16-byte chunks of a row (Qp a multiple of 64)
+  for (int p = 0; p < np; ++p) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(zrow + p * Qp);
+    uint4 *dst = reinterpret_cast<uint4 *>(a.Z[p] + (size_t)j * a.ldz);
+    for (int v = lane; v < nvec; v += 32) dst[v] = src[v];
   }
 }
 
@@ -643,7 +682,7 @@ cudaError_t grid_prepare_gemm() {
   cudaError_t e = cudaFuncSetAttribute(grid_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(grid_samples_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)grid_samples_smem(kGridRmax));
+                             (int)grid_samples_smem(kGridRmax, kGridRmax * kGridRmax, 3, kMaxOrder));
   if (e == cudaSuccess) e = grid_fused_prepare();
   return e;
 }
@@ -710,7 +749,7 @@ static cudaError_t launch_samples(const GridPath &g, const ProbDesc &D, int n, l
   int rmax = 1;
   for (int k = 0; k < N; ++k) rmax = std::max(rmax, D.R[k]);
   const int blocks = (int)((j1 - j0 + kSpc - 1) / kSpc);
-  grid_samples_kernel<<<blocks, kSmpThreads, grid_samples_smem(rmax), s>>>(sa);
+  grid_samples_kernel<<<blocks, kSmpThreads, grid_samples_smem(rmax, Qp, g.npz, N), s>>>(sa);
   cudaError_t e = cudaGetLastError();
   if (!transpose) return e;
   // Z^T for the gradient's K-major B operand (and both Gram operands)
@@ -872,6 +911,7 @@ cudaError_t launch_grid_apply(const GridPath &g, const ProbDesc &D, int n, const
     sa.gsplits = gsplits;
     sa.In = In;
     sa.Q = Q;
+    sa.sms = g.sms;
     sa.hscale = 1.0 / (double)(g.JH > 0 ? g.JH : D.J);
     sa.damping = D.damping;
     sa.Lfac = g.Lfac;

@@ -23,14 +23,17 @@
 //       grown by 1e-12 tr(h)/Q * 10^m, m = 0..6 (then TRSGD_ENUMERIC).
 //       Output: every block of L below the diagonal and the inverted
 //       diagonal blocks, each stored as-is and transposed.
-//   grid_scaled_apply_kernel  one warp per row of g (8 rows per CTA, the
-//       blocks of L staged once per CTA in shared memory, double-buffered):
-//       the fixed-order sum of the partial gradients, then u L^T = -g by
-//       blocked forward substitution and p L = u by blocked backward
+//   grid_scaled_apply_kernel  one warp per row of g (the rows spread over
+//       every SM, at most 16 per CTA), the blocks of L streamed through a
+//       ring of shared-memory stages by bulk copies that one producer warp
+//       issues: the fixed-order sum of the partial gradients, then u L^T = -g
+//       by blocked forward substitution and p L = u by blocked backward
 //       substitution, each 32 x 32 diagonal step a product with the inverted
 //       block; then fixed alpha or AdaGrad and the update, exactly as the
 //       plain update kernel does with p = -g.
 #include <cooperative_groups.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "df64.cuh"
@@ -49,7 +52,12 @@ constexpr int kGfMaxNb = kGridScaledMaxQ / kGfB;           // 16 block rows
 constexpr int kGfSlots = (kGfMaxNb * (kGfMaxNb + 1) / 2 + kGfC - 1) / kGfC;   // blocks per CTA
 constexpr int kGfPitchT = 33;                              // transposed staging pitch (conflict-free)
 constexpr int kGfPlaneT = kGfB * kGfPitchT;                // floats per transposed plane
-constexpr int kBlkF = 4 * kGfB * kGfB;                     // floats per output block: X hi, X lo, X^T hi, X^T lo
+// output block: [orientation: X, X^T][hi, lo][32 rows][kLp], rows padded to
+// kLp floats so that a lane reads four consecutive entries of its row as one
+// 16-byte load without bank conflicts (8 lanes of a quarter warp: banks 4 c)
+constexpr int kLp = 36;
+constexpr int kLpl = kGfB * kLp;                           // floats per plane
+constexpr int kBlkF = 4 * kLpl;                            // floats per output block
 
 // shared memory of the factor kernel (floats): local blocks (hi plane, lo
 // plane), the transposed panel staging, the row-major L_kk^{-1} / U^{-1}
@@ -212,10 +220,10 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
             const df64 v = cc <= r ? df_mul(lds(W, r * kGfB + cc), qr) : df64{0.f, 0.f};
             sts(W, r * kGfB + cc, v);
             float *o = a.Lout + (size_t)blk_rm(k, k) * kBlkF;
-            o[r * kGfB + cc] = v.hi;
-            o[kGfB * kGfB + r * kGfB + cc] = v.lo;
-            o[2 * kGfB * kGfB + cc * kGfB + r] = v.hi;
-            o[3 * kGfB * kGfB + cc * kGfB + r] = v.lo;
+            o[r * kLp + cc] = v.hi;
+            o[kLpl + r * kLp + cc] = v.lo;
+            o[2 * kLpl + cc * kLp + r] = v.hi;
+            o[3 * kLpl + cc * kLp + r] = v.lo;
           }
         }
         if (tid == 0) fail_s = bad ? 1 : 0;
@@ -253,10 +261,10 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
           for (int h = 0; h < 2; ++h) {
             const int r = r0 + 16 * h;
             sts(A, r * kGfB + cc, out[h]);
-            o[r * kGfB + cc] = out[h].hi;
-            o[kGfB * kGfB + r * kGfB + cc] = out[h].lo;
-            o[2 * kGfB * kGfB + cc * kGfB + r] = out[h].hi;
-            o[3 * kGfB * kGfB + cc * kGfB + r] = out[h].lo;
+            o[r * kLp + cc] = out[h].hi;
+            o[kLpl + r * kLp + cc] = out[h].lo;
+            o[2 * kLpl + cc * kLp + r] = out[h].hi;
+            o[3 * kLpl + cc * kLp + r] = out[h].lo;
           }
         }
       }
@@ -313,6 +321,7 @@ struct ScaledApplyArgs {
   const float *gpart;     // [splits][In][Q] partial gradients
   long long cstride;
   int splits, In, Q, nb;
+  int rows;               // rows of g per CTA (one consumer warp each)
   const float *Lblk;      // blocks written by grid_gram_factor_kernel
   const int *ok;
   int rule;
@@ -323,142 +332,200 @@ struct ScaledApplyArgs {
   int *status;
 };
 
-constexpr int kApRows = 8;   // rows of g per CTA (one warp each)
-constexpr int kApDepth = 6;  // staged blocks in flight: a stage's arithmetic is far shorter than an L2 round trip
+constexpr int kApMaxRows = 16;                 // consumer warps per CTA at most
+constexpr int kApDepth = 8;                    // staged blocks in flight
+constexpr int kApStage = 2 * kLpl;             // floats per stage: one orientation, hi and lo planes
+constexpr long long kApWait = 1LL << 24;
 
-__global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const __grid_constant__ ScaledApplyArgs a) {
+__device__ __forceinline__ void ap_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// s + lo -= (ah + al)(bh + bl), the sum kept unnormalised: the leading
+// product is split exactly (Dekker's two-product through an FMA) and
+// subtracted from s exactly (Knuth's two-sum); the two-sum's error, the
+// product's error and the two cross terms are summed in float and added to
+// lo.  11 float operations, one of them on each accumulator's dependency
+// chain; the pair is renormalised once, after the last term.
+__device__ __forceinline__ void dacc_fnms(float ah, float al, float bh, float bl, float &s, float &lo) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p);
+  const float t = s - p;
+  const float bb = t - s;
+  const float err = (s - (t - bb)) + (-p - bb);
+  lo += fmaf(-al, bh, fmaf(-ah, bl, err - e));
+  s = t;
+}
+
+// Four accumulators (one per t mod 4) of a 32-term row product, renormalised
+// and added in a fixed order.
+struct DAcc4 {
+  float s[4], lo[4];
+  __device__ __forceinline__ void reset(df64 first) {
+    s[0] = first.hi;
+    lo[0] = first.lo;
+    s[1] = s[2] = s[3] = lo[1] = lo[2] = lo[3] = 0.f;
+  }
+  // this lane's row of a staged plane pair (X[c][t]: hi at xh, lo at xl)
+  // against the vector v[0..31]; sign -1: subtract, +1: add
+  template <int SIGN>
+  __device__ __forceinline__ void row(const float *xh, const float *xl, const df64 *v) {
+    const float4 *h4 = reinterpret_cast<const float4 *>(xh);
+    const float4 *l4 = reinterpret_cast<const float4 *>(xl);
+    const float4 *v4 = reinterpret_cast<const float4 *>(v);
+#pragma unroll
+    for (int t4 = 0; t4 < kGfB / 4; ++t4) {
+      const float4 h = h4[t4], l = l4[t4], u01 = v4[2 * t4], u23 = v4[2 * t4 + 1];
+      const float sg = SIGN < 0 ? 1.f : -1.f;
+      dacc_fnms(sg * h.x, sg * l.x, u01.x, u01.y, s[0], lo[0]);
+      dacc_fnms(sg * h.y, sg * l.y, u01.z, u01.w, s[1], lo[1]);
+      dacc_fnms(sg * h.z, sg * l.z, u23.x, u23.y, s[2], lo[2]);
+      dacc_fnms(sg * h.w, sg * l.w, u23.z, u23.w, s[3], lo[3]);
+    }
+  }
+  __device__ __forceinline__ df64 total() const {
+    df64 r[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r[k] = df_two_sum(s[k], lo[k]);
+    return df_add(df_add(r[0], r[1]), df_add(r[2], r[3]));
+  }
+};
+
+// One warp per row of g, rows() consumer warps per CTA plus one producer warp
+// whose lane 0 streams the blocks of L through a ring of kApDepth shared
+// stages by bulk copies (TMA engine), each completing on its stage's "full"
+// mbarrier; a consumer warp that is done with a stage arrives on its "empty"
+// mbarrier, which the producer waits on before refilling it.  The sequence of
+// stages: forward (block row b: (b, m), m < b, then the inverted diagonal
+// block), as stored; backward (block column b = nb-1 .. 0: (m, b), m > b,
+// then the inverted diagonal block), transposed.  Every wait is bounded: a
+// timeout latches TRSGD_ETIMEOUT and the stage is waited for once more, so
+// that no copy is left in flight when the CTA exits.
+__global__ void __launch_bounds__(32 * (kApMaxRows + 1), 1) grid_scaled_apply_kernel(const __grid_constant__ ScaledApplyArgs a) {
   if (!*a.ok) return;   // no factor: the status is latched, G_n stays as it is
-  extern __shared__ __align__(16) float aps[];
-  const int nb = a.nb, Q = a.Q, Qp = nb * kGfB;
-  float(*stage)[2 * kGfB * kGfB] = reinterpret_cast<float(*)[2 * kGfB * kGfB]>(aps);   // ring of plane pairs (hi, lo)
-  df64 *vecb = reinterpret_cast<df64 *>(aps + kApDepth * 2 * kGfB * kGfB);              // [kApRows][Qp]: -g, u, p
+  extern __shared__ __align__(128) float aps[];
+  __shared__ __align__(8) uint64_t full[kApDepth], empty[kApDepth];
+  const int RW = a.rows, nb = a.nb, Q = a.Q, Qp = nb * kGfB;
+  float *ring = aps;
+  df64 *vecb = reinterpret_cast<df64 *>(aps + kApDepth * kApStage);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  df64 *vrow = vecb + (size_t)warp * Qp;
-#define vec_w(i) vrow[i]
-  const int row = blockIdx.x * kApRows + warp;
+  const int nfw = nb * (nb + 1) / 2, S = 2 * nfw;
+  if (tid == 0) {
+    for (int k = 0; k < kApDepth; ++k) {
+      mbar_init(&full[k], 1);
+      mbar_init(&empty[k], (uint32_t)RW);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (warp == RW) {   // producer
+    if (lane == 0) {
+      int b = 0, m = 0;   // block of stage s: forward row b, column m (m == b: diagonal)
+      for (int s = 0; s < S; ++s) {
+        const int slot = s % kApDepth;
+        if (s >= kApDepth && !mbar_wait_bounded(&empty[slot], (uint32_t)((s / kApDepth - 1) & 1), kApWait))
+          latch_status(a.status, kStatusTimeout);
+        int bi, bj, tr;
+        if (s < nfw) {
+          bi = b;
+          bj = m;
+          tr = 0;
+          if (++m > b) {
+            ++b;
+            m = 0;
+          }
+          if (s + 1 == nfw) {   // first backward stage: column nb-1, its diagonal block
+            b = nb - 1;
+            m = nb - 1;
+          }
+        } else {
+          bi = m;
+          bj = b;
+          tr = 1;
+          if (--m < b) {   // after the diagonal block of column b: column b-1 from row nb-1
+            --b;
+            m = nb - 1;
+          }
+        }
+        mbar_arrive_expect_tx(&full[slot], (uint32_t)(kApStage * sizeof(float)));
+        tma_load_1d(ring + (size_t)slot * kApStage, a.Lblk + (size_t)blk_rm(bi, bj) * kBlkF + tr * kApStage,
+                    (uint32_t)(kApStage * sizeof(float)), &full[slot]);
+      }
+    }
+    return;
+  }
+  df64 *v = vecb + (size_t)warp * Qp;
+  const int row = blockIdx.x * RW + warp;
   const bool live = row < a.In;
   // -g of this warp's row (the plain update's fixed-order sum of the partials)
   for (int q = lane; q < Qp; q += 32) {
     float g = 0.f;
     if (live && q < Q)
       for (int z = 0; z < a.splits; ++z) g += __ldcg(a.gpart + z * a.cstride + (long long)row * Q + q);
-    vec_w(q) = df64{-g, 0.f};
+    v[q] = df64{-g, 0.f};
     if (live && q < Q && a.dbg_g) a.dbg_g[(long long)row * Q + q] = g;
   }
-  // the sequence of staged blocks: forward (b, m < b) as C^T then (b, b) as
-  // L_bb^{-T}; backward (m > b, b) as C then (b, b) as L_bb^{-1}
-  const int nfw = nb * (nb + 1) / 2, S = 2 * nfw;
-  auto stage_src = [&](int s) -> const float * {
-    int bi, bj, tr;
-    if (s < nfw) {   // forward: block row b, m = 0..b
-      int b = 0;
-      while ((b + 1) * (b + 2) / 2 <= s) ++b;
-      bi = b;
-      bj = s - b * (b + 1) / 2;
-      tr = 1;
-    } else {         // backward: block column b = nb-1..0, m = nb-1..b
-      int u = s - nfw, b = nb - 1;
-      while (u >= nb - b) {
-        u -= nb - b;
-        --b;
-      }
-      bi = nb - 1 - u;
-      bj = b;
-      tr = 0;
-    }
-    return a.Lblk + (size_t)blk_rm(bi, bj) * kBlkF + (tr ? 2 * kGfB * kGfB : 0);
-  };
-  // one commit group per stage slot (empty past the end), so that "all but the
-  // newest kApDepth - 1 groups complete" always means "stage s arrived"
-  auto issue = [&](int s) {
-    if (s < S) {
-      const float *src = stage_src(s);
-      float *dst = stage[s % kApDepth];
-      for (int e = tid; e < 2 * kGfB * kGfB / 4; e += 32 * kApRows) cp_async16(dst + 4 * e, src + 4 * e);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  for (int k = 0; k < kApDepth; ++k) issue(k);
   __syncwarp();
   int s = 0;
-  auto wait_stage = [&]() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(kApDepth - 1) : "memory");
-    __syncthreads();
+  auto acquire = [&]() -> const float * {
+    const int slot = s % kApDepth;
+    const uint32_t par = (uint32_t)((s / kApDepth) & 1);
+    if (!mbar_wait_bounded(&full[slot], par, kApWait)) {
+      latch_status(a.status, kStatusTimeout);
+      mbar_wait_bounded(&full[slot], par, kApWait);
+    }
+    return ring + (size_t)slot * kApStage + lane * kLp;   // this lane's row of the hi plane
   };
   auto release = [&]() {
-    __syncthreads();
-    issue(s + kApDepth);
+    __syncwarp();
+    if (lane == 0) ap_arrive(&empty[s % kApDepth]);
     ++s;
   };
-  // four independent partial sums per lane (t mod 4): four dependency chains in flight
-  df64 pa[4];
-  auto reset = [&](df64 first) {
-    pa[0] = first;
-    pa[1] = pa[2] = pa[3] = df64{0.f, 0.f};
-  };
-  auto total = [&]() { return df_add(df_add(pa[0], pa[1]), df_add(pa[2], pa[3])); };
-  // forward: u L^T = -g
+  DAcc4 acc;
+  // forward: u L^T = -g; block row b: r = -g_b - sum_{m<b} C_bm u_m, u_b = L_bb^{-1} r
   for (int b = 0; b < nb; ++b) {
-    reset(vec_w(b * kGfB + lane));
-    for (int m = 0; m < b; ++m) {   // acc[c] -= sum_t C_bm[c][t] u_m[t]
-      wait_stage();
-      const float *X = stage[s % kApDepth];
-#pragma unroll 8
-      for (int t = 0; t < kGfB; ++t)
-        pa[t & 3] = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t),
-                                 pa[t & 3]);
+    acc.reset(v[b * kGfB + lane]);
+    for (int m = 0; m < b; ++m) {
+      const float *X = acquire();
+      acc.row<-1>(X, X + kLpl, v + m * kGfB);
       release();
     }
-    vec_w(b * kGfB + lane) = total();
+    const df64 r = acc.total();
     __syncwarp();
-    wait_stage();
-    {   // u_b[c] = sum_{t <= c} L_bb^{-1}[c][t] r[t]
-      const float *X = stage[s % kApDepth];
-      reset(df64{0.f, 0.f});
-#pragma unroll 8
-      for (int t = 0; t < kGfB; ++t)
-        if (t <= lane)
-          pa[t & 3] = df_fma(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(b * kGfB + t), pa[t & 3]);
-      const df64 u = total();
-      __syncwarp();
-      vec_w(b * kGfB + lane) = u;
-      __syncwarp();
-    }
+    v[b * kGfB + lane] = r;
+    __syncwarp();
+    const float *X = acquire();
+    acc.reset(df64{0.f, 0.f});
+    acc.row<1>(X, X + kLpl, v + b * kGfB);   // the inverse is lower triangular: zeros above the diagonal
+    const df64 u = acc.total();
     release();
+    v[b * kGfB + lane] = u;
+    __syncwarp();
   }
-  // backward: p L = u
+  // backward: p L = u; block column b: s = u_b - sum_{m>b} C_mb^T p_m, p_b = L_bb^{-T} s
   for (int b = nb - 1; b >= 0; --b) {
-    reset(vec_w(b * kGfB + lane));
-    for (int m = nb - 1; m > b; --m) {   // acc[c] -= sum_t C_mb[t][c] p_m[t]
-      wait_stage();
-      const float *X = stage[s % kApDepth];
-#pragma unroll 8
-      for (int t = 0; t < kGfB; ++t)
-        pa[t & 3] = df_fnms_fast(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(m * kGfB + t),
-                                 pa[t & 3]);
+    acc.reset(v[b * kGfB + lane]);
+    for (int m = nb - 1; m > b; --m) {
+      const float *X = acquire();
+      acc.row<-1>(X, X + kLpl, v + m * kGfB);
       release();
     }
-    vec_w(b * kGfB + lane) = total();
+    const df64 r = acc.total();
     __syncwarp();
-    wait_stage();
-    {   // p_b[c] = sum_{t >= c} L_bb^{-1}[t][c] s[t]
-      const float *X = stage[s % kApDepth];
-      reset(df64{0.f, 0.f});
-#pragma unroll 8
-      for (int t = 0; t < kGfB; ++t)
-        if (t >= lane)
-          pa[t & 3] = df_fma(df64{X[t * kGfB + lane], X[kGfB * kGfB + t * kGfB + lane]}, vec_w(b * kGfB + t), pa[t & 3]);
-      const df64 p = total();
-      __syncwarp();
-      vec_w(b * kGfB + lane) = p;
-      __syncwarp();
-    }
+    v[b * kGfB + lane] = r;
+    __syncwarp();
+    const float *X = acquire();
+    acc.reset(df64{0.f, 0.f});
+    acc.row<1>(X, X + kLpl, v + b * kGfB);
+    const df64 p = acc.total();
     release();
+    v[b * kGfB + lane] = p;
+    __syncwarp();
   }
   if (!live) return;
   // step rule and update (as the plain update kernel, with this p)
   for (int q = lane; q < Q; q += 32) {
-    const df64 pd = vec_w(q);
+    const df64 pd = v[q];
     const float p = pd.hi + pd.lo;
     const long long e = (long long)row * Q + q;
     float d;
@@ -478,8 +545,6 @@ __global__ void __launch_bounds__(32 * kApRows) grid_scaled_apply_kernel(const _
   }
 }
 
-#undef vec_w
-
 // ---- host side ----------------------------------------------------------------
 size_t grid_scaled_factor_floats(int Q) {
   const int nb = (Q + kGfB - 1) / kGfB;
@@ -492,8 +557,8 @@ cudaError_t grid_scaled_prepare() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(grid_gram_factor_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(grid_scaled_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)kApDepth * 2 * kGfB * kGfB * sizeof(float) +
-                                   (size_t)kApRows * kGridScaledMaxQ * sizeof(df64)));
+                             (int)((size_t)kApDepth * kApStage * sizeof(float) +
+                                   (size_t)kApMaxRows * kGridScaledMaxQ * sizeof(df64)));
   return e;
 }
 
@@ -547,8 +612,11 @@ cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
   aa.dbg_g = s.dbg_g;
   aa.dbg_p = s.dbg_p;
   aa.status = s.status;
-  const size_t smem = (size_t)kApDepth * 2 * kGfB * kGfB * sizeof(float) + (size_t)kApRows * nb * kGfB * sizeof(df64);
-  grid_scaled_apply_kernel<<<(s.In + kApRows - 1) / kApRows, 32 * kApRows, smem, st>>>(aa);
+  // rows per CTA: the rows spread over every SM (one CTA each) where they allow
+  const int sms = s.sms > 0 ? s.sms : 1;
+  aa.rows = std::min(kApMaxRows, std::max(1, (s.In + sms - 1) / sms));
+  const size_t smem = (size_t)kApDepth * kApStage * sizeof(float) + (size_t)aa.rows * nb * kGfB * sizeof(df64);
+  grid_scaled_apply_kernel<<<(s.In + aa.rows - 1) / aa.rows, 32 * (aa.rows + 1), smem, st>>>(aa);
   return cudaGetLastError();
 }
 

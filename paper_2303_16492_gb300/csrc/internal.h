@@ -140,6 +140,7 @@ struct GridScaledArgs {
   long long gstride;
   int gsplits;
   int In, Q;
+  int sms;                 // SMs of the device (rows of the direction spread over them)
   double hscale;           // 1 / |H|
   double damping;
   float *Lfac;
