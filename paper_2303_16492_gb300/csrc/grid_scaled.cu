@@ -75,8 +75,6 @@ __device__ __forceinline__ void stt(float *b, int e, df64 v) {
   b[e] = v.hi;
   b[e + kGfPlaneT] = v.lo;
 }
-// c + a b in double-float (the fused form of df64.cuh, c - (-a) b)
-__device__ __forceinline__ df64 df_fma(df64 a, df64 b, df64 c) { return df_fnms_fast(df_neg(a), b, c); }
 
 // column-major packed position of block (i, j), i >= j, of an nb x nb block triangle
 __device__ __forceinline__ int blk_cm(int i, int j, int nb) { return j * nb - j * (j - 1) / 2 + (i - j); }
@@ -97,15 +95,55 @@ struct GramFactorArgs {
   int *status;
 };
 
+// s + lo -= (ah + al)(bh + bl), the sum kept unnormalised: the leading
+// product is split exactly (Dekker's two-product through an FMA) and
+// subtracted from s exactly (Knuth's two-sum); the two-sum's error, the
+// product's error and the two cross terms are summed in float and added to
+// lo.  11 float operations, one of them on each accumulator's dependency
+// chain; the pair is renormalised once, after the last term.
+__device__ __forceinline__ void dacc_fnms(float ah, float al, float bh, float bl, float &s, float &lo) {
+  const float p = ah * bh;
+  const float e = fmaf(ah, bh, -p);
+  const float t = s - p;
+  const float bb = t - s;
+  const float err = (s - (t - bb)) + (-p - bb);
+  lo += fmaf(-al, bh, fmaf(-ah, bl, err - e));
+  s = t;
+}
+
+// the four accumulators of dacc_fnms renormalised and added in a fixed order
+__device__ __forceinline__ df64 dacc_total(const float (&s)[4], const float (&lo)[4]) {
+  df64 r[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) r[k] = df_two_sum(s[k], lo[k]);
+  return df_add(df_add(r[0], r[1]), df_add(r[2], r[3]));
+}
+
+// ready flags of the factor's blocks, read and written at cluster scope
+__device__ __forceinline__ int gf_ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.cluster.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void gf_st_release(int *p, int v) {
+  asm volatile("st.release.cluster.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+constexpr long long kGfSpin = 1LL << 22;   // polls of a ready flag before a wait gives up
+// outcome of a wait or of an attempt, shared by the CTA's threads
+enum : int { kGfOk = 0, kGfAbandoned = 1, kGfTimedOut = 2 };
+
 __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_constant__ GramFactorArgs a) {
   cg::cluster_group cluster = cg::this_cluster();
   const int cta = (int)cluster.block_rank();
   extern __shared__ __align__(16) float gfs[];
   float *slots = gfs;                                     // [kGfSlots][2][32 * 32]
   float *panelT = slots + kGfSlots * kGfSlotF;            // [kGfMaxNb][2][32 * 33], block (i, k) transposed
-  float *W = panelT + (size_t)kGfMaxNb * 2 * kGfPlaneT;   // [2][32 * 32] U^{-1}, then L_kk^{-1} (owner)
-  float *linvT = W + kGfSlotF;                            // [2][32 * 33] L_kk^{-1} transposed (every CTA)
-  __shared__ int blk_i[kGfSlots], blk_j[kGfSlots], nslots_s, fail_s;
+  float *W = panelT + (size_t)kGfMaxNb * 2 * kGfPlaneT;   // [2][32 * 32] U^{-1} of the diagonal elimination
+  float *linvT = W + kGfSlotF;                            // [2][32 * 33] L_kk^{-1} transposed
+  __shared__ int blk_i[kGfSlots], blk_j[kGfSlots], nslots_s;
+  __shared__ int ready[kGfSlots];   // epoch in which the slot's block became final (L_ik, or L_kk^{-1})
+  __shared__ int fail_flag;         // 4 epoch + outcome of an attempt this CTA abandoned
+  __shared__ int wait_s;            // outcome of the last wait, for every thread of the CTA
   __shared__ double diag_s[kGridScaledMaxQ];
   const int tid = threadIdx.x, cc = tid & 31, r0 = tid >> 5;
   const int nb = a.nb, Q = a.Q, nblk = nb * (nb + 1) / 2;
@@ -116,13 +154,17 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
       while (blk_cm(nb - 1, j, nb) < idx) ++j;   // last position of column j >= idx
       blk_i[n] = j + (idx - blk_cm(j, j, nb));
       blk_j[n] = j;
+      ready[n] = 0;
       ++n;
     }
     nslots_s = n;
+    fail_flag = 0;
   }
   __syncthreads();
   const int nslots = nslots_s;
   const df64 scale = df_from_double(a.scale);
+  auto owner = [&](int i, int j) { return blk_cm(i, j, nb) % kGfC; };
+  auto slot_of = [&](int i, int j) { return blk_cm(i, j, nb) / kGfC; };
 
   // h(ga, gb) as double-float: the partials summed in increasing order
   auto gram_entry = [&](int ga, int gb) {
@@ -130,18 +172,175 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
     for (int z = 0; z < a.splits; ++z) v = df_add(v, df64{__ldcg(a.hpart + z * a.pstride + (long long)ga * Q + gb), 0.f});
     return df_mul(v, scale);
   };
+  auto publish = [&](int slot, int epoch) {   // after every thread's writes to the block
+    __syncthreads();
+    if (tid == 0) gf_st_release(&ready[slot], epoch);
+  };
+  // thread 0 waits until the blocks (i, k), i in `rows`, are final in this
+  // epoch, or until the owner of one of them abandoned the attempt; every
+  // thread returns the outcome
+  auto wait_rows = [&](int k, unsigned rows, int epoch) -> int {
+    if (tid == 0) {
+      int res = kGfOk;
+      for (int i = k; i < nb && res == kGfOk; ++i) {
+        if (!((rows >> i) & 1u)) continue;
+        const int o = owner(i, k);
+        const int *rf = cluster.map_shared_rank(&ready[slot_of(i, k)], o);
+        const int *ff = cluster.map_shared_rank(&fail_flag, o);
+        res = kGfTimedOut;
+        for (long long it = 0; it < kGfSpin; ++it) {
+          if (gf_ld_acquire(rf) == epoch) {
+            res = kGfOk;
+            break;
+          }
+          if ((gf_ld_acquire(ff) >> 2) == epoch) {
+            res = kGfAbandoned;
+            break;
+          }
+        }
+      }
+      wait_s = res;
+    }
+    __syncthreads();
+    const int res = wait_s;
+    __syncthreads();
+    return res;
+  };
+  // the panel blocks (i, k), i in `rows`, into panelT[i] (transposed) from
+  // their owners' shared memory
+  auto fetch = [&](int k, unsigned rows, int epoch) -> int {
+    if (!rows) return kGfOk;
+    const int res = wait_rows(k, rows, epoch);
+    if (res != kGfOk) return res;
+    for (int i = k + 1; i < nb; ++i) {
+      if (!((rows >> i) & 1u)) continue;
+      const float *src = cluster.map_shared_rank(slots + slot_of(i, k) * kGfSlotF, owner(i, k));
+      float *dst = panelT + (size_t)i * 2 * kGfPlaneT;
+      for (int e = tid; e < kGfB * kGfB; e += kGfT) stt(dst, (e & 31) * kGfPitchT + (e >> 5), lds(src, e));
+    }
+    __syncthreads();
+    return kGfOk;
+  };
+  // diagonal block (k, k), held here: LDL^T with the row operations applied
+  // to an identity, then L_kk^{-1} = D^{-1/2} U^{-1} into the block's slot
+  // (and the output); false on a non-positive or non-finite pivot
+  auto diag = [&](int k) -> bool {
+    float *A = slots + slot_of(k, k) * kGfSlotF;
+    for (int e = tid; e < kGfB * kGfB; e += kGfT) sts(W, e, df64{(e >> 5) == (e & 31) ? 1.f : 0.f, 0.f});
+    __syncthreads();
+    for (int j = 0; j < kGfB; ++j) {
+      const df64 d = lds(A, j * kGfB + j);
+      if (!(d.hi > 0.f) || !isfinite(d.hi)) return false;   // the same value in every thread
+      const df64 invd = df_rcp(d);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = r0 + 16 * h;
+        if (r > j) {   // the same in the whole warp
+          // columns right of the pivot in A, the others in W: one select, no divergence
+          float *B = cc > j ? A : W;
+          const df64 l = df_mul(lds(A, r * kGfB + j), invd);
+          sts(B, r * kGfB + cc, df_fnms_fast(l, lds(B, j * kGfB + cc), lds(B, r * kGfB + cc)));
+        }
+      }
+      __syncthreads();
+    }
+    df64 v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = r0 + 16 * h;
+      const df64 qr = df_rcp(df_sqrt(lds(A, r * kGfB + r)));
+      v[h] = cc <= r ? df_mul(lds(W, r * kGfB + cc), qr) : df64{0.f, 0.f};
+    }
+    __syncthreads();   // every thread has read the pivots
+#pragma unroll
+    for (int h = 0; h < 2; ++h) sts(A, (r0 + 16 * h) * kGfB + cc, v[h]);
+    return true;
+  };
+  // a final block (slot s, position (i, j)) into the output, in both
+  // orientations; after its ready flag, off the critical path
+  auto write_out = [&](int s, int i, int j) {
+    const float *A = slots + s * kGfSlotF;
+    float *o = a.Lout + (size_t)blk_rm(i, j) * kBlkF;
+    for (int e = tid; e < kGfB * kGfB; e += kGfT) {
+      const int r = e >> 5, c = e & 31;
+      const df64 v = lds(A, e);
+      o[r * kLp + c] = v.hi;
+      o[kLpl + r * kLp + c] = v.lo;
+    }
+    for (int e = tid; e < kGfB * kGfB; e += kGfT) {   // consecutive threads: consecutive entries of a transposed row
+      const int c = e >> 5, r = e & 31;
+      const df64 v = lds(A, r * kGfB + c);
+      o[2 * kLpl + c * kLp + r] = v.hi;
+      o[3 * kLpl + c * kLp + r] = v.lo;
+    }
+  };
+  // panel of column k: L_ik = A_ik L_kk^{-T} for the blocks (i, k), i > k,
+  // held here, once L_kk^{-1} is final in its owner
+  auto panel_col = [&](int k, int epoch) -> int {
+    bool have = false;
+    for (int s = 0; s < nslots; ++s) have |= (blk_j[s] == k && blk_i[s] > k);
+    if (!have) return kGfOk;
+    const int res = wait_rows(k, 1u << k, epoch);
+    if (res != kGfOk) return res;
+    const float *Lk = cluster.map_shared_rank(slots + slot_of(k, k) * kGfSlotF, owner(k, k));
+    for (int e = tid; e < kGfB * kGfB; e += kGfT) stt(linvT, (e & 31) * kGfPitchT + (e >> 5), lds(Lk, e));
+    __syncthreads();
+    for (int s = 0; s < nslots; ++s) {
+      if (blk_j[s] != k || blk_i[s] <= k) continue;
+      float *A = slots + s * kGfSlotF;
+      df64 out[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = r0 + 16 * h;
+        // four unnormalised partial sums (t mod 4); L_kk^{-1} holds exact zeros
+        // above its diagonal, so the terms t > cc add nothing
+        float sa[4] = {0.f, 0.f, 0.f, 0.f}, la[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
+        for (int t = 0; t < kGfB; ++t) {
+          const df64 x = lds(A, r * kGfB + t), y = ldt(linvT, t * kGfPitchT + cc);
+          dacc_fnms(-x.hi, -x.lo, y.hi, y.lo, sa[t & 3], la[t & 3]);
+        }
+        out[h] = dacc_total(sa, la);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) sts(A, (r0 + 16 * h) * kGfB + cc, out[h]);
+      publish(s, epoch);
+      write_out(s, blk_i[s], k);
+    }
+    return kGfOk;
+  };
+  // trailing update A_ij -= L_ik L_jk^T of the block in slot s (panels staged)
+  auto trail = [&](int s) {
+    float *A = slots + s * kGfSlotF;
+    const float *Pi = panelT + (size_t)blk_i[s] * 2 * kGfPlaneT;
+    const float *Pj = panelT + (size_t)blk_j[s] * 2 * kGfPlaneT;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = r0 + 16 * h;
+      const df64 a0 = lds(A, r * kGfB + cc);
+      float sa[4] = {a0.hi, 0.f, 0.f, 0.f}, la[4] = {a0.lo, 0.f, 0.f, 0.f};
+#pragma unroll 8
+      for (int t = 0; t < kGfB; ++t) {
+        const df64 x = ldt(Pi, t * kGfPitchT + r), y = ldt(Pj, t * kGfPitchT + cc);
+        dacc_fnms(x.hi, x.lo, y.hi, y.lo, sa[t & 3], la[t & 3]);
+      }
+      sts(A, r * kGfB + cc, dacc_total(sa, la));
+    }
+  };
 
-  bool ok = false;
+  bool ok = false, timed_out = false;
   double extra = 0.0, tr = -1.0;
-  for (int m = -1; m < 7 && !ok; ++m) {
+  for (int m = -1; m < 7 && !ok && !timed_out; ++m) {
+    const int epoch = m + 2;
     if (m >= 0) {
       if (tr < 0.0) {   // trace of the undamped h, same fixed order in every CTA
         for (int q = tid; q < Q; q += kGfT) diag_s[q] = df_to_double(gram_entry(q, q));
         __syncthreads();
         if (tid == 0) {
-          double s = 0.0;
-          for (int q = 0; q < Q; ++q) s += diag_s[q];
-          diag_s[0] = s;
+          double sum = 0.0;
+          for (int q = 0; q < Q; ++q) sum += diag_s[q];
+          diag_s[0] = sum;
         }
         __syncthreads();
         tr = diag_s[0];
@@ -183,129 +382,64 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
         sts(A, e, v);
       }
     }
-    if (tid == 0) fail_s = 0;
-    cluster.sync();
-    bool failed = false;
-    for (int k = 0; k < nb && !failed; ++k) {
-      const int own_kk = blk_cm(k, k, nb) % kGfC;
-      // (1) diagonal block: LDL^T with the row operations applied to an identity
-      if (cta == own_kk) {
-        float *A = slots + (blk_cm(k, k, nb) / kGfC) * kGfSlotF;
-        for (int e = tid; e < kGfB * kGfB; e += kGfT) sts(W, e, df64{(e >> 5) == (e & 31) ? 1.f : 0.f, 0.f});
-        __syncthreads();
-        bool bad = false;
-        for (int j = 0; j < kGfB; ++j) {
-          const df64 d = lds(A, j * kGfB + j);
-          if (!(d.hi > 0.f) || !isfinite(d.hi)) {
-            bad = true;
-            break;
-          }
-          const df64 invd = df_rcp(d);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int r = r0 + 16 * h;
-            if (r > j) {
-              const df64 l = df_mul(lds(A, r * kGfB + j), invd);
-              if (cc > j) sts(A, r * kGfB + cc, df_fnms_fast(l, lds(A, j * kGfB + cc), lds(A, r * kGfB + cc)));
-              else sts(W, r * kGfB + cc, df_fnms_fast(l, lds(W, j * kGfB + cc), lds(W, r * kGfB + cc)));
-            }
-          }
-          __syncthreads();
-        }
-        if (!bad) {   // L_kk^{-1} = D^{-1/2} U^{-1}, in place in W
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int r = r0 + 16 * h;
-            const df64 qr = df_rcp(df_sqrt(lds(A, r * kGfB + r)));
-            const df64 v = cc <= r ? df_mul(lds(W, r * kGfB + cc), qr) : df64{0.f, 0.f};
-            sts(W, r * kGfB + cc, v);
-            float *o = a.Lout + (size_t)blk_rm(k, k) * kBlkF;
-            o[r * kLp + cc] = v.hi;
-            o[kLpl + r * kLp + cc] = v.lo;
-            o[2 * kLpl + cc * kLp + r] = v.hi;
-            o[3 * kLpl + cc * kLp + r] = v.lo;
-          }
-        }
-        if (tid == 0) fail_s = bad ? 1 : 0;
+    __syncthreads();
+    cluster.sync();   // every block loaded; the previous attempt's remote reads are over
+    // Right-looking block elimination with look-ahead: in step k a CTA first
+    // updates its blocks of column k + 1, so that the diagonal block k + 1 is
+    // factored and the panel of column k + 1 formed while the rest of the
+    // trailing update of step k is still running elsewhere; the blocks a
+    // step needs are waited for through their owners' ready flags.
+    int res = kGfOk;
+    if (owner(0, 0) == cta) {
+      if (diag(0)) {
+        publish(slot_of(0, 0), epoch);
+        write_out(slot_of(0, 0), 0, 0);
+      } else {
+        res = kGfAbandoned;
       }
-      cluster.sync();
-      failed = *cluster.map_shared_rank(&fail_s, own_kk) != 0;
-      if (failed) break;
-      // (2) panel: L_ik = A_ik L_kk^{-T} for the blocks (i, k), i > k, held here
-      bool have_panel = false;
-      for (int s = 0; s < nslots; ++s) have_panel |= (blk_j[s] == k && blk_i[s] > k);
-      if (have_panel) {
-        const float *Wk = cluster.map_shared_rank(W, own_kk);
-        for (int e = tid; e < kGfB * kGfB; e += kGfT) {
-          const int r = e >> 5, c = e & 31;
-          stt(linvT, c * kGfPitchT + r, lds(Wk, e));
-        }
-        __syncthreads();
-        for (int s = 0; s < nslots; ++s) {
-          if (blk_j[s] != k || blk_i[s] <= k) continue;
-          float *A = slots + s * kGfSlotF;
-          df64 out[2];
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int r = r0 + 16 * h;
-            // four independent partial sums (t mod 4): four chains in flight
-            df64 acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 8
-            for (int t = 0; t < kGfB; ++t)
-              if (t <= cc) acc[t & 3] = df_fma(lds(A, r * kGfB + t), ldt(linvT, t * kGfPitchT + cc), acc[t & 3]);
-            out[h] = df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3]));
-          }
-          __syncthreads();
-          float *o = a.Lout + (size_t)blk_rm(blk_i[s], k) * kBlkF;
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int r = r0 + 16 * h;
-            sts(A, r * kGfB + cc, out[h]);
-            o[r * kLp + cc] = out[h].hi;
-            o[kLpl + r * kLp + cc] = out[h].lo;
-            o[2 * kLpl + cc * kLp + r] = out[h].hi;
-            o[3 * kLpl + cc * kLp + r] = out[h].lo;
-          }
-        }
-      }
-      cluster.sync();
-      // (3) trailing update A_ij -= L_ik L_jk^T, k < j <= i, of the blocks held here
-      unsigned need = 0u;
-      for (int s = 0; s < nslots; ++s)
-        if (blk_j[s] > k) need |= (1u << blk_i[s]) | (1u << blk_j[s]);
-      for (int i = k + 1; i < nb; ++i) {
-        if (!((need >> i) & 1u)) continue;
-        const int pos = blk_cm(i, k, nb);
-        const float *src = cluster.map_shared_rank(slots + (pos / kGfC) * kGfSlotF, pos % kGfC);
-        float *dst = panelT + (size_t)i * 2 * kGfPlaneT;
-        for (int e = tid; e < kGfB * kGfB; e += kGfT) stt(dst, (e & 31) * kGfPitchT + (e >> 5), lds(src, e));
-      }
-      __syncthreads();
-      for (int s = 0; s < nslots; ++s) {
-        if (blk_j[s] <= k) continue;
-        float *A = slots + s * kGfSlotF;
-        const float *Pi = panelT + (size_t)blk_i[s] * 2 * kGfPlaneT;
-        const float *Pj = panelT + (size_t)blk_j[s] * 2 * kGfPlaneT;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int r = r0 + 16 * h;
-          df64 acc[4] = {lds(A, r * kGfB + cc), {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 8
-          for (int t = 0; t < kGfB; ++t)
-            acc[t & 3] = df_fnms_fast(ldt(Pi, t * kGfPitchT + r), ldt(Pj, t * kGfPitchT + cc), acc[t & 3]);
-          sts(A, r * kGfB + cc, df_add(df_add(acc[0], acc[1]), df_add(acc[2], acc[3])));
-        }
-      }
-      // the panel staging and the blocks are read again only after the next
-      // step's first cluster barrier
-      __syncthreads();
     }
-    ok = !failed;
-    cluster.sync();   // every CTA done with the others' shared memory before a restart reloads it
+    if (res == kGfOk) res = panel_col(0, epoch);
+    for (int k = 0; k + 1 < nb && res == kGfOk; ++k) {
+      unsigned need1 = 0u, need2 = 0u;   // rows of column k the two parts of the update read
+      for (int s = 0; s < nslots; ++s) {
+        if (blk_j[s] == k + 1) need1 |= (1u << blk_i[s]) | (1u << (k + 1));
+        else if (blk_j[s] > k + 1) need2 |= (1u << blk_i[s]) | (1u << blk_j[s]);
+      }
+      need2 &= ~need1;
+      if ((res = fetch(k, need1, epoch)) != kGfOk) break;
+      for (int s = 0; s < nslots; ++s)
+        if (blk_j[s] == k + 1) trail(s);
+      __syncthreads();
+      if (owner(k + 1, k + 1) == cta) {
+        if (!diag(k + 1)) {
+          res = kGfAbandoned;
+          break;
+        }
+        publish(slot_of(k + 1, k + 1), epoch);
+        write_out(slot_of(k + 1, k + 1), k + 1, k + 1);
+      }
+      if ((res = panel_col(k + 1, epoch)) != kGfOk) break;
+      if ((res = fetch(k, need2, epoch)) != kGfOk) break;
+      for (int s = 0; s < nslots; ++s)
+        if (blk_j[s] > k + 1) trail(s);
+      __syncthreads();   // panelT is rewritten by the next step's fetch
+    }
+    if (res != kGfOk && tid == 0) gf_st_release(&fail_flag, 4 * epoch + res);
+    cluster.sync();   // the attempt is over in every CTA
+    bool any = false;
+    for (int c = 0; c < kGfC; ++c) {
+      const int f = *cluster.map_shared_rank(&fail_flag, c);
+      if ((f >> 2) == epoch) {
+        any = true;
+        timed_out |= (f & 3) == kGfTimedOut;
+      }
+    }
+    ok = !any;
+    cluster.sync();   // every CTA has read the flags before the next attempt can set them
   }
   if (cta == 0 && tid == 0) {
     *a.ok = ok ? 1 : 0;
-    if (!ok) latch_status(a.status, kStatusNumeric);
+    if (!ok) latch_status(a.status, timed_out ? kStatusTimeout : kStatusNumeric);
   }
   if (ok && a.dbg_h) {   // the damped h that was factored, for the record
     const double dtot = a.damping + extra;
@@ -341,22 +475,6 @@ __device__ __forceinline__ void ap_arrive(uint64_t *bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// s + lo -= (ah + al)(bh + bl), the sum kept unnormalised: the leading
-// product is split exactly (Dekker's two-product through an FMA) and
-// subtracted from s exactly (Knuth's two-sum); the two-sum's error, the
-// product's error and the two cross terms are summed in float and added to
-// lo.  11 float operations, one of them on each accumulator's dependency
-// chain; the pair is renormalised once, after the last term.
-__device__ __forceinline__ void dacc_fnms(float ah, float al, float bh, float bl, float &s, float &lo) {
-  const float p = ah * bh;
-  const float e = fmaf(ah, bh, -p);
-  const float t = s - p;
-  const float bb = t - s;
-  const float err = (s - (t - bb)) + (-p - bb);
-  lo += fmaf(-al, bh, fmaf(-ah, bl, err - e));
-  s = t;
-}
-
 // Four accumulators (one per t mod 4) of a 32-term row product, renormalised
 // and added in a fixed order.
 struct DAcc4 {
@@ -383,12 +501,7 @@ struct DAcc4 {
       dacc_fnms(sg * h.w, sg * l.w, u23.z, u23.w, s[3], lo[3]);
     }
   }
-  __device__ __forceinline__ df64 total() const {
-    df64 r[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) r[k] = df_two_sum(s[k], lo[k]);
-    return df_add(df_add(r[0], r[1]), df_add(r[2], r[3]));
-  }
+  __device__ __forceinline__ df64 total() const { return dacc_total(s, lo); }
 };
 
 // One warp per row of g, rows() consumer warps per CTA plus one producer warp
