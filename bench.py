@@ -16,6 +16,7 @@ oracle on the same workload instead (host cores).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -36,9 +37,11 @@ WORKLOAD_DESC = {
     "c2": "N=4 100^4 FP32, R=10, ill-conditioned planted cores, noise 1e-4, |F|=1000, uniform sampling, "
           "plain TR-BRSGD, fixed step",
     "c3": "N=5 40^5 FP32, R=8, Gaussian planted cores, noise 1e-3, |F|=2048, uniform, fixed step",
-    "c5": "N=3 1000^3, R=20, ill-conditioned planted cores, noise 1e-3, |F|=4096, BF16 operands, AdaGrad, "
-          "whole-GPU path",
-    "c5p": "profiling size of c5: 1000x400x400, R=20, |F|=4096, BF16 operands, AdaGrad, whole-GPU path",
+    "c5": "N=3 1000^3 with X stored in BF16 (2 GB), R=20, ill-conditioned planted cores (1 -> 1e-2), noise 1e-3, "
+          "|F|=4096, scaled variant (TR-ScaledBRSGD, h from the same batch) with AdaGrad, BF16 tensor-core "
+          "operands, whole-GPU path",
+    "c5p": "profiling size of the 1000^3 workload, plain direction: 1000x400x400, R=20, |F|=4096, BF16 operands, "
+           "AdaGrad, whole-GPU path",
     "c5ps": "profiling size of c5, scaled variant: 1000x400x400, R=20, |F|=4096, BF16 operands, AdaGrad",
 }
 DTYPE_NAME = {0: "f64", 1: "f32", 2: "bf16 operands, f32 accumulate"}
@@ -124,10 +127,31 @@ def device_problem(w, device, seed_offset=0):
     return X, Xtrue, init
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum per step of the c2 step kernel,
-# from one ncu capture of 200 steps (101.38 MB); a kernel changed since its
-# capture has no entry (traffic null)
-MEASURED_TRAFFIC_PER_STEP = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per step of a kernel on a
+# workload, from one ncu capture (c2: one launch of 200 steps, 99,271,680 B
+# read + 1,653,504 B written), with the SHA-256 prefix of the kernel's source
+# files at the time of the capture: when the sources differ now, the kernel
+# has changed since and the traffic is reported as null
+STEP_KERNEL_SOURCES = ["step_kernel.cuh", "blocks.cuh", "common.cuh", "tables.cuh", "df64.cuh", "gramsolve.cuh",
+                       "internal.h", "step_f32x3.cu"]
+MEASURED_TRAFFIC_PER_STEP = {
+    ("c2", "step_cluster_kernel<float,float,12,3,false>"): {"bytes": 504625.92, "sources": "7cbc93e23654f5d3"},
+}
+
+
+def sources_digest(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2303_16492_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload, kernel):
+    rec = MEASURED_TRAFFIC_PER_STEP.get((workload, kernel))
+    if rec is None or sources_digest(STEP_KERNEL_SOURCES) != rec["sources"]:
+        return None
+    return rec["bytes"]
 
 
 def algorithmic_per_step(w):
@@ -257,7 +281,7 @@ def run_ours(args):
         kernel = f"step_cluster_kernel<float,float,{rmax},{pieces},false>"   # plain variant: scaled code compiled out
         # DRAM read+write per step of this kernel on this workload, from one ncu capture
         # (scaled to the timed launch); null when the kernel changed since the capture
-        traffic_step = MEASURED_TRAFFIC_PER_STEP.get((args.workload, kernel))
+        traffic_step = measured_traffic(args.workload, kernel)
         achieved = by / (ms_per_step * 1e-3) / 1e9
         peak = pk.get("hbm_gbs", 6800.0)
         fp32_peak = measured_fp32_peak()

@@ -120,35 +120,35 @@ struct FastDiv {
 // emit(r, value) as soon as it is formed.
 template <typename Emit>
 __device__ __forceinline__ void chain_row(const float (&prow)[kGridRmax], const float *S, int Ra, int Rb, Emit emit) {
+  // the outputs in a loop (the code stays small enough for the instruction
+  // cache), each inner product unrolled against the registers
   if ((Ra & 3) == 0) {
     const int Ra4 = Ra >> 2;
+#pragma unroll 1
+    for (int r = 0; r < Rb; ++r) {
+      const float4 *col = reinterpret_cast<const float4 *>(S + r * Ra);
+      float acc = 0.f;
 #pragma unroll
-    for (int r = 0; r < kGridRmax; ++r)
-      if (r < Rb) {
-        const float4 *col = reinterpret_cast<const float4 *>(S + r * Ra);
-        float acc = 0.f;
-#pragma unroll
-        for (int c4 = 0; c4 < kGridRmax / 4; ++c4)
-          if (c4 < Ra4) {
-            const float4 sv = col[c4];
-            acc = fmaf(prow[4 * c4], sv.x, acc);
-            acc = fmaf(prow[4 * c4 + 1], sv.y, acc);
-            acc = fmaf(prow[4 * c4 + 2], sv.z, acc);
-            acc = fmaf(prow[4 * c4 + 3], sv.w, acc);
-          }
-        emit(r, acc);
-      }
+      for (int c4 = 0; c4 < kGridRmax / 4; ++c4)
+        if (c4 < Ra4) {
+          const float4 sv = col[c4];
+          acc = fmaf(prow[4 * c4], sv.x, acc);
+          acc = fmaf(prow[4 * c4 + 1], sv.y, acc);
+          acc = fmaf(prow[4 * c4 + 2], sv.z, acc);
+          acc = fmaf(prow[4 * c4 + 3], sv.w, acc);
+        }
+      emit(r, acc);
+    }
   } else {
+#pragma unroll 1
+    for (int r = 0; r < Rb; ++r) {
+      const float *col = S + r * Ra;
+      float acc = 0.f;
 #pragma unroll
-    for (int r = 0; r < kGridRmax; ++r)
-      if (r < Rb) {
-        const float *col = S + r * Ra;
-        float acc = 0.f;
-#pragma unroll
-        for (int c = 0; c < kGridRmax; ++c)
-          if (c < Ra) acc = fmaf(prow[c], col[c], acc);
-        emit(r, acc);
-      }
+      for (int c = 0; c < kGridRmax; ++c)
+        if (c < Ra) acc = fmaf(prow[c], col[c], acc);
+      emit(r, acc);
+    }
   }
 }
 

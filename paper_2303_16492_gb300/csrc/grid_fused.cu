@@ -247,12 +247,16 @@ __global__ void __launch_bounds__(kFzThreads, 1) grid_fused_kernel(const __grid_
   // scratch (rows padded to Q4 = a multiple of 4 columns: 16-byte stores; zero
   // when this CTA had no samples); after the cluster barrier, the fixed-order
   // sum over the S slots and the update of this CTA's rows
+  // A tensor-memory load gives a thread one row; the 32 x 32 block a warp
+  // loads goes through shared memory (the Z tile is free now) and out as
+  // whole 128-byte row segments, eight lanes per row.
   const int Q4 = (Q + 3) & ~3;
   tc_fence_after();
   if (warp < 4) {
-    const int r = warp * 32 + lane;
     const uint32_t trow = tb + 64 + ((uint32_t)(warp * 32) << 16);
-    float4 *dst = reinterpret_cast<float4 *>(a.gpart + (size_t)s * a.pstride + (size_t)(m0 + r) * Q4);
+    float *tp = reinterpret_cast<float *>(Zs) + warp * 32 * 33;   // [32 rows][33]
+    float *slot = a.gpart + (size_t)s * a.pstride;
+    const int rq = lane >> 3, c4 = (lane & 7) * 4;
     for (int cb = 0; cb < kq * 2; ++cb) {   // 32 columns per load
       float v[32];
       if (any) {
@@ -261,10 +265,18 @@ __global__ void __launch_bounds__(kFzThreads, 1) grid_fused_kernel(const __grid_
 #pragma unroll
         for (int u = 0; u < 32; ++u) v[u] = 0.f;
       }
-      if (m0 + r < In)
 #pragma unroll
-        for (int u4 = 0; u4 < 8; ++u4)
-          if (cb * 32 + u4 * 4 < Q4) __stcg(dst + cb * 8 + u4, make_float4(v[4 * u4], v[4 * u4 + 1], v[4 * u4 + 2], v[4 * u4 + 3]));
+      for (int u = 0; u < 32; ++u) tp[lane * 33 + u] = v[u];
+      __syncwarp();
+      const int c = cb * 32 + c4;
+#pragma unroll
+      for (int it = 0; it < 8; ++it) {
+        const int row = it * 4 + rq, m = m0 + warp * 32 + row;
+        const float *t = tp + row * 33 + c4;
+        if (m < In && c < Q4)
+          __stcg(reinterpret_cast<float4 *>(slot + (size_t)m * Q4 + c), make_float4(t[0], t[1], t[2], t[3]));
+      }
+      __syncwarp();
     }
   }
   tc_fence_before();
