@@ -141,30 +141,40 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
   float *W = panelT + (size_t)kGfMaxNb * 2 * kGfPlaneT;   // [2][32 * 32] U^{-1} of the diagonal elimination
   float *linvT = W + kGfSlotF;                            // [2][32 * 33] L_kk^{-1} transposed
   __shared__ int blk_i[kGfSlots], blk_j[kGfSlots], nslots_s;
+  __shared__ unsigned char own_tab[kGfMaxNb * (kGfMaxNb + 1) / 2], slot_tab[kGfMaxNb * (kGfMaxNb + 1) / 2];
   __shared__ int ready[kGfSlots];   // epoch in which the slot's block became final (L_ik, or L_kk^{-1})
   __shared__ int fail_flag;         // 4 epoch + outcome of an attempt this CTA abandoned
   __shared__ int wait_s;            // outcome of the last wait, for every thread of the CTA
   __shared__ double diag_s[kGridScaledMaxQ];
   const int tid = threadIdx.x, cc = tid & 31, r0 = tid >> 5;
-  const int nb = a.nb, Q = a.Q, nblk = nb * (nb + 1) / 2;
+  const int nb = a.nb, Q = a.Q;
+  // Block ownership, the same table in every CTA: column-major order dealt
+  // round robin over the CTAs, so that the blocks of one column (the panel
+  // of a step) are formed by different CTAs in parallel.
   if (tid == 0) {
-    int n = 0;
-    for (int idx = cta; idx < nblk; idx += kGfC) {
-      int j = 0;
-      while (blk_cm(nb - 1, j, nb) < idx) ++j;   // last position of column j >= idx
-      blk_i[n] = j + (idx - blk_cm(j, j, nb));
-      blk_j[n] = j;
-      ready[n] = 0;
-      ++n;
+    for (int idx = 0; idx < nb * (nb + 1) / 2; ++idx) {
+      own_tab[idx] = (unsigned char)(idx % kGfC);
+      slot_tab[idx] = (unsigned char)(idx / kGfC);
     }
+    int n = 0;
+    for (int j = 0; j < nb; ++j)
+      for (int i = j; i < nb; ++i) {
+        const int idx = blk_cm(i, j, nb);
+        if (own_tab[idx] != cta) continue;
+        const int sl = slot_tab[idx];
+        blk_i[sl] = i;
+        blk_j[sl] = j;
+        ready[sl] = 0;
+        ++n;
+      }
     nslots_s = n;
     fail_flag = 0;
   }
   __syncthreads();
   const int nslots = nslots_s;
   const df64 scale = df_from_double(a.scale);
-  auto owner = [&](int i, int j) { return blk_cm(i, j, nb) % kGfC; };
-  auto slot_of = [&](int i, int j) { return blk_cm(i, j, nb) / kGfC; };
+  auto owner = [&](int i, int j) { return (int)own_tab[blk_cm(i, j, nb)]; };
+  auto slot_of = [&](int i, int j) { return (int)slot_tab[blk_cm(i, j, nb)]; };
 
   // h(ga, gb) as double-float: the partials summed in increasing order
   auto gram_entry = [&](int ga, int gb) {
@@ -274,40 +284,49 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
       o[3 * kLpl + c * kLp + r] = v.lo;
     }
   };
-  // panel of column k: L_ik = A_ik L_kk^{-T} for the blocks (i, k), i > k,
-  // held here, once L_kk^{-1} is final in its owner
-  auto panel_col = [&](int k, int epoch) -> int {
-    bool have = false;
-    for (int s = 0; s < nslots; ++s) have |= (blk_j[s] == k && blk_i[s] > k);
-    if (!have) return kGfOk;
-    const int res = wait_rows(k, 1u << k, epoch);
-    if (res != kGfOk) return res;
+  // L_kk^{-1} (final in its owner) into linvT, transposed
+  auto stage_linv = [&](int k) {
     const float *Lk = cluster.map_shared_rank(slots + slot_of(k, k) * kGfSlotF, owner(k, k));
     for (int e = tid; e < kGfB * kGfB; e += kGfT) stt(linvT, (e & 31) * kGfPitchT + (e >> 5), lds(Lk, e));
     __syncthreads();
-    for (int s = 0; s < nslots; ++s) {
-      if (blk_j[s] != k || blk_i[s] <= k) continue;
-      float *A = slots + s * kGfSlotF;
-      df64 out[2];
+  };
+  // panel block in slot s, (i, k): L_ik = A_ik L_kk^{-T} (linvT staged), then
+  // its ready flag and its output
+  auto panel_block = [&](int s, int k, int epoch) {
+    float *A = slots + s * kGfSlotF;
+    df64 out[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = r0 + 16 * h;
-        // four unnormalised partial sums (t mod 4); L_kk^{-1} holds exact zeros
-        // above its diagonal, so the terms t > cc add nothing
-        float sa[4] = {0.f, 0.f, 0.f, 0.f}, la[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int h = 0; h < 2; ++h) {
+      const int r = r0 + 16 * h;
+      // four unnormalised partial sums (t mod 4); L_kk^{-1} holds exact zeros
+      // above its diagonal, so the terms t > cc add nothing
+      float sa[4] = {0.f, 0.f, 0.f, 0.f}, la[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll 8
-        for (int t = 0; t < kGfB; ++t) {
-          const df64 x = lds(A, r * kGfB + t), y = ldt(linvT, t * kGfPitchT + cc);
-          dacc_fnms(-x.hi, -x.lo, y.hi, y.lo, sa[t & 3], la[t & 3]);
-        }
-        out[h] = dacc_total(sa, la);
+      for (int t = 0; t < kGfB; ++t) {
+        const df64 x = lds(A, r * kGfB + t), y = ldt(linvT, t * kGfPitchT + cc);
+        dacc_fnms(-x.hi, -x.lo, y.hi, y.lo, sa[t & 3], la[t & 3]);
       }
-      __syncthreads();
-#pragma unroll
-      for (int h = 0; h < 2; ++h) sts(A, (r0 + 16 * h) * kGfB + cc, out[h]);
-      publish(s, epoch);
-      write_out(s, blk_i[s], k);
+      out[h] = dacc_total(sa, la);
     }
+    __syncthreads();
+#pragma unroll
+    for (int h = 0; h < 2; ++h) sts(A, (r0 + 16 * h) * kGfB + cc, out[h]);
+    publish(s, epoch);
+    write_out(s, blk_i[s], k);
+  };
+  // the panel blocks (i, k), i > k, held here and not in `done` (a slot
+  // mask), once L_kk^{-1} is final (`staged`: already in linvT)
+  auto panel_col = [&](int k, int epoch, unsigned done, bool staged) -> int {
+    bool have = false;
+    for (int s = 0; s < nslots; ++s) have |= (blk_j[s] == k && blk_i[s] > k && !((done >> s) & 1u));
+    if (!have) return kGfOk;
+    if (!staged) {
+      const int res = wait_rows(k, 1u << k, epoch);
+      if (res != kGfOk) return res;
+      stage_linv(k);
+    }
+    for (int s = 0; s < nslots; ++s)
+      if (blk_j[s] == k && blk_i[s] > k && !((done >> s) & 1u)) panel_block(s, k, epoch);
     return kGfOk;
   };
   // trailing update A_ij -= L_ik L_jk^T of the block in slot s (panels staged)
@@ -391,37 +410,60 @@ __global__ void __launch_bounds__(kGfT, 1) grid_gram_factor_kernel(const __grid_
     // step needs are waited for through their owners' ready flags.
     int res = kGfOk;
     if (owner(0, 0) == cta) {
-      if (diag(0)) {
-        publish(slot_of(0, 0), epoch);
-        write_out(slot_of(0, 0), 0, 0);
-      } else {
-        res = kGfAbandoned;
-      }
+      if (diag(0)) publish(slot_of(0, 0), epoch);
+      else res = kGfAbandoned;
     }
-    if (res == kGfOk) res = panel_col(0, epoch);
+    if (res == kGfOk) res = panel_col(0, epoch, 0u, false);
+    if (res == kGfOk && owner(0, 0) == cta) write_out(slot_of(0, 0), 0, 0);
     for (int k = 0; k + 1 < nb && res == kGfOk; ++k) {
-      unsigned need1 = 0u, need2 = 0u;   // rows of column k the two parts of the update read
-      for (int s = 0; s < nslots; ++s) {
-        if (blk_j[s] == k + 1) need1 |= (1u << blk_i[s]) | (1u << (k + 1));
-        else if (blk_j[s] > k + 1) need2 |= (1u << blk_i[s]) | (1u << blk_j[s]);
-      }
-      need2 &= ~need1;
-      if ((res = fetch(k, need1, epoch)) != kGfOk) break;
-      for (int s = 0; s < nslots; ++s)
-        if (blk_j[s] == k + 1) trail(s);
-      __syncthreads();
-      if (owner(k + 1, k + 1) == cta) {
-        if (!diag(k + 1)) {
+      const int kd = k + 1;
+      unsigned fetched = 0u, trailed = 0u, paneled = 0u;   // rows of column k; slots done in this step
+      bool staged = false;                                 // L_{kd kd}^{-1} in linvT
+      if (owner(kd, kd) == cta) {
+        // the critical chain first: the diagonal block of column kd, factored
+        // as soon as it is updated, then the block below it (held here too)
+        const int sd = slot_of(kd, kd);
+        if ((res = fetch(k, 1u << kd, epoch)) != kGfOk) break;
+        fetched |= 1u << kd;
+        trail(sd);
+        trailed |= 1u << sd;
+        __syncthreads();
+        if (!diag(kd)) {
           res = kGfAbandoned;
           break;
         }
-        publish(slot_of(k + 1, k + 1), epoch);
-        write_out(slot_of(k + 1, k + 1), k + 1, k + 1);
+        publish(sd, epoch);
+        if (kd + 1 < nb && owner(kd + 1, kd) == cta) {
+          const int sb = slot_of(kd + 1, kd);
+          if ((res = fetch(k, 1u << (kd + 1), epoch)) != kGfOk) break;
+          fetched |= 1u << (kd + 1);
+          trail(sb);
+          trailed |= 1u << sb;
+          __syncthreads();
+          stage_linv(kd);
+          staged = true;
+          panel_block(sb, kd, epoch);
+          paneled |= 1u << sb;
+        }
       }
-      if ((res = panel_col(k + 1, epoch)) != kGfOk) break;
+      unsigned need1 = 0u, need2 = 0u;   // rows of column k the rest of the update reads
+      for (int s = 0; s < nslots; ++s) {
+        if ((trailed >> s) & 1u) continue;
+        if (blk_j[s] == kd) need1 |= (1u << blk_i[s]) | (1u << kd);
+        else if (blk_j[s] > kd) need2 |= (1u << blk_i[s]) | (1u << blk_j[s]);
+      }
+      need1 &= ~fetched;
+      if ((res = fetch(k, need1, epoch)) != kGfOk) break;
+      fetched |= need1;
+      for (int s = 0; s < nslots; ++s)
+        if (blk_j[s] == kd && !((trailed >> s) & 1u)) trail(s);
+      __syncthreads();
+      if ((res = panel_col(kd, epoch, paneled, staged)) != kGfOk) break;
+      if (owner(kd, kd) == cta) write_out(slot_of(kd, kd), kd, kd);
+      need2 &= ~fetched;
       if ((res = fetch(k, need2, epoch)) != kGfOk) break;
       for (int s = 0; s < nslots; ++s)
-        if (blk_j[s] > k + 1) trail(s);
+        if (blk_j[s] > kd) trail(s);
       __syncthreads();   // panelT is rewritten by the next step's fetch
     }
     if (res != kGfOk && tid == 0) gf_st_release(&fail_flag, 4 * epoch + res);
