@@ -47,7 +47,9 @@ typedef enum {
   TRSGD_ECUDA = 3,        /* a CUDA runtime call failed                   */
   TRSGD_ENUMERIC = 4,     /* non-finite step or non-SPD preconditioner    */
   TRSGD_ETIMEOUT = 5,     /* a bounded device wait ran out                */
-  TRSGD_EUNSUPPORTED = 6  /* valid, but outside what this build supports  */
+  TRSGD_EUNSUPPORTED = 6, /* valid, but outside what this build supports  */
+  TRSGD_EBADINDEX = 7     /* debug build: a drawn slice index or a fiber
+                             column outside its range (replaced by 0)     */
 } trsgd_status;
 
 /* Mini-batch distributions of Sec. 3.2: uniform, leverage-based (Lemma
@@ -265,6 +267,21 @@ trsgd_status trsgd_set_debug(trsgd_handle *h, int32_t on);
  * a negative value makes every first try time out.  Applies to every problem
  * of the handle.  Synchronising. */
 trsgd_status trsgd_set_wait_limit(trsgd_handle *h, int64_t polls);
+
+/* Index checks of the debug build (the library compiled with -DTRSGD_DEBUG,
+ * _lib/libtrsgd_debug.so): every drawn slice index i_k (Algorithm 2) is
+ * checked against [0, I_k) and every fiber column of X_[n] against
+ * [0, prod_{k != n} I_k) before anything is read with it; a violation
+ * latches TRSGD_EBADINDEX in the device status word (read by the next
+ * synchronising call) and the index is replaced by 0, so no access leaves
+ * its buffer and nothing traps.  This call replaces the upper bound of the
+ * check on core k's indices by `bound` (1 <= bound <= I_k; 0 restores I_k)
+ * for every problem of the handle, so that the reporting path can be
+ * exercised with indices that are valid for the memory they address; the
+ * draws themselves do not change.  Synchronising.  TRSGD_EINVAL for a null
+ * handle, k outside [0, N) or bound outside [0, I_k]; TRSGD_EUNSUPPORTED in
+ * the product build, which has no checks compiled in. */
+trsgd_status trsgd_debug_index_bound(trsgd_handle *h, int32_t k, int64_t bound);
 
 typedef enum {
   TRSGD_DBG_MODE = 0,   /* int32 [1]                                   */

@@ -9,7 +9,7 @@ from . import build as _build
 
 MAX_ORDER = 8
 
-OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED = range(7)
+OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, EUNSUPPORTED, EBADINDEX = range(8)
 DIST_UNIFORM, DIST_LEVERAGE, DIST_EUCLIDEAN, DIST_OPTIMAL = range(4)
 PLAIN, SCALED = 0, 1
 STEP_FIXED, STEP_ADAGRAD = 0, 1
@@ -105,6 +105,7 @@ _SIGNATURES = {
     "trsgd_step_apply": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
                                         ctypes.c_void_p, ctypes.c_int64]),
     "trsgd_set_wait_limit": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64]),
+    "trsgd_debug_index_bound": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64]),
     "trsgd_probe_peak": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p,
                                         ctypes.POINTER(ctypes.c_double)]),
     "trsgd_destroy": (None, [ctypes.c_void_p]),
@@ -119,14 +120,23 @@ def header_symbols():
     return sorted(set(re.findall(r"\b(trsgd_[a-z_0-9]+)\s*\(", text)))
 
 
+def library_path() -> str:
+    """libtrsgd.so, or with TRSGD_DEBUG=1 in the environment the debug build
+    (index checks compiled in)."""
+    return _build.DEBUG_LIB if os.environ.get("TRSGD_DEBUG") == "1" else _build.LIB
+
+
 def lib():
-    """The loaded libtrsgd.so; raises if it has not been built."""
+    """The loaded library; raises if it has not been built (there is no
+    fallback)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"{_build.LIB} is missing: build the CUDA library first "
-                               "(python -m paper_2303_16492_gb300.build)")
-        L = ctypes.CDLL(_build.LIB)
+        path = library_path()
+        if not os.path.exists(path):
+            flag = " --debug" if path == _build.DEBUG_LIB else ""
+            raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                               f"(python -m paper_2303_16492_gb300.build{flag})")
+        L = ctypes.CDLL(path)
         for name, (res, args) in _SIGNATURES.items():
             fn = getattr(L, name)
             fn.restype = res

@@ -162,6 +162,10 @@ class Solver:
         """trsgd_set_wait_limit (failure-path testing; 0 restores the default)."""
         check(_abi.lib().trsgd_set_wait_limit(self._h, int(polls)), "trsgd_set_wait_limit")
 
+    def debug_index_bound(self, k: int, bound: int):
+        """trsgd_debug_index_bound (debug build only; 0 restores I_k)."""
+        check(_abi.lib().trsgd_debug_index_bound(self._h, int(k), int(bound)), "trsgd_debug_index_bound")
+
     def shard_plan(self, t: int, rank: int, world: int) -> _abi.Shard:
         """trsgd_shard_plan: this rank's sample ranges of iteration t."""
         sh = _abi.Shard()

@@ -3,7 +3,10 @@
 Each translation unit under csrc/ is compiled by nvcc in parallel with
 ``-gencode arch=compute_103a,code=sm_103a -lineinfo -O3`` and linked into
 ``_lib/libtrsgd.so`` against the shared CUDA runtime (the one PyTorch loads).
-Usage: ``python -m paper_2303_16492_gb300.build [--force]``.
+``debug=True`` builds the same sources with ``-DTRSGD_DEBUG`` (index checks
+that report ``TRSGD_EBADINDEX``) into ``_lib/libtrsgd_debug.so``; the library
+loader picks it when the environment sets ``TRSGD_DEBUG=1``.
+Usage: ``python -m paper_2303_16492_gb300.build [--force] [--debug]``.
 """
 from __future__ import annotations
 
@@ -17,6 +20,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libtrsgd.so")
+DEBUG_OUT = os.path.join(OUT, "debug")
+DEBUG_LIB = os.path.join(OUT, "libtrsgd_debug.so")
 ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -35,16 +40,16 @@ def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "trsgd.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra, out: str = OUT) -> str:
+    obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -52,23 +57,25 @@ def _compile(src: str, extra) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every .cu under csrc/ and link libtrsgd.so; returns its path."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT, exist_ok=True)
-    extra = list(extra) + (["-Xptxas", "-v"] if verbose else [])
+def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = False) -> str:
+    """Compile every .cu under csrc/ and link libtrsgd.so (or, debug,
+    libtrsgd_debug.so); returns its path."""
+    lib, out = (DEBUG_LIB, DEBUG_OUT) if debug else (LIB, OUT)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out, exist_ok=True)
+    extra = list(extra) + (["-Xptxas", "-v"] if verbose else []) + (["-DTRSGD_DEBUG"] if debug else [])
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + ".tmp"
+        objs = list(ex.map(lambda s: _compile(s, extra, out), srcs))
+    tmp = lib + ".tmp"
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv, debug="--debug" in sys.argv))

@@ -9,6 +9,7 @@
 #include "trsgd.h"
 #include "common.cuh"
 #include "internal.h"
+#include "nvtx.h"
 #include "tables.cuh"
 
 using namespace trsgd;
@@ -365,6 +366,7 @@ const char *trsgd_status_string(trsgd_status s) {
     case TRSGD_ENUMERIC: return "numerical failure (non-finite step or non-SPD preconditioner)";
     case TRSGD_ETIMEOUT: return "bounded device wait timed out";
     case TRSGD_EUNSUPPORTED: return "unsupported configuration";
+    case TRSGD_EBADINDEX: return "index out of range (debug build checks)";
   }
   return "unknown status";
 }
@@ -599,6 +601,7 @@ static trsgd_status read_status(trsgd_handle *h) {
   cudaMemsetAsync(h->d_status, 0, sizeof(int), h->stream);
   if (s == kStatusTimeout) return TRSGD_ETIMEOUT;
   if (s == kStatusNumeric) return TRSGD_ENUMERIC;
+  if (s == kStatusBadIndex) return TRSGD_EBADINDEX;
   return TRSGD_ECUDA;
 }
 
@@ -606,6 +609,7 @@ static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
   if (h->grid) {   // the mode is drawn on the host; five kernels per iteration
     const ProbDesc &D = h->hdesc[0];
     for (int64_t t = t0; t < t0 + nsteps; ++t) {
+      NvtxRange r("trsgd iteration (whole GPU)");
       const int n = draw_mode(D.seed, t, D.N);
       cudaError_t e = launch_grid_step(h->gp, D, n, t, h->dbg ? 1 : 0, h->stream);
       if (e != cudaSuccess) return from_cuda(e);
@@ -616,6 +620,7 @@ static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
   if (h->optimal) {   // per step: the optimal distribution of this step's mode, its draws, then the step
     const ProbDesc &D = h->hdesc[0];
     for (int64_t t = t0; t < t0 + nsteps; ++t) {
+      NvtxRange r("trsgd iteration (optimal distribution)");
       const int n = draw_mode(D.seed, t, D.N);
       cudaError_t e = launch_optimal_sampling(h->core_dtype, h->xc_dtype, D.N, n, D.I, D.R,
                                               (const void *const *)D.cores, D.xmode[n], D.ldx[n], D.seed, t, D.J,
@@ -629,6 +634,7 @@ static trsgd_status launch_steps(trsgd_handle *h, int64_t t0, int64_t nsteps) {
     return TRSGD_OK;
   }
   while (nsteps > 0) {
+    NvtxRange r("trsgd step_cluster_kernel launch (K iterations)");
     const int n = (int)std::min<int64_t>(nsteps, 1 << 20);
     cudaError_t e = launch_step(h->core_dtype, h->xc_dtype, h->rmax, h->ddesc, h->nprob, h->lay, h->threads, t0,
                                 n, nullptr, h->stream);
@@ -668,6 +674,7 @@ trsgd_status trsgd_set_counter(trsgd_handle *h, int64_t t) {
 
 trsgd_status trsgd_rel_error(trsgd_handle *h, int32_t problem, const void *Xref_dev, double *out) {
   if (!h || !out || problem < 0 || problem >= h->nprob) return TRSGD_EINVAL;
+  NvtxRange r("trsgd_rel_error");
   const trsgd_config &c = h->cfg[problem];
   const ProbDesc &D = h->hdesc[problem];
   // the reference is read in the cores' dtype: the caller's own X only when it has that dtype
@@ -807,6 +814,20 @@ trsgd_status trsgd_set_wait_limit(trsgd_handle *h, int64_t polls) {
                                   h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   return from_cuda(e);
+}
+
+trsgd_status trsgd_debug_index_bound(trsgd_handle *h, int32_t k, int64_t bound) {
+  if (!h || h->nprob < 1) return TRSGD_EINVAL;
+  for (const auto &c : h->cfg)
+    if (k < 0 || k >= c.N || bound < 0 || bound > c.I[k]) return TRSGD_EINVAL;
+  if (kDebugChecks) {
+    for (auto &D : h->hdesc) D.dbg_bound[k] = (int)bound;
+    cudaError_t e = cudaMemcpyAsync(h->ddesc, h->hdesc.data(), sizeof(ProbDesc) * h->nprob, cudaMemcpyHostToDevice,
+                                    h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    return from_cuda(e);
+  }
+  return TRSGD_EUNSUPPORTED;   // the product build has no checks compiled in
 }
 
 trsgd_status trsgd_get_debug(trsgd_handle *h, int32_t item, void *out_host, size_t bytes, size_t *written) {

@@ -239,4 +239,21 @@ __device__ __forceinline__ void latch_status(int *status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// Index checks of the debug build (-DTRSGD_DEBUG): an index outside
+// [0, bound) latches TRSGD_EBADINDEX and is replaced by 0, so that nothing is
+// read outside its buffer; the product build compiles the checks out.
+#ifdef TRSGD_DEBUG
+constexpr bool kDebugChecks = true;
+#else
+constexpr bool kDebugChecks = false;
+#endif
+template <typename I>
+__device__ __forceinline__ I debug_checked(I i, long long bound, int *status) {
+  if (kDebugChecks && (i < 0 || (long long)i >= bound)) {
+    latch_status(status, kStatusBadIndex);
+    return I(0);
+  }
+  return i;
+}
+
 }  // namespace trsgd

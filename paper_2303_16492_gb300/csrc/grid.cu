@@ -24,6 +24,7 @@
 // to about 2^-24 relative per term, accumulated in FP32 in tensor memory.
 #include "common.cuh"
 #include "internal.h"
+#include "nvtx.h"
 
 #include <cuda_bf16.h>
 
@@ -86,6 +87,8 @@ struct GridSampleArgs {
   double *dbg_pf;                       // [J]
   float *dbg_z;                         // [J][Q]
   int *dbg_n;
+  int bound[kMaxOrder];                 // debug build: upper bounds of the index checks
+  int *status;
 };
 
 constexpr int kGridRmax = 32;
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(kSmpThreads, 3) grid_samples_kernel(GridSample
   for (int e = tid; e < nj * L; e += kSmpThreads) {
     const int jl = e / L, sf = e - jl * L, k = (n + 1 + sf) % N;
     const uint64_t u = draw_u64(a.seed, a.t, a.stream, k, (uint32_t)(jbase + jl));
-    idx_s[jl][sf] = (int)mulhi64(u, (uint64_t)a.I[k]);
+    idx_s[jl][sf] = debug_checked((int)mulhi64(u, (uint64_t)a.I[k]), a.bound[k], a.status);
   }
   __syncthreads();
   if (a.col || a.rec) {
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kSmpThreads, 3) grid_samples_kernel(GridSample
         col += (long long)idx_s[jl][sf] * st;
         st *= a.I[k];
       }
-      if (a.col) a.col[j] = col;
+      if (a.col) a.col[j] = debug_checked(col, st, a.status);
       if (a.rec) {   // p_F in ring order (FP64), only for the record
         double pf = 1.0;
         for (int sf = 0; sf < L; ++sf) pf = __dmul_rn(pf, __ddiv_rn(1.0, (double)a.I[(n + 1 + sf) % N]));
@@ -719,6 +722,7 @@ static int nsplits(long long j0, long long j1, long long unit) { return (int)((j
 // columns only for the F batch
 static cudaError_t launch_samples(const GridPath &g, const ProbDesc &D, int n, long long t, long long j0,
                                   long long j1, int stream, int rec, cudaStream_t s, bool transpose = true) {
+  NvtxRange r("grid_samples_kernel (+ transposes)");
   const int N = D.N, Q = D.R[n] * D.R[(n + 1) % N];
   const int Qp = (Q + 63) / 64 * 64;
   GridSampleArgs sa = {};
@@ -746,6 +750,8 @@ static cudaError_t launch_samples(const GridPath &g, const ProbDesc &D, int n, l
   sa.dbg_pf = D.dbg_pf;
   sa.dbg_z = static_cast<float *>(D.dbg_z);
   sa.dbg_n = D.dbg_n;
+  for (int k = 0; k < N; ++k) sa.bound[k] = D.dbg_bound[k] > 0 ? D.dbg_bound[k] : D.I[k];
+  sa.status = D.status;
   int rmax = 1;
   for (int k = 0; k < N; ++k) rmax = std::max(rmax, D.R[k]);
   const int blocks = (int)((j1 - j0 + kSpc - 1) / kSpc);
@@ -795,6 +801,7 @@ static cudaError_t launch_gram(const GridPath &g, int Q, long long j0, long long
 cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, long long t, long long j0,
                                 long long j1, long long h0, long long h1, int rec, float *gout, float *hout,
                                 cudaStream_t s) {
+  NvtxRange r("grid partial sums (G pieces, samples, tcgen05 GEMMs)");
   const int N = D.N, In = D.I[n], Q = D.R[n] * D.R[(n + 1) % N];
   const int Ip = (In + 127) / 128 * 128, Qp = (Q + 63) / 64 * 64;
   const int np = g.np;
@@ -900,6 +907,7 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
 
 cudaError_t launch_grid_apply(const GridPath &g, const ProbDesc &D, int n, const float *gparts, int gsplits,
                               const float *hparts, int hsplits, int rec, cudaStream_t s) {
+  NvtxRange r("grid apply (sum of the partials, direction, step rule, update)");
   const int N = D.N, In = D.I[n], Q = D.R[n] * D.R[(n + 1) % N];
   if (g.scaled) {
     GridScaledArgs sa = {};
@@ -969,11 +977,17 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
     const int In = D.I[n], Q = D.R[n] * D.R[(n + 1) % D.N];
     const int Ip = (In + 127) / 128 * 128, Qp = (Q + 63) / 64 * 64;
     const long long total = (long long)Ip * Qp;
-    grid_prepare_kernel<<<(int)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(
-        static_cast<const float *>(D.cores[n]), In, Q, Ip, Qp, g.ldg, 1, g.Gp[0], g.Gp[1], g.Gp[2]);
+    {
+      NvtxRange r("grid_prepare_kernel");
+      grid_prepare_kernel<<<(int)std::min<long long>((total + 255) / 256, 4096), 256, 0, s>>>(
+          static_cast<const float *>(D.cores[n]), In, Q, Ip, Qp, g.ldg, 1, g.Gp[0], g.Gp[1], g.Gp[2]);
+    }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_samples(g, D, n, t, 0, D.J, kStreamF, rec, s, false);
-    if (e == cudaSuccess) e = launch_grid_fused(g.tmZc, g.tmG[0], g.gpart, D, n, g.col, g.w, S, rec, s);
+    if (e == cudaSuccess) {
+      NvtxRange r("grid_fused_kernel");
+      e = launch_grid_fused(g.tmZc, g.tmG[0], g.gpart, D, n, g.col, g.w, S, rec, s);
+    }
     return e;
   }
   const long long JH = g.JH > 0 ? g.JH : D.J;

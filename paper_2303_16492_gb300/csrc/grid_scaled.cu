@@ -38,6 +38,7 @@
 #include "common.cuh"
 #include "df64.cuh"
 #include "internal.h"
+#include "nvtx.h"
 
 namespace cg = cooperative_groups;
 
@@ -721,6 +722,7 @@ cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
   const int nb = (s.Q + kGfB - 1) / kGfB;
   if (s.Q < 1 || s.Q > kGridScaledMaxQ) return cudaErrorInvalidValue;
   {
+    NvtxRange r("grid_gram_factor_kernel");
     GramFactorArgs fa = {};
     fa.hpart = s.hpart;
     fa.pstride = s.hstride;
@@ -748,6 +750,7 @@ cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
     cudaError_t e = cudaLaunchKernelEx(&cfg, grid_gram_factor_kernel, fa);
     if (e != cudaSuccess) return e;
   }
+  NvtxRange r("grid_scaled_apply_kernel");
   ScaledApplyArgs aa = {};
   aa.gpart = s.gpart;
   aa.cstride = s.gstride;

@@ -32,6 +32,9 @@ struct ProbDesc {
   // default 2^22; negative: none, every first try times out); the timed-out
   // operation is then drained by a second wait of the default length
   long long wait_limit;
+  // upper bounds of the debug build's checks of the drawn indices of core k
+  // (0: I_k); see trsgd_debug_index_bound
+  int dbg_bound[8];
   // recording of intermediates (problem 0 only)
   int dbg;
   int *dbg_n, *dbg_idx;

@@ -474,6 +474,14 @@ __global__ void __launch_bounds__(kMaxThreads)
       }
       const double w = need_pf ? __ddiv_rn(1.0, __dmul_rn(cst[8 + n], pF)) : cst[16];
       wt_s[jl] = need_pf ? (T)w : wt_uni;
+      if (kDebugChecks) {   // debug build: this sample's indices and fiber column (st = J_n here)
+        for (int sp = 0; sp < L; ++sp) {
+          const int k = ring(sp);
+          idx_s[jl * kMaxOrder + k] =
+              debug_checked(idx_s[jl * kMaxOrder + k], D.dbg_bound[k] > 0 ? D.dbg_bound[k] : I[k], D.status);
+        }
+        col = debug_checked(col, st, D.status);
+      }
       col_s[jl] = col;
       if (rec) {
         D.dbg_pf[j0 + jl] = pF;
@@ -891,7 +899,7 @@ __global__ void __launch_bounds__(kMaxThreads)
               i = cdf_search(cdf, Ik, mulhi64(u, W));
               pH = __dmul_rn(pH, __ldcg(D.prob[k] + i));
             }
-            hidx[jl * kMaxOrder + k] = i;
+            hidx[jl * kMaxOrder + k] = debug_checked(i, D.dbg_bound[k] > 0 ? D.dbg_bound[k] : Ik, D.status);
           }
           hw[jl] = (T)__ddiv_rn(1.0, __dmul_rn(cst[24 + n], pH));
         }

@@ -23,10 +23,22 @@ def test_every_declared_symbol_is_exported(lib):
     assert set(names) == set(_abi._SIGNATURES)
 
 
+def test_debug_build_exports_every_symbol():
+    """The debug build (index checks compiled in) links and exports the same
+    entry points; loaded on its own, without touching the product library."""
+    import ctypes as C
+    path = _build.build(debug=True)
+    L = C.CDLL(path)
+    assert [n for n in _abi.header_symbols() if not hasattr(L, n)] == []
+    L.trsgd_status_string.restype = C.c_char_p
+    assert b"index" in L.trsgd_status_string(_abi.EBADINDEX)
+
+
 def test_status_strings(lib):
-    for s in range(7):
-        assert _abi.status_string(s)
+    for s in range(8):
+        assert _abi.status_string(s) != "unknown status"
     assert "invalid" in _abi.status_string(_abi.EINVAL)
+    assert "index" in _abi.status_string(_abi.EBADINDEX)
 
 
 def test_config_struct_layout():
@@ -124,6 +136,7 @@ def test_null_handle_calls(lib):
     out = ctypes.c_double()
     assert lib.trsgd_rel_error(None, 0, None, ctypes.byref(out)) == _abi.EINVAL
     assert lib.trsgd_set_debug(None, 1) == _abi.EINVAL
+    assert lib.trsgd_debug_index_bound(None, 0, 0) == _abi.EINVAL
     assert lib.trsgd_launch_count(None) == -1
     assert lib.trsgd_tensor_pieces(None) == -1
     assert lib.trsgd_gd_step(None, 0, 0.1, 0.0) == _abi.EINVAL
