@@ -53,7 +53,9 @@ struct trsgd_handle {
   int core_dtype = 1, xc_dtype = 1, rmax = 4;
   int fp32_pieces = 1;   // FP32 contractions on the tensor cores as three BF16 pieces when they fit
   std::vector<ProbDesc> hdesc;
-  ProbDesc *ddesc = nullptr;
+  ProbDesc *ddesc = nullptr;   // in launch order: cluster b steps problem perm[b]
+  std::vector<int> perm;       // launch order of the problems
+  std::vector<ProbDesc> ldesc; // host copy in launch order (the source of the last upload)
   Buffers buf;
   StepLayout lay = {};
   int threads = 512;
@@ -371,6 +373,31 @@ const char *trsgd_status_string(trsgd_status s) {
   return "unknown status";
 }
 
+// The descriptors in launch order: batched problems are stepped by one
+// cluster each, in order of decreasing work (sum over the modes of
+// I_n R_n R_{n+1} |F|), so that when the clusters run in waves the largest
+// problems share the first wave and the last wave holds the smallest.
+static void launch_order(trsgd_handle *h) {
+  const int P = h->nprob;
+  std::vector<double> cost(P, 0.0);
+  for (int p = 0; p < P; ++p) {
+    const trsgd_config &c = h->cfg[p];
+    for (int k = 0; k < c.N; ++k) cost[p] += (double)c.I[k] * (double)(c.R[k] * c.R[(k + 1) % c.N]) * (double)c.J;
+  }
+  h->perm.resize(P);
+  for (int p = 0; p < P; ++p) h->perm[p] = p;
+  std::stable_sort(h->perm.begin(), h->perm.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+}
+
+static cudaError_t upload_descs(trsgd_handle *h) {
+  h->ldesc.resize(h->nprob);
+  for (int b = 0; b < h->nprob; ++b) h->ldesc[b] = h->hdesc[h->perm[b]];
+  cudaError_t e = cudaMemcpyAsync(h->ddesc, h->ldesc.data(), sizeof(ProbDesc) * h->nprob, cudaMemcpyHostToDevice,
+                                  h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  return e;
+}
+
 trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *const *X_dev,
                         void *const *cores_dev, void *stream, trsgd_handle **out) {
   if (!out) return TRSGD_EINVAL;
@@ -583,10 +610,8 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
     if (e != cudaSuccess) return fail(from_cuda(e));
   }
   h->threads = 512;
-  if ((e = cudaMemcpyAsync(h->ddesc, h->hdesc.data(), sizeof(ProbDesc) * nproblems, cudaMemcpyHostToDevice,
-                           h->stream)) != cudaSuccess)
-    return fail(from_cuda(e));
-  if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return fail(from_cuda(e));
+  launch_order(h);
+  if ((e = upload_descs(h)) != cudaSuccess) return fail(from_cuda(e));
   if ((e = cudaGetLastError()) != cudaSuccess) return fail(from_cuda(e));
   *out = h;
   return TRSGD_OK;
@@ -802,18 +827,13 @@ trsgd_status trsgd_set_debug(trsgd_handle *h, int32_t on) {
   }
   D.dbg = on ? 1 : 0;
   h->dbg = on != 0;
-  cudaError_t e = cudaMemcpyAsync(h->ddesc, &D, sizeof(ProbDesc), cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  return from_cuda(e);
+  return from_cuda(upload_descs(h));
 }
 
 trsgd_status trsgd_set_wait_limit(trsgd_handle *h, int64_t polls) {
   if (!h) return TRSGD_EINVAL;
   for (auto &D : h->hdesc) D.wait_limit = polls;
-  cudaError_t e = cudaMemcpyAsync(h->ddesc, h->hdesc.data(), sizeof(ProbDesc) * h->nprob, cudaMemcpyHostToDevice,
-                                  h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-  return from_cuda(e);
+  return from_cuda(upload_descs(h));
 }
 
 trsgd_status trsgd_debug_index_bound(trsgd_handle *h, int32_t k, int64_t bound) {
@@ -822,10 +842,7 @@ trsgd_status trsgd_debug_index_bound(trsgd_handle *h, int32_t k, int64_t bound) 
     if (k < 0 || k >= c.N || bound < 0 || bound > c.I[k]) return TRSGD_EINVAL;
   if (kDebugChecks) {
     for (auto &D : h->hdesc) D.dbg_bound[k] = (int)bound;
-    cudaError_t e = cudaMemcpyAsync(h->ddesc, h->hdesc.data(), sizeof(ProbDesc) * h->nprob, cudaMemcpyHostToDevice,
-                                    h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    return from_cuda(e);
+    return from_cuda(upload_descs(h));
   }
   return TRSGD_EUNSUPPORTED;   // the product build has no checks compiled in
 }
