@@ -35,7 +35,8 @@ namespace trsgd {
 
 namespace {
 
-constexpr int kFzThreads = 160;          // warps 0-3: epilogue (TMEM lane quarters), warp 4: issue
+constexpr int kFzThreads = 288;          // warps 0-7: epilogue (two per TMEM lane quarter, one half of the
+                                         // columns each); thread 0 issues; warp 8 gathers and sums
 constexpr int kFzChunk = 64;             // samples per chunk
 constexpr long long kFzWait = 1LL << 24;
 
@@ -197,27 +198,26 @@ __global__ void __launch_bounds__(kFzThreads, 1) grid_fused_kernel(const __grid_
     fz_wait(&mdone, pm, a.status);
     pm ^= 1u;
     tc_fence_after();
-    // weighted residual Ew = w (D_E - X) in BF16, row r of the tile per thread
-    if (warp < 4) {
-      const int r = warp * 32 + lane, m = m0 + r;
-      const uint32_t trow = tb + ((uint32_t)(warp * 32) << 16);
+    // weighted residual Ew = w (D_E - X) in BF16: row r of the tile per
+    // thread, samples [32 half, 32 half + 32) of the chunk per warp
+    if (warp < 8) {
+      const int qw = warp & 3, half = warp >> 2;
+      const int r = qw * 32 + lane, m = m0 + r;
+      const uint32_t trow = tb + ((uint32_t)(qw * 32) << 16);
+      float v[32];
+      tmem_ld32x(trow + (uint32_t)(half * 32), v);
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        float v[32];
-        tmem_ld32x(trow + (uint32_t)(half * 32), v);
+      for (int g8 = 0; g8 < 4; ++g8) {
+        __nv_bfloat16 h[8];
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) {
-          __nv_bfloat16 h[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            const int jl = half * 32 + g8 * 8 + u, j = j0 + jl;
-            const bool valid = m < In && j < J;
-            const float e = valid ? v[g8 * 8 + u] - __bfloat162float(Xs[jl * 128 + r]) : 0.f;
-            if (valid && a.dbg_e) a.dbg_e[(size_t)j * In + m] = e;
-            h[u] = __float2bfloat16_rn(e * a.w);
-          }
-          *reinterpret_cast<uint4 *>(Es + sw128_off(r, half * 32 + g8 * 8)) = *reinterpret_cast<const uint4 *>(h);
+        for (int u = 0; u < 8; ++u) {
+          const int jl = half * 32 + g8 * 8 + u, j = j0 + jl;
+          const bool valid = m < In && j < J;
+          const float e = valid ? v[g8 * 8 + u] - __bfloat162float(Xs[jl * 128 + r]) : 0.f;
+          if (valid && a.dbg_e) a.dbg_e[(size_t)j * In + m] = e;
+          h[u] = __float2bfloat16_rn(e * a.w);
         }
+        *reinterpret_cast<uint4 *>(Es + sw128_off(r, half * 32 + g8 * 8)) = *reinterpret_cast<const uint4 *>(h);
       }
     }
     fence_proxy_async_smem();
@@ -248,16 +248,18 @@ __global__ void __launch_bounds__(kFzThreads, 1) grid_fused_kernel(const __grid_
   // when this CTA had no samples); after the cluster barrier, the fixed-order
   // sum over the S slots and the update of this CTA's rows
   // A tensor-memory load gives a thread one row; the 32 x 32 block a warp
-  // loads goes through shared memory (the Z tile is free now) and out as
-  // whole 128-byte row segments, eight lanes per row.
+  // loads goes through shared memory (the G tile is free now) and out as
+  // whole 128-byte row segments, eight lanes per row. Two warps per lane
+  // quarter take alternate blocks of 32 columns.
   const int Q4 = (Q + 3) & ~3;
   tc_fence_after();
-  if (warp < 4) {
-    const uint32_t trow = tb + 64 + ((uint32_t)(warp * 32) << 16);
-    float *tp = reinterpret_cast<float *>(Zs) + warp * 32 * 33;   // [32 rows][33]
+  if (warp < 8) {
+    const int qw = warp & 3, half = warp >> 2;
+    const uint32_t trow = tb + 64 + ((uint32_t)(qw * 32) << 16);
+    float *tp = reinterpret_cast<float *>(As) + warp * 32 * 33;   // [32 rows][33]
     float *slot = a.gpart + (size_t)s * a.pstride;
     const int rq = lane >> 3, c4 = (lane & 7) * 4;
-    for (int cb = 0; cb < kq * 2; ++cb) {   // 32 columns per load
+    for (int cb = half; cb < kq * 2; cb += 2) {   // 32 columns per load
       float v[32];
       if (any) {
         tmem_ld32x(trow + (uint32_t)(cb * 32), v);
@@ -271,7 +273,7 @@ __global__ void __launch_bounds__(kFzThreads, 1) grid_fused_kernel(const __grid_
       const int c = cb * 32 + c4;
 #pragma unroll
       for (int it = 0; it < 8; ++it) {
-        const int row = it * 4 + rq, m = m0 + warp * 32 + row;
+        const int row = it * 4 + rq, m = m0 + qw * 32 + row;
         const float *t = tp + row * 33 + c4;
         if (m < In && c < Q4)
           __stcg(reinterpret_cast<float4 *>(slot + (size_t)m * Q4 + c), make_float4(t[0], t[1], t[2], t[3]));
