@@ -313,7 +313,11 @@ def run_ours(args):
                           "launch": {"cluster_ctas": cluster, "threads": threads, "steps_per_launch": args.steps},
                           "l2": f"inputs larger than L2 (X {x_mb:.0f} MB and its {len(w.dims)} mode-major copies; "
                                 "fibers sampled at random each step; the cores stay resident as the iterate)"},
-               "rse_after": rse, "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+               "rse_after": rse, "roofline": roofline,
+               # J * mean_n I_n * bytes(x) per step: the sampled fibers moved per second
+               "sampled_fiber_gbs": round(w.J * sum(w.dims) / len(w.dims) * X.element_size() / (ms_per_step * 1e-3) / 1e9,
+                                          3),
+               "gpu_launches": launches, "clocks": clocks,
                "e2e": e2e, "cpu_baseline": cpu, "time_to_rse": ttr, "extras": extras}
         print(json.dumps(out), flush=True)
     solver.close()
@@ -672,7 +676,8 @@ def run_large(args, device, target=1e-2, check=100, max_steps=4000, timed_steps=
             "time_to_rse": {"target": target, "iterations": it, "reached": reached, "rse": rse,
                             "seconds": round(ms_total * 1e-3, 4)},
             "method_tflops": round(fl / (ms * 1e-3) / 1e12, 2),
-            "frac_of_bf16_sustained": round(fl / (ms * 1e-3) / 1e12 / peak, 4)}
+            "frac_of_bf16_sustained": round(fl / (ms * 1e-3) / 1e12 / peak, 4),
+            "sampled_fiber_gbs": round(w.J * sum(w.dims) / len(w.dims) * (2 if bf else 4) / (ms * 1e-3) / 1e9, 2)}
     out["c5_config"] = {"dims": w.dims, "ranks": w.ranks, "J": w.J, "rule": "AdaGrad", "eta_plain": w.eta,
                         "eta_scaled": w.extra.get("eta_scaled", w.eta), "path": "grid (whole GPU)",
                         "x_storage": "BF16 (2 GB) for the BF16 runs; FP32 (4 GB) for the FP32 runs",
