@@ -327,7 +327,8 @@ trsgd_status trsgd_autotune(trsgd_handle *h, int32_t steps_per_trial);
  * The samples of a batch fall into split units (a multiple of 256 samples,
  * fixed by the problem and the device); one partial is one unit's sum
  * (gelems = I_n R_n R_{n+1} floats for the gradient, helems =
- * (R_n R_{n+1})^2 for the Gram).  trsgd_shard_plan deals the units of
+ * (R_n R_{n+1})^2 for the Gram; a Gram unit is the gradient's unit over a
+ * power of two, so a rank's gradient units hold whole Gram units).  trsgd_shard_plan deals the units of
  * iteration t to `world` ranks in contiguous runs (rank r gets units
  * [r U / world, (r+1) U / world) of U); a rank may get none.
  *   trsgd_shard_plan    host-only; fills *out for rank `rank` of `world`.
@@ -349,7 +350,7 @@ typedef struct {
   int32_t mode;                     /* n of iteration t                        */
   int64_t j0, j1;                   /* this rank's samples of F                */
   int64_t h0, h1;                   /* this rank's samples of H (J_H > 0)      */
-  int64_t gunit, hunit;             /* samples per unit of F and H             */
+  int64_t gunit, hunit;             /* samples per gradient / Gram partial     */
   int64_t gsplits, hsplits;         /* partials this rank computes             */
   int64_t gsplits_max, hsplits_max; /* the largest count over the ranks        */
   int64_t gelems, helems;           /* floats per partial                      */

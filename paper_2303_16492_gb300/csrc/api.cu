@@ -1018,14 +1018,14 @@ trsgd_status trsgd_shard_plan(trsgd_handle *h, int64_t t, int32_t rank, int32_t 
   sh.gelems = (long long)D.I[n] * Q;
   if (g.scaled) {
     const long long JH = g.JH > 0 ? g.JH : D.J;
-    sh.hunit = grid_split_unit(g, D, n, JH);
+    sh.hunit = grid_gram_unit(g, D, n, JH);
     if (g.JH > 0) {
       deal(JH, sh.hunit, sh.h0, sh.h1, sh.hsplits, sh.hsplits_max);
-    } else {   // H = F: the Gram over this rank's F samples, in the same units
+    } else {   // H = F: the Gram over this rank's F samples, in Gram units (whole ones: hunit divides gunit)
       sh.h0 = sh.j0;
       sh.h1 = sh.j1;
-      sh.hsplits = sh.gsplits;
-      sh.hsplits_max = sh.gsplits_max;
+      sh.hsplits = (sh.j1 - sh.j0 + sh.hunit - 1) / sh.hunit;
+      sh.hsplits_max = sh.gsplits_max * (sh.gunit / sh.hunit);
     }
     sh.helems = Q * Q;
   }

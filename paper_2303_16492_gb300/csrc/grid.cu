@@ -331,6 +331,9 @@ struct __align__(64) GridGemmArgs {
   int npe;
   float *dbg_e;            // [J][In] or null
   int *status;
+  // Gram partials: only tiles that hold an entry (a, b) of the 32 x 32 block
+  // lower triangle (block(a) >= block(b)), the entries the factorisation reads
+  int lower_only;
 };
 
 __host__ __device__ inline size_t grid_gemm_stage_bytes(int npa, int npb, int NT) {
@@ -397,6 +400,7 @@ __global__ void __launch_bounds__(kGemmThreads) grid_gemm_kernel(const __grid_co
   unsigned char *smem = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int m0 = blockIdx.x * 128, n0 = a.nbase + blockIdx.y * NT;
+  if (a.lower_only && (m0 + 127) / 32 < n0 / 32) return;   // a tile above the block diagonal: never read
   const int kbeg = a.kbase + blockIdx.z * a.kper, kend = min(kbeg + a.kper, a.kbase + a.kchunks);
   const int nck = max(0, kend - kbeg);
   const size_t stage = grid_gemm_stage_bytes(npa, npb, NT);
@@ -718,6 +722,25 @@ long long grid_split_unit(const GridPath &g, const ProbDesc &D, int n, long long
 
 static int nsplits(long long j0, long long j1, long long unit) { return (int)((j1 - j0 + unit - 1) / unit); }
 
+// Split unit of the Gram partials: the unit of the same sample batch halved
+// (at most twice) while it stays a multiple of 256 samples and the Gram's
+// tiles times its splits stay within one wave of the SMs. A unit of the
+// gradient then holds a whole number of Gram units, so a rank's range of
+// gradient units is also a range of Gram units, and the fixed-order sum of
+// the Gram partials does not depend on how the ranks split the batch.
+long long grid_gram_unit(const GridPath &g, const ProbDesc &D, int n, long long nsamples) {
+  const int N = D.N, Q = D.R[n] * D.R[(n + 1) % N];
+  int NT = 0;
+  const long long tiles = (long long)((Q + 127) / 128) * grid_ntiles(Q, 3, NT);
+  long long unit = grid_split_unit(g, D, n, nsamples);
+  for (int halvings = 0; halvings < 2; ++halvings) {
+    const long long u2 = unit / 2;
+    if (u2 < 256 || u2 % 256 != 0 || tiles * ((nsamples + u2 - 1) / u2) > g.sms) break;
+    unit = u2;
+  }
+  return unit;
+}
+
 // Z (and Z^T) of the samples [j0, j1) on Philox stream `stream`; fiber
 // columns only for the F batch
 static cudaError_t launch_samples(const GridPath &g, const ProbDesc &D, int n, long long t, long long j0,
@@ -769,7 +792,7 @@ static cudaError_t launch_samples(const GridPath &g, const ProbDesc &D, int n, l
 
 // Z^T Z over the samples [j0, j1) held in Z^T, one FP32 partial per unit
 static cudaError_t launch_gram(const GridPath &g, int Q, long long j0, long long j1, long long unit, int n,
-                               float *hout, int *status, cudaStream_t s) {
+                               float *hout, int *status, int rec, cudaStream_t s) {
   int NT = 0;
   const int ntile = grid_ntiles(Q, 3, NT);
   GridGemmArgs ga = {};
@@ -793,6 +816,7 @@ static cudaError_t launch_gram(const GridPath &g, int Q, long long j0, long long
   ga.Mv = Q;
   ga.Nv = Q;
   ga.status = status;
+  ga.lower_only = rec ? 0 : 1;   // the record keeps the whole h
   dim3 grid((unsigned)((Q + 127) / 128), ntile, nsplits(j0, j1, unit));
   grid_gemm_kernel<<<grid, kGemmThreads, grid_gemm_smem(3, 3, NT, ga.S), s>>>(ga);
   return cudaGetLastError();
@@ -891,14 +915,15 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
   // 5. scaled variant: partial Grams of the Hessian batch (H = F: the same samples)
   if (g.scaled) {
     if (g.JH > 0) {
-      const long long uh = grid_split_unit(g, D, n, g.JH);
+      const long long uh = grid_gram_unit(g, D, n, g.JH);
       if (h0 < 0 || h1 > g.JH || h0 > h1 || (h0 % uh) != 0 || ((h1 % uh) != 0 && h1 != g.JH))
         return cudaErrorInvalidValue;
       if (h1 > h0) {
         if ((e = launch_samples(g, D, n, t, h0, h1, kStreamH, 0, s)) != cudaSuccess) return e;
-        if ((e = launch_gram(g, Q, h0, h1, uh, n, hout, D.status, s)) != cudaSuccess) return e;
+        if ((e = launch_gram(g, Q, h0, h1, uh, n, hout, D.status, rec, s)) != cudaSuccess) return e;
       }
-    } else if (fpart && (e = launch_gram(g, Q, j0, j1, unit, n, hout, D.status, s)) != cudaSuccess) {
+    } else if (fpart && (e = launch_gram(g, Q, j0, j1, grid_gram_unit(g, D, n, D.J), n, hout, D.status, rec, s)) !=
+                            cudaSuccess) {
       return e;
     }
   }
@@ -992,7 +1017,7 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
   }
   const long long JH = g.JH > 0 ? g.JH : D.J;
   const int gs = nsplits(0, D.J, grid_split_unit(g, D, n, D.J));
-  const int hs = g.scaled ? nsplits(0, JH, grid_split_unit(g, D, n, JH)) : 0;
+  const int hs = g.scaled ? nsplits(0, JH, grid_gram_unit(g, D, n, JH)) : 0;
   cudaError_t e = launch_grid_partial(g, D, n, t, 0, D.J, 0, g.JH, rec, g.gpart, g.hpart, s);
   if (e == cudaSuccess) e = launch_grid_apply(g, D, n, g.gpart, gs, g.hpart, hs, rec, s);
   return e;
@@ -1038,7 +1063,7 @@ void grid_layout(const int *I, const int *R, int N, int J, int np, int scaled, i
   // a range of samples yields at most max_splits + 1 partials (unit rounding)
   // (and the fused BF16 kernel's 16 slots of rows padded to a multiple of 4 columns)
   g.gpart_elems = std::max((size_t)(g.max_splits + 1) * Imax * Qmax, (size_t)16 * Imax * ((Qmax + 3) & ~3));
-  g.hpart_elems = scaled ? (size_t)(g.max_splits + 1) * Qmax * Qmax : 0;
+  g.hpart_elems = scaled ? (size_t)(4 * g.max_splits + 1) * Qmax * Qmax : 0;   // Gram units: up to 4 per unit
 }
 
 }  // namespace trsgd

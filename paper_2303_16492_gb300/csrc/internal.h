@@ -170,6 +170,7 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
 // Split-K unit of mode n (samples per partial, a multiple of 256) and the
 // number of partials a sample range [j0, j1) produces.
 long long grid_split_unit(const GridPath &g, const ProbDesc &D, int n, long long nsamples);
+long long grid_gram_unit(const GridPath &g, const ProbDesc &D, int n, long long nsamples);
 // The two halves of an iteration: the partial gradient (and partial Gram)
 // over the sample ranges [j0, j1) of F and [h0, h1) of H, written as one
 // FP32 partial per split unit; then the fixed-order sum of gsplits (hsplits)
