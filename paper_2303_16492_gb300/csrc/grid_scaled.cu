@@ -23,10 +23,11 @@
 //       grown by 1e-12 tr(h)/Q * 10^m, m = 0..6 (then TRSGD_ENUMERIC).
 //       Output: every block of L below the diagonal and the inverted
 //       diagonal blocks, each stored as-is and transposed.
-//   grid_scaled_apply_kernel  one warp per row of g (the rows spread over
-//       every SM, at most 16 per CTA), the blocks of L streamed through a
-//       ring of shared-memory stages by bulk copies that one producer warp
-//       issues: the fixed-order sum of the partial gradients, then u L^T = -g
+//   grid_scaled_apply_kernel  two warps per row of g (halves of the terms;
+//       the rows spread over every SM, at most 8 per CTA), the blocks of L
+//       streamed through a ring of shared-memory stages by bulk copies that
+//       one producer warp issues: the fixed-order sum of the partial
+//       gradients, then u L^T = -g
 //       by blocked forward substitution and p L = u by blocked backward
 //       substitution, each 32 x 32 diagonal step a product with the inverted
 //       block; then fixed alpha or AdaGrad and the update, exactly as the
@@ -509,7 +510,7 @@ struct ScaledApplyArgs {
   int *status;
 };
 
-constexpr int kApMaxRows = 16;                 // consumer warps per CTA at most
+constexpr int kApMaxRows = 8;                  // rows of g per CTA at most (two consumer warps each)
 constexpr int kApDepth = 8;                    // staged blocks in flight
 constexpr int kApStage = 2 * kLpl;             // floats per stage: one orientation, hi and lo planes
 constexpr long long kApWait = 1LL << 24;
@@ -544,37 +545,56 @@ struct DAcc4 {
       dacc_fnms(sg * h.w, sg * l.w, u23.z, u23.w, s[3], lo[3]);
     }
   }
+  // the same for the terms t of one half, [16 half, 16 half + 16)
+  template <int SIGN>
+  __device__ __forceinline__ void half_row(const float *xh, const float *xl, const df64 *v, int half) {
+    const float4 *h4 = reinterpret_cast<const float4 *>(xh) + 4 * half;
+    const float4 *l4 = reinterpret_cast<const float4 *>(xl) + 4 * half;
+    const float4 *v4 = reinterpret_cast<const float4 *>(v) + 8 * half;
+#pragma unroll
+    for (int t4 = 0; t4 < kGfB / 8; ++t4) {
+      const float4 h = h4[t4], l = l4[t4], u01 = v4[2 * t4], u23 = v4[2 * t4 + 1];
+      const float sg = SIGN < 0 ? 1.f : -1.f;
+      dacc_fnms(sg * h.x, sg * l.x, u01.x, u01.y, s[0], lo[0]);
+      dacc_fnms(sg * h.y, sg * l.y, u01.z, u01.w, s[1], lo[1]);
+      dacc_fnms(sg * h.z, sg * l.z, u23.x, u23.y, s[2], lo[2]);
+      dacc_fnms(sg * h.w, sg * l.w, u23.z, u23.w, s[3], lo[3]);
+    }
+  }
   __device__ __forceinline__ df64 total() const { return dacc_total(s, lo); }
 };
 
-// One warp per row of g, rows() consumer warps per CTA plus one producer warp
-// whose lane 0 streams the blocks of L through a ring of kApDepth shared
-// stages by bulk copies (TMA engine), each completing on its stage's "full"
-// mbarrier; a consumer warp that is done with a stage arrives on its "empty"
-// mbarrier, which the producer waits on before refilling it.  The sequence of
-// stages: forward (block row b: (b, m), m < b, then the inverted diagonal
-// block), as stored; backward (block column b = nb-1 .. 0: (m, b), m > b,
-// then the inverted diagonal block), transposed.  Every wait is bounded: a
-// timeout latches TRSGD_ETIMEOUT and the stage is waited for once more, so
-// that no copy is left in flight when the CTA exits.
-__global__ void __launch_bounds__(32 * (kApMaxRows + 1), 1) grid_scaled_apply_kernel(const __grid_constant__ ScaledApplyArgs a) {
+// Two warps per row of g (each takes half of the 32 terms of every block
+// product; the halves meet in shared memory at the end of each block row),
+// rows() rows per CTA, plus one producer warp whose lane 0 streams the blocks
+// of L through a ring of kApDepth shared stages by bulk copies (TMA engine),
+// each completing on its stage's "full" mbarrier; a consumer warp that is
+// done with a stage arrives on its "empty" mbarrier, which the producer waits
+// on before refilling it.  The sequence of stages: forward (block row b:
+// (b, m), m < b, then the inverted diagonal block), as stored; backward
+// (block column b = nb-1 .. 0: (m, b), m > b, then the inverted diagonal
+// block), transposed.  Every wait is bounded: a timeout latches
+// TRSGD_ETIMEOUT and the stage is waited for once more, so that no copy is
+// left in flight when the CTA exits.
+__global__ void __launch_bounds__(32 * (2 * kApMaxRows + 1), 1) grid_scaled_apply_kernel(const __grid_constant__ ScaledApplyArgs a) {
   if (!*a.ok) return;   // no factor: the status is latched, G_n stays as it is
   extern __shared__ __align__(128) float aps[];
   __shared__ __align__(8) uint64_t full[kApDepth], empty[kApDepth];
   const int RW = a.rows, nb = a.nb, Q = a.Q, Qp = nb * kGfB;
   float *ring = aps;
   df64 *vecb = reinterpret_cast<df64 *>(aps + kApDepth * kApStage);
+  df64 *cmbb = vecb + (size_t)RW * Qp;   // [RW][32]: the second half's partial sums
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nfw = nb * (nb + 1) / 2, S = 2 * nfw;
   if (tid == 0) {
     for (int k = 0; k < kApDepth; ++k) {
       mbar_init(&full[k], 1);
-      mbar_init(&empty[k], (uint32_t)RW);
+      mbar_init(&empty[k], (uint32_t)(2 * RW));
     }
     fence_mbar_init();
   }
   __syncthreads();
-  if (warp == RW) {   // producer
+  if (warp == 2 * RW) {   // producer
     if (lane == 0) {
       int b = 0, m = 0;   // block of stage s: forward row b, column m (m == b: diagonal)
       for (int s = 0; s < S; ++s) {
@@ -610,18 +630,22 @@ __global__ void __launch_bounds__(32 * (kApMaxRows + 1), 1) grid_scaled_apply_ke
     }
     return;
   }
-  df64 *v = vecb + (size_t)warp * Qp;
-  const int row = blockIdx.x * RW + warp;
+  const int pr = warp >> 1, half = warp & 1;   // row of the CTA, half of the terms
+  df64 *v = vecb + (size_t)pr * Qp;
+  df64 *cmb = cmbb + (size_t)pr * kGfB;
+  const int row = blockIdx.x * RW + pr;
   const bool live = row < a.In;
-  // -g of this warp's row (the plain update's fixed-order sum of the partials)
-  for (int q = lane; q < Qp; q += 32) {
+  // the two warps of a row meet at a named barrier of their own (id 1 + pr)
+  auto pair_sync = [&]() { asm volatile("bar.sync %0, 64;" ::"r"(1 + pr) : "memory"); };
+  // -g of this row (the plain update's fixed-order sum of the partials)
+  for (int q = lane + 32 * half; q < Qp; q += 64) {
     float g = 0.f;
     if (live && q < Q)
       for (int z = 0; z < a.splits; ++z) g += __ldcg(a.gpart + z * a.cstride + (long long)row * Q + q);
     v[q] = df64{-g, 0.f};
     if (live && q < Q && a.dbg_g) a.dbg_g[(long long)row * Q + q] = g;
   }
-  __syncwarp();
+  pair_sync();
   int s = 0;
   auto acquire = [&]() -> const float * {
     const int slot = s % kApDepth;
@@ -637,50 +661,51 @@ __global__ void __launch_bounds__(32 * (kApMaxRows + 1), 1) grid_scaled_apply_ke
     if (lane == 0) ap_arrive(&empty[s % kApDepth]);
     ++s;
   };
+  // the row's two halves of an entry summed into v[i] (the first half's warp
+  // adds the second's, read after the pair barrier), visible to both after
+  // the second barrier
+  auto combine_into = [&](int i, df64 part) {
+    if (half) cmb[lane] = part;
+    pair_sync();
+    if (!half) v[i] = df_add(part, cmb[lane]);
+    pair_sync();
+  };
   DAcc4 acc;
   // forward: u L^T = -g; block row b: r = -g_b - sum_{m<b} C_bm u_m, u_b = L_bb^{-1} r
   for (int b = 0; b < nb; ++b) {
-    acc.reset(v[b * kGfB + lane]);
+    acc.reset(half == 0 ? v[b * kGfB + lane] : df64{0.f, 0.f});
     for (int m = 0; m < b; ++m) {
       const float *X = acquire();
-      acc.row<-1>(X, X + kLpl, v + m * kGfB);
+      acc.half_row<-1>(X, X + kLpl, v + m * kGfB, half);
       release();
     }
-    const df64 r = acc.total();
-    __syncwarp();
-    v[b * kGfB + lane] = r;
-    __syncwarp();
+    combine_into(b * kGfB + lane, acc.total());
     const float *X = acquire();
     acc.reset(df64{0.f, 0.f});
-    acc.row<1>(X, X + kLpl, v + b * kGfB);   // the inverse is lower triangular: zeros above the diagonal
+    acc.half_row<1>(X, X + kLpl, v + b * kGfB, half);   // the inverse is lower triangular: zeros above the diagonal
     const df64 u = acc.total();
     release();
-    v[b * kGfB + lane] = u;
-    __syncwarp();
+    combine_into(b * kGfB + lane, u);
   }
   // backward: p L = u; block column b: s = u_b - sum_{m>b} C_mb^T p_m, p_b = L_bb^{-T} s
   for (int b = nb - 1; b >= 0; --b) {
-    acc.reset(v[b * kGfB + lane]);
+    acc.reset(half == 0 ? v[b * kGfB + lane] : df64{0.f, 0.f});
     for (int m = nb - 1; m > b; --m) {
       const float *X = acquire();
-      acc.row<-1>(X, X + kLpl, v + m * kGfB);
+      acc.half_row<-1>(X, X + kLpl, v + m * kGfB, half);
       release();
     }
-    const df64 r = acc.total();
-    __syncwarp();
-    v[b * kGfB + lane] = r;
-    __syncwarp();
+    combine_into(b * kGfB + lane, acc.total());
     const float *X = acquire();
     acc.reset(df64{0.f, 0.f});
-    acc.row<1>(X, X + kLpl, v + b * kGfB);
+    acc.half_row<1>(X, X + kLpl, v + b * kGfB, half);
     const df64 p = acc.total();
     release();
-    v[b * kGfB + lane] = p;
-    __syncwarp();
+    combine_into(b * kGfB + lane, p);
   }
   if (!live) return;
   // step rule and update (as the plain update kernel, with this p)
-  for (int q = lane; q < Q; q += 32) {
+  for (int q = lane + 32 * half; q < Q; q += 64) {
     const df64 pd = v[q];
     const float p = pd.hi + pd.lo;
     const long long e = (long long)row * Q + q;
@@ -714,7 +739,7 @@ cudaError_t grid_scaled_prepare() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(grid_scaled_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)((size_t)kApDepth * kApStage * sizeof(float) +
-                                   (size_t)kApMaxRows * kGridScaledMaxQ * sizeof(df64)));
+                                   (size_t)kApMaxRows * (kGridScaledMaxQ + kGfB) * sizeof(df64)));
   return e;
 }
 
@@ -773,8 +798,9 @@ cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
   // rows per CTA: the rows spread over every SM (one CTA each) where they allow
   const int sms = s.sms > 0 ? s.sms : 1;
   aa.rows = std::min(kApMaxRows, std::max(1, (s.In + sms - 1) / sms));
-  const size_t smem = (size_t)kApDepth * kApStage * sizeof(float) + (size_t)aa.rows * nb * kGfB * sizeof(df64);
-  grid_scaled_apply_kernel<<<(s.In + aa.rows - 1) / aa.rows, 32 * (aa.rows + 1), smem, st>>>(aa);
+  const size_t smem =
+      (size_t)kApDepth * kApStage * sizeof(float) + (size_t)aa.rows * (nb * kGfB + kGfB) * sizeof(df64);
+  grid_scaled_apply_kernel<<<(s.In + aa.rows - 1) / aa.rows, 32 * (2 * aa.rows + 1), smem, st>>>(aa);
   return cudaGetLastError();
 }
 
