@@ -373,6 +373,18 @@ const char *trsgd_status_string(trsgd_status s) {
   return "unknown status";
 }
 
+// the whole-GPU path's second stream and its events
+static void release_grid_streams(trsgd_handle *h) {
+  if (h->gp.s2) {
+    cudaStreamSynchronize(h->gp.s2);
+    cudaStreamDestroy(h->gp.s2);
+    h->gp.s2 = nullptr;
+  }
+  if (h->gp.ev_fork) cudaEventDestroy(h->gp.ev_fork);
+  if (h->gp.ev_join) cudaEventDestroy(h->gp.ev_join);
+  h->gp.ev_fork = h->gp.ev_join = nullptr;
+}
+
 // The descriptors in launch order: batched problems are stepped by one
 // cluster each, in order of decreasing work (sum over the modes of
 // I_n R_n R_{n+1} |F|), so that when the clusters run in waves the largest
@@ -425,6 +437,7 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
     for (int k = 0; k < cfg[p].N; ++k) rmax = std::max<int>(rmax, (int)cfg[p].R[k]);
   h->rmax = rmax;
   auto fail = [&](trsgd_status s) {
+    release_grid_streams(h);
     delete h;
     return s;
   };
@@ -601,6 +614,10 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
           (e = h->buf.alloc((void **)&g.Lfac, grid_scaled_factor_floats(qmax) * 4)) == cudaSuccess &&
           (e = h->buf.alloc((void **)&g.fac_ok, 16)) == cudaSuccess)
         e = grid_scaled_prepare();
+      // the factorisation's own stream (beside the GEMMs of the same iteration)
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.s2, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.ev_fork, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.ev_join, cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = grid_prepare_gemm();
     if (e == cudaSuccess) e = grid_tensor_maps(Ri, c.N, g);
@@ -1043,7 +1060,8 @@ trsgd_status trsgd_step_partial(trsgd_handle *h, int64_t t, const trsgd_shard *p
   if (plan->mode != n || (g.scaled && !hpart_dev)) return TRSGD_EINVAL;
   if (plan->gsplits > plan->gsplits_max || plan->hsplits > plan->hsplits_max) return TRSGD_EINVAL;
   cudaError_t e = launch_grid_partial(g, D, n, t, plan->j0, plan->j1, g.JH > 0 ? plan->h0 : 0,
-                                      g.JH > 0 ? plan->h1 : 0, h->dbg ? 1 : 0, gpart_dev, hpart_dev, h->stream);
+                                      g.JH > 0 ? plan->h1 : 0, h->dbg ? 1 : 0, gpart_dev, hpart_dev, h->stream,
+                                      nullptr);
   if (e == cudaErrorInvalidValue) return TRSGD_EINVAL;
   // zero partials up to the common count, so that a gather of every rank's
   // buffer sums to the same values
@@ -1140,6 +1158,7 @@ int32_t trsgd_tensor_pieces(const trsgd_handle *h) {
 void trsgd_destroy(trsgd_handle *h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  release_grid_streams(h);
   delete h;
 }
 

@@ -822,9 +822,42 @@ static cudaError_t launch_gram(const GridPath &g, int Q, long long j0, long long
   return cudaGetLastError();
 }
 
+// the scaled variant's factorisation and direction for mode n, from the
+// given partial gradients and Grams
+static GridScaledArgs grid_scaled_args(const GridPath &g, const ProbDesc &D, int n, const float *gparts, int gsplits,
+                                       const float *hparts, int hsplits, int rec) {
+  const int N = D.N, In = D.I[n], Q = D.R[n] * D.R[(n + 1) % N];
+  GridScaledArgs sa = {};
+  sa.hpart = hparts;
+  sa.hstride = (long long)Q * Q;
+  sa.hsplits = hsplits;
+  sa.gpart = gparts;
+  sa.gstride = (long long)In * Q;
+  sa.gsplits = gsplits;
+  sa.In = In;
+  sa.Q = Q;
+  sa.sms = g.sms;
+  sa.hscale = 1.0 / (double)(g.JH > 0 ? g.JH : D.J);
+  sa.damping = D.damping;
+  sa.Lfac = g.Lfac;
+  sa.ok = g.fac_ok;
+  sa.rule = D.rule;
+  sa.alpha = (float)D.alpha;
+  sa.eta = (float)D.eta;
+  sa.b = (float)D.b;
+  sa.eps = D.eps;
+  sa.G = static_cast<float *>(D.cores[n]);
+  sa.acc = static_cast<float *>(D.acc[n]);
+  sa.dbg_g = rec ? static_cast<float *>(D.dbg_g) : nullptr;
+  sa.dbg_p = rec ? static_cast<float *>(D.dbg_p) : nullptr;
+  sa.dbg_h = rec ? D.dbg_h : nullptr;
+  sa.status = D.status;
+  return sa;
+}
+
 cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, long long t, long long j0,
                                 long long j1, long long h0, long long h1, int rec, float *gout, float *hout,
-                                cudaStream_t s) {
+                                cudaStream_t s, const GridScaledArgs *fork_factor) {
   NvtxRange r("grid partial sums (G pieces, samples, tcgen05 GEMMs)");
   const int N = D.N, In = D.I[n], Q = D.R[n] * D.R[(n + 1) % N];
   const int Ip = (In + 127) / 128 * 128, Qp = (Q + 63) / 64 * 64;
@@ -844,6 +877,18 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
   }
   // 2. samples of F and Z (and Z^T)
   if (fpart && (e = launch_samples(g, D, n, t, j0, j1, kStreamF, rec, s)) != cudaSuccess) return e;
+  // scaled variant with H = F: the partial Grams first; the factorisation may
+  // then run on the second stream beside the residual and gradient GEMMs
+  if (g.scaled && g.JH == 0 && fpart) {
+    if ((e = launch_gram(g, Q, j0, j1, grid_gram_unit(g, D, n, D.J), n, hout, D.status, rec, s)) != cudaSuccess)
+      return e;
+    if (fork_factor) {
+      if ((e = cudaEventRecord(g.ev_fork, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(g.s2, g.ev_fork, 0)) != cudaSuccess) return e;
+      if ((e = launch_grid_factor(*fork_factor, g.s2)) != cudaSuccess) return e;
+      if ((e = cudaEventRecord(g.ev_join, g.s2)) != cudaSuccess) return e;
+    }
+  }
   const int maxord = np == 1 ? 0 : 2;
   // 3. residual: E = G_n Z^T - X_S (M = Ip, N = the samples of the range, K = Qp), weighted, as pieces
   if (fpart) {
@@ -922,9 +967,6 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
         if ((e = launch_samples(g, D, n, t, h0, h1, kStreamH, 0, s)) != cudaSuccess) return e;
         if ((e = launch_gram(g, Q, h0, h1, uh, n, hout, D.status, rec, s)) != cudaSuccess) return e;
       }
-    } else if (fpart && (e = launch_gram(g, Q, j0, j1, grid_gram_unit(g, D, n, D.J), n, hout, D.status, rec, s)) !=
-                            cudaSuccess) {
-      return e;
     }
   }
   return cudaSuccess;
@@ -934,34 +976,7 @@ cudaError_t launch_grid_apply(const GridPath &g, const ProbDesc &D, int n, const
                               const float *hparts, int hsplits, int rec, cudaStream_t s) {
   NvtxRange r("grid apply (sum of the partials, direction, step rule, update)");
   const int N = D.N, In = D.I[n], Q = D.R[n] * D.R[(n + 1) % N];
-  if (g.scaled) {
-    GridScaledArgs sa = {};
-    sa.hpart = hparts;
-    sa.hstride = (long long)Q * Q;
-    sa.hsplits = hsplits;
-    sa.gpart = gparts;
-    sa.gstride = (long long)In * Q;
-    sa.gsplits = gsplits;
-    sa.In = In;
-    sa.Q = Q;
-    sa.sms = g.sms;
-    sa.hscale = 1.0 / (double)(g.JH > 0 ? g.JH : D.J);
-    sa.damping = D.damping;
-    sa.Lfac = g.Lfac;
-    sa.ok = g.fac_ok;
-    sa.rule = D.rule;
-    sa.alpha = (float)D.alpha;
-    sa.eta = (float)D.eta;
-    sa.b = (float)D.b;
-    sa.eps = D.eps;
-    sa.G = static_cast<float *>(D.cores[n]);
-    sa.acc = static_cast<float *>(D.acc[n]);
-    sa.dbg_g = rec ? static_cast<float *>(D.dbg_g) : nullptr;
-    sa.dbg_p = rec ? static_cast<float *>(D.dbg_p) : nullptr;
-    sa.dbg_h = rec ? D.dbg_h : nullptr;
-    sa.status = D.status;
-    return launch_grid_scaled(sa, s);
-  }
+  if (g.scaled) return launch_grid_scaled(grid_scaled_args(g, D, n, gparts, gsplits, hparts, hsplits, rec), s);
   GridUpdateArgs ua = {};
   ua.gpart = gparts;
   ua.cstride = (long long)In * Q;
@@ -1018,7 +1033,14 @@ cudaError_t launch_grid_step(const GridPath &g, const ProbDesc &D, int n, long l
   const long long JH = g.JH > 0 ? g.JH : D.J;
   const int gs = nsplits(0, D.J, grid_split_unit(g, D, n, D.J));
   const int hs = g.scaled ? nsplits(0, JH, grid_gram_unit(g, D, n, JH)) : 0;
-  cudaError_t e = launch_grid_partial(g, D, n, t, 0, D.J, 0, g.JH, rec, g.gpart, g.hpart, s);
+  if (g.scaled && g.JH == 0 && g.s2) {   // the factorisation beside the residual and gradient GEMMs
+    const GridScaledArgs sa = grid_scaled_args(g, D, n, g.gpart, gs, g.hpart, hs, rec);
+    cudaError_t e = launch_grid_partial(g, D, n, t, 0, D.J, 0, 0, rec, g.gpart, g.hpart, s, &sa);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, g.ev_join, 0);
+    if (e == cudaSuccess) e = launch_grid_direction(sa, s);
+    return e;
+  }
+  cudaError_t e = launch_grid_partial(g, D, n, t, 0, D.J, 0, g.JH, rec, g.gpart, g.hpart, s, nullptr);
   if (e == cudaSuccess) e = launch_grid_apply(g, D, n, g.gpart, gs, g.hpart, hs, rec, s);
   return e;
 }

@@ -743,7 +743,7 @@ cudaError_t grid_scaled_prepare() {
   return e;
 }
 
-cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
+cudaError_t launch_grid_factor(const GridScaledArgs &s, cudaStream_t st) {
   const int nb = (s.Q + kGfB - 1) / kGfB;
   if (s.Q < 1 || s.Q > kGridScaledMaxQ) return cudaErrorInvalidValue;
   {
@@ -772,9 +772,13 @@ cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaError_t e = cudaLaunchKernelEx(&cfg, grid_gram_factor_kernel, fa);
-    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, grid_gram_factor_kernel, fa);
   }
+}
+
+cudaError_t launch_grid_direction(const GridScaledArgs &s, cudaStream_t st) {
+  const int nb = (s.Q + kGfB - 1) / kGfB;
+  if (s.Q < 1 || s.Q > kGridScaledMaxQ) return cudaErrorInvalidValue;
   NvtxRange r("grid_scaled_apply_kernel");
   ScaledApplyArgs aa = {};
   aa.gpart = s.gpart;
@@ -802,6 +806,11 @@ cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
       (size_t)kApDepth * kApStage * sizeof(float) + (size_t)aa.rows * (nb * kGfB + kGfB) * sizeof(df64);
   grid_scaled_apply_kernel<<<(s.In + aa.rows - 1) / aa.rows, 32 * (2 * aa.rows + 1), smem, st>>>(aa);
   return cudaGetLastError();
+}
+
+cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st) {
+  cudaError_t e = launch_grid_factor(s, st);
+  return e == cudaSuccess ? launch_grid_direction(s, st) : e;
 }
 
 }  // namespace trsgd

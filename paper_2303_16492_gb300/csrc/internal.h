@@ -98,6 +98,10 @@ struct OptBuffers {
 // map (boxes of 64 K-elements, 128-byte swizzle); Z^T's box height depends on
 // the mode, so it has one map per mode.
 struct GridPath {
+  // scaled variant, H = F: a second stream on which the Gram factorisation
+  // (one cluster of 16 SMs) runs beside the residual and gradient GEMMs
+  cudaStream_t s2;
+  cudaEvent_t ev_fork, ev_join;
   int np;                  // BF16 pieces per operand of the residual and gradient GEMMs (1 or 3)
   int npz;                 // pieces of Z kept (3 for the scaled variant: its Gram is formed from three)
   int scaled;              // scaled variant (Sec. 3.3)
@@ -159,6 +163,8 @@ struct GridScaledArgs {
 size_t grid_scaled_factor_floats(int Q);
 cudaError_t grid_scaled_prepare();
 cudaError_t launch_grid_scaled(const GridScaledArgs &s, cudaStream_t st);
+cudaError_t launch_grid_factor(const GridScaledArgs &s, cudaStream_t st);
+cudaError_t launch_grid_direction(const GridScaledArgs &s, cudaStream_t st);
 
 // kernel launchers (defined in the .cu files)
 void grid_layout(const int *I, const int *R, int N, int J, int np, int scaled, int JH, GridPath &g);
@@ -177,7 +183,7 @@ long long grid_gram_unit(const GridPath &g, const ProbDesc &D, int n, long long 
 // partials, the direction, the step rule and the update of G_n.
 cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, long long t, long long j0,
                                 long long j1, long long h0, long long h1, int rec, float *gout, float *hout,
-                                cudaStream_t s);
+                                cudaStream_t s, const GridScaledArgs *fork_factor);
 cudaError_t launch_grid_apply(const GridPath &g, const ProbDesc &D, int n, const float *gparts, int gsplits,
                               const float *hparts, int hsplits, int rec, cudaStream_t s);
 cudaError_t launch_optimal_sampling(int core_dtype, int x_dtype, int N, int n, const int *I, const int *R,
