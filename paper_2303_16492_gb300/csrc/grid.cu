@@ -867,15 +867,7 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
   if (j0 < 0 || j1 > D.J || j0 > j1 || (j0 % unit) != 0 || ((j1 % unit) != 0 && j1 != D.J))
     return cudaErrorInvalidValue;
   const bool fpart = j1 > j0;   // a rank may hold no sample of F but some of H
-  // 1. operand pieces of G_n
-  if (fpart) {
-    const long long total = (long long)Ip * Qp;
-    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
-    grid_prepare_kernel<<<blocks, 256, 0, s>>>(static_cast<const float *>(D.cores[n]), In, Q, Ip, Qp, g.ldg, np,
-                                               g.Gp[0], g.Gp[1], g.Gp[2]);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  // 2. samples of F and Z (and Z^T)
+  // 1. samples of F and Z (and Z^T)
   if (fpart && (e = launch_samples(g, D, n, t, j0, j1, kStreamF, rec, s)) != cudaSuccess) return e;
   // scaled variant with H = F: the partial Grams first; the factorisation may
   // then run on the second stream beside the residual and gradient GEMMs
@@ -888,6 +880,14 @@ cudaError_t launch_grid_partial(const GridPath &g, const ProbDesc &D, int n, lon
       if ((e = launch_grid_factor(*fork_factor, g.s2)) != cudaSuccess) return e;
       if ((e = cudaEventRecord(g.ev_join, g.s2)) != cudaSuccess) return e;
     }
+  }
+  // 2. operand pieces of G_n (after the fork: the factorisation does not wait for them)
+  if (fpart) {
+    const long long total = (long long)Ip * Qp;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 4096);
+    grid_prepare_kernel<<<blocks, 256, 0, s>>>(static_cast<const float *>(D.cores[n]), In, Q, Ip, Qp, g.ldg, np,
+                                               g.Gp[0], g.Gp[1], g.Gp[2]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   const int maxord = np == 1 ? 0 : 2;
   // 3. residual: E = G_n Z^T - X_S (M = Ip, N = the samples of the range, K = Qp), weighted, as pieces
