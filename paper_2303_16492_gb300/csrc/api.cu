@@ -200,7 +200,7 @@ static bool make_layout_p(const trsgd_handle &h, int C, int tcp, bool tab, StepL
     off += bytes;
     return o;
   };
-  L.off_bar = take(16, 16);
+  L.off_bar = take(32, 16);   // fibers, MMA completion, G_n pieces
   L.off_misc = take(64, 16);
   L.off_const = take(32 * 8, 16);
   L.off_ord = take(3 * kMaxOrder * 4, 16);   // chain order, staged-slice offsets and pitches
@@ -579,6 +579,20 @@ trsgd_status trsgd_init(const trsgd_config *cfg, int32_t nproblems, const void *
     st = choose_layout(*h, default_cluster(*h));
     if (st == TRSGD_EUNSUPPORTED && cfg[0].path == TRSGD_PATH_AUTO && grid_fits(cfg, nproblems)) h->grid = true;
     else if (st != TRSGD_OK) return fail(st);
+  }
+  // FP32 cores of plain problems: room for the BF16 pieces of every core in the
+  // tensor-core operand tile layout (used by the launches that take the
+  // tensor-core step; the layout's qp does not change with the cluster size)
+  if (!h->grid && h->core_dtype == 1 && h->lay.qp <= 256) {
+    for (int p = 0; p < nproblems; ++p) {
+      ProbDesc &D = h->hdesc[p];
+      if (cfg[p].variant == TRSGD_SCALED) continue;
+      for (int k = 0; k < cfg[p].N; ++k) {
+        const size_t b = (size_t)((cfg[p].I[k] + 127) / 128) * 3 * 128 * h->lay.qp * 2;
+        if ((e = h->buf.alloc(&D.gpc[k], b)) != cudaSuccess) return fail(from_cuda(e));
+        cudaMemsetAsync(D.gpc[k], 0, b, h->stream);
+      }
+    }
   }
   if (h->grid) {
     const trsgd_config &c = cfg[0];

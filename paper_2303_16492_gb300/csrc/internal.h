@@ -20,6 +20,11 @@ struct ProbDesc {
   const void *xmode[8];           // mode-major copies: fiber col of X_[k] at xmode[k] + col*ldx[k]
   long long ldx[8];               // row stride of xmode[k] in elements (16-byte multiple)
   void *acc[8];                   // AdaGrad sums (core dtype), or null
+  // FP32 cores on the tensor-core path, plain variant: core k as BF16 pieces in
+  // the operand tile layout (per chunk of 128 rows, per piece, a no-swizzle
+  // K-major 128 x qp tile; 3 pieces of room), rebuilt by every launch and kept
+  // current by the update; null: G_n is converted per chunk instead
+  void *gpc[8];
   double *prob[8];                // p_k (non-uniform distributions)
   unsigned long long *cdf[8];     // inclusive prefix sums of round(p_k * 2^52)
   double *snorm[8];               // Euclidean slice norms ||G_k(i)||_F^2

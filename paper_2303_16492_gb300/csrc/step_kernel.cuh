@@ -92,6 +92,35 @@ __device__ __forceinline__ void bf16_split8(const float (&v)[8], uint4 (&w)[PA])
   for (int k = 0; k < P; ++k) w[k] = make_uint4(u[k][0], u[k][1], u[k][2], u[k][3]);
 }
 
+// The same split for four consecutive values (8 bytes per piece) and for one
+// value (2 bytes per piece).
+template <int P>
+__device__ __forceinline__ void bf16_split4(const float (&v)[4], uint2 (&w)[P]) {
+  uint32_t u[P][2];
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    float a = v[2 * j], b = v[2 * j + 1];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+      const float2 hf = __bfloat1622float2(h);
+      a -= hf.x;
+      b -= hf.y;
+      u[k][j] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < P; ++k) w[k] = make_uint2(u[k][0], u[k][1]);
+}
+template <int P>
+__device__ __forceinline__ void bf16_split1(float a, __nv_bfloat16 (&w)[P]) {
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    w[k] = __float2bfloat16_rn(a);
+    a -= __bfloat162float(w[k]);
+  }
+}
+
 // Commit this thread's outstanding cp.async copies as one group; wait until at
 // most n of its most recent groups are still in flight (n >= 6: 6).
 __device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -277,6 +306,7 @@ __global__ void __launch_bounds__(kMaxThreads)
   if (tid == 0) {
     mbar_init(bar, 1);
     mbar_init(bar_mma, 1);
+    mbar_init(bar + 2, 1);
     fence_mbar_init();
   }
   if constexpr (kTC) {
@@ -314,6 +344,45 @@ __global__ void __launch_bounds__(kMaxThreads)
   __syncthreads();
   const T wt_uni = (T)cst[16];
   uint32_t phase = 0;
+
+  // Plain variant on the tensor cores: every core is kept in global memory as
+  // its NPC BF16 pieces, in the residual's operand tile layout (per chunk of
+  // 128 rows and per piece one K-major 128 x qp tile), so that a chunk's G_n
+  // operand arrives by bulk copies instead of being converted every step.  The
+  // pieces are rebuilt here, at the start of every launch (the cores may have
+  // changed between launches), and the owners of the updated rows rewrite
+  // theirs with the update.
+  const bool gbulk = kTC && !scaled && D.gpc[0] != nullptr;
+  uint64_t *bar_g = bar + 2;
+  uint32_t gphase = 0;
+  const size_t gcs = (size_t)lay.qp * 256;   // bytes of one piece of one chunk (128 x qp BF16)
+  if constexpr (kTC) {
+    if (gbulk) {
+      const int QC = lay.qp / 8;
+      for (int k = 0; k < N; ++k) {
+        const int Qk = R[k] * R[(k + 1) % N], Ik = I[k];
+        const float *G = static_cast<const float *>(D.cores[k]);
+        unsigned char *dst = static_cast<unsigned char *>(D.gpc[k]);
+        // 8 consecutive threads: the 8 rows of one 128-byte core matrix
+        for (int e = c * NT + tid; e < ((Ik + 7) & ~7) * QC; e += C * NT) {
+          const int rest = e >> 3, qb = rest % QC, i = (rest / QC) * 8 + (e & 7);
+          float v[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int q = qb * 8 + j;
+            v[j] = (i < Ik && q < Qk) ? __ldcg(G + (size_t)i * Qk + q) : 0.f;
+          }
+          uint4 w[NPC > 0 ? NPC : 1];
+          bf16_split8<NPC>(v, w);
+          unsigned char *o = dst + (size_t)(i >> 7) * NPC * gcs + kmaj_off(i & 127, qb * 8, QC);
+#pragma unroll
+          for (int p = 0; p < NPC; ++p) *reinterpret_cast<uint4 *>(o + p * gcs) = w[p];
+        }
+      }
+      fence_proxy_async_global();
+      cluster.sync();
+    }
+  }
 
   // sum of one element of a shared-memory buffer over the cluster's CTAs in
   // fixed CTA order 0..C-1 (deterministic); the C remote loads are issued together
@@ -523,6 +592,42 @@ __global__ void __launch_bounds__(kMaxThreads)
     }
   };
 
+  // The G_n pieces of the chunk of ti rows at row i0 into its operand tiles by
+  // NPC bulk copies completing on bar_g (only the core-matrix rows that hold
+  // rows of the chunk), and the FP32 rows [r0, r1) of the chunk this CTA
+  // updates into gown (16-byte asynchronous copies, waited for before the
+  // residual).  The operand tiles alias the staged slices and the chain
+  // buffers: called once those are dead.
+  auto g_issue = [&](int ti, int i0) {
+    if constexpr (kTC) {
+      const int n = cur_n, Q = cur_Q;
+      const float *Gn = static_cast<const float *>(D.cores[n]);
+      const int QC = lay.qp / 8;
+      const uint32_t bytes = (uint32_t)(((ti + 7) & ~7) >> 3) * (uint32_t)QC * 128u;
+      if (tid == 0) {
+        fence_proxy_async_smem();   // earlier generic accesses of the region come first
+        mbar_arrive_expect_tx(bar_g, (uint32_t)NPC * bytes);
+        const unsigned char *src = static_cast<const unsigned char *>(D.gpc[n]) + (size_t)(i0 >> 7) * NPC * gcs;
+#pragma unroll
+        for (int p = 0; p < NPC; ++p) tma_load_1d(smem + lay.off_reg + p * gcs, src + p * gcs, bytes, bar_g);
+      }
+      const int r0 = ti * c / C, r1 = ti * (c + 1) / C;
+      float *own = reinterpret_cast<float *>(gown);
+      if ((Q & 3) == 0 && ((D.slice_tma >> n) & 1)) {
+        const int nch = Q >> 2;
+        for (int e = tid; e < (r1 - r0) * nch; e += NT) {
+          const int ii = e / nch, ch = e - ii * nch;
+          cp_async16(own + (size_t)ii * ldq + 4 * ch, Gn + (size_t)(i0 + r0 + ii) * Q + 4 * ch);
+        }
+      } else {
+        for (int e = tid; e < (r1 - r0) * Q; e += NT) {
+          const int ii = e / Q, q = e - ii * Q;
+          own[(size_t)ii * ldq + q] = __ldcg(Gn + (size_t)(i0 + r0 + ii) * Q + q);
+        }
+      }
+    }
+  };
+
   // Tensor-core residual and partial gradient of one chunk of <= 128 rows of
   // G_n (operands as NPC BF16 pieces, FP32 accumulation in TMEM):
   //   D_R(i, jl) = G(i, :) Z(jl, :)^T  as the piece products of total order
@@ -553,7 +658,16 @@ __global__ void __launch_bounds__(kMaxThreads)
       // products depends on row i of G (and of Ew) only, and rows >= ti of the
       // results are never read
       const int ti8 = (ti + 7) & ~7;
-      for (int e = tid; e < ti8 * QC; e += NT) {
+      if (gbulk) {
+        if (i0 > 0) g_issue(ti, i0);   // the first chunk's copies were issued beside the Z pieces
+        cp_async_wait_all();           // the owned rows
+        if (!mbar_wait_bounded(bar_g, gphase, wlim)) {
+          latch_status(D.status, kStatusTimeout);
+          mbar_wait_bounded(bar_g, gphase, kWaitLimit);
+        }
+        gphase ^= 1u;
+      }
+      for (int e = tid; !gbulk && e < ti8 * QC; e += NT) {
         // 8 consecutive threads: the 8 rows of one core matrix, so that each
         // piece store of a warp covers 512 contiguous bytes (no bank conflicts)
         const int rest = e >> 3, qb = rest % QC, ii = (rest / QC) * 8 + (e & 7);
@@ -837,6 +951,7 @@ __global__ void __launch_bounds__(kMaxThreads)
       for (int e = tid; e < jb * (Q4 - Q); e += NT) zs[(size_t)(e / (Q4 - Q)) * ldq + Q + e % (Q4 - Q)] = T(0);
     for (int e = tid; e < (jb4 - jb) * Q4; e += NT) zs[(size_t)(jb + e / Q4) * ldq + e % Q4] = T(0);
     __syncthreads();
+    if (gbulk && c >= lay.cw0) g_issue(min(lay.TI, In), 0);   // lands while the Z pieces are formed
     if constexpr (kTC) {
       // Z as NPC BF16 pieces in the no-swizzle K-major tiles [JBP rows jl][QP cols q]
       const int QC = lay.qp / 8;
@@ -1003,6 +1118,11 @@ __global__ void __launch_bounds__(kMaxThreads)
       pf_t = (pipe && i0 + ti >= In && s + 1 < nsteps) ? t + 1 : -1;
       if (c < lay.cw0) {   // no samples on this CTA: a zero partial gradient
         for (int e = tid; e < ti * Q; e += NT) reg[(size_t)(e / Q) * ldq + e % Q] = T(0);
+        if (kTC && !scaled) {   // a plain problem beside scaled ones: the update reads its rows from gown
+          const int r0 = ti * c / C, r1 = ti * (c + 1) / C;
+          for (int e = tid; e < (r1 - r0) * Q; e += NT)
+            gown[(size_t)(e / Q) * ldq + e % Q] = ld_l2(Gn + (size_t)(i0 + r0 + e / Q) * Q + e % Q);
+        }
       } else {
         if constexpr (kTC) {
           tc_chunk(ti, i0);
@@ -1061,21 +1181,45 @@ __global__ void __launch_bounds__(kMaxThreads)
       }
       pf_t = -1;
       const int r0 = ti * c / C, r1 = ti * (c + 1) / C;
-      // reduced gradient of one owned entry -> step rule and update (or kept for the solve)
-      auto own_entry = [&](int ii, int q, T g) {
+      // reduced gradient of one owned entry -> step rule and update (or kept for
+      // the solve); returns the updated entry (plain variant)
+      auto own_entry = [&](int ii, int q, T g) -> T {
         const size_t gi = (size_t)(i0 + ii) * Q + q;
         if (rec) static_cast<T *>(D.dbg_g)[gi] = g;
         if (scaled) {
           gown[(size_t)(own_rows + ii - r0) * ldq + q] = g;
-        } else {
-          const T p = -g;
-          T *own = gown + (size_t)(ii - r0) * ldq + q;
-          const T cur = kTC ? *own : ld_l2(Gn + gi);   // the tensor-core chunk kept the owned rows
-          const T nv = cur + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
-          if (!isfinite(nv)) latch_status(D.status, kStatusNumeric);
-          Gn[gi] = nv;
-          *own = nv;
-          if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
+          return g;
+        }
+        const T p = -g;
+        T *own = gown + (size_t)(ii - r0) * ldq + q;
+        const T cur = kTC ? *own : ld_l2(Gn + gi);   // the tensor-core chunk kept the owned rows
+        const T nv = cur + step_delta<T>(D.rule, alpha_t, eta_t, b_t, D.eps, accn, gi, p);
+        if (!isfinite(nv)) latch_status(D.status, kStatusNumeric);
+        Gn[gi] = nv;
+        *own = nv;
+        if (rec) static_cast<T *>(D.dbg_p)[gi] = p;
+        return nv;
+      };
+      // the pieces of updated entries (q0, 4 values / q, one value) of row ii of
+      // the chunk in the global piece tiles of core n
+      unsigned char *gpn = gbulk ? static_cast<unsigned char *>(D.gpc[n]) + (size_t)(i0 >> 7) * NPC * gcs : nullptr;
+      auto put_pieces4 = [&](int ii, int q0, float v0, float v1, float v2, float v3) {
+        if constexpr (kTC) {
+          const float v[4] = {v0, v1, v2, v3};
+          uint2 w[NPC > 0 ? NPC : 1];
+          bf16_split4<NPC>(v, w);
+          unsigned char *o = gpn + kmaj_off(ii, q0, lay.qp / 8);
+#pragma unroll
+          for (int p = 0; p < NPC; ++p) *reinterpret_cast<uint2 *>(o + p * gcs) = w[p];
+        }
+      };
+      auto put_piece1 = [&](int ii, int q, T v) {
+        if constexpr (kTC) {
+          __nv_bfloat16 w[NPC > 0 ? NPC : 1];
+          bf16_split1<NPC>((float)v, w);
+          unsigned char *o = gpn + kmaj_off(ii, q, lay.qp / 8);
+#pragma unroll
+          for (int p = 0; p < NPC; ++p) *reinterpret_cast<__nv_bfloat16 *>(o + p * gcs) = w[p];
         }
       };
       if constexpr (sizeof(T) == 4) {
@@ -1102,15 +1246,15 @@ __global__ void __launch_bounds__(kMaxThreads)
                 g.z += v[u].z;
                 g.w += v[u].w;
               }
-            own_entry(ii, q0, g.x);
-            own_entry(ii, q0 + 1, g.y);
-            own_entry(ii, q0 + 2, g.z);
-            own_entry(ii, q0 + 3, g.w);
+            const float n0 = own_entry(ii, q0, g.x), n1 = own_entry(ii, q0 + 1, g.y);
+            const float n2 = own_entry(ii, q0 + 2, g.z), n3 = own_entry(ii, q0 + 3, g.w);
+            if (gbulk) put_pieces4(ii, q0, n0, n1, n2, n3);
           }
         } else {
           for (int e = tid; tid < rt && e < (r1 - r0) * Q; e += rt) {
             const int ii = r0 + e / Q, q = e % Q;
-            own_entry(ii, q, cluster_sum(reg, (size_t)ii * ldq + q));
+            const T nv = own_entry(ii, q, cluster_sum(reg, (size_t)ii * ldq + q));
+            if (gbulk) put_piece1(ii, q, nv);
           }
         }
       } else {
@@ -1132,6 +1276,7 @@ __global__ void __launch_bounds__(kMaxThreads)
         }
       }
       own_rows += r1 - r0;
+      if (gbulk) fence_proxy_async_global();   // the rewritten pieces before the next bulk copies
       cluster.sync();
     }
 

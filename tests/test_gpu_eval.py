@@ -7,7 +7,7 @@ import torch
 from oracle import brsgd as ob
 from oracle import tr
 from tests._util import random_cores, to_lib_cores
-from tests.gpu_helpers import Case, api, cuda, assert_close
+from tests.gpu_helpers import Case, api, cuda, assert_close, assert_update_close
 
 pytestmark = [pytest.mark.gpu, cuda]
 
@@ -104,3 +104,48 @@ def test_batched_problems_match_independent_oracle_runs():
         ob.run(st, X, cfgs[p], 40)
         for k in range(3):
             assert_close(cores_d[p][k].cpu().numpy(), tr.unfold2(st.cores[k]), 1e-11, "cores_d[p][k]")
+
+
+def test_mixed_variant_batch_on_tensor_pieces():
+    """Plain and scaled problems stepped together in one launch, FP32 on the
+    tensor cores as three BF16 pieces, clusters of several CTAs.  With a
+    scaled problem in the launch, CTA 0 of every cluster takes no samples (it
+    factorises the Gram matrix of a scaled problem meanwhile), so CTA 0 of a
+    plain problem updates its rows of G_n from a zero partial gradient.  Every
+    problem's cores are compared, update by update and element by element,
+    with its own oracle step from the same starting cores."""
+    from tests._util import make_problem
+    A = api()
+    rng = np.random.default_rng(31)
+    variants = [ob.VARIANT_PLAIN, ob.VARIANT_SCALED, ob.VARIANT_PLAIN, ob.VARIANT_SCALED]
+    Xs, Xd, cores_d, pcs, cfgs, ranks_l = [], [], [], [], [], []
+    for p, var in enumerate(variants):
+        dims = [int(v) for v in rng.integers(20, 45, size=3)]
+        ranks = [int(v) for v in rng.integers(3, 6, size=3)]
+        std = (ranks[0] * ranks[1]) ** -0.25
+        _, _, X = make_problem(dims, ranks, 300 + p, noise_rel=0.05, std=std)
+        X = X.astype(np.float32).astype(np.float64)
+        start = [G.astype(np.float32).astype(np.float64) for G in random_cores(dims, ranks, 400 + p, std=0.5 * std)]
+        alpha = 0.3 if var == ob.VARIANT_SCALED else 0.05
+        Xs.append(X)
+        Xd.append(torch.from_numpy(np.ascontiguousarray(X.ravel(order="F")).astype(np.float32)).cuda())
+        cores_d.append([torch.from_numpy(G.astype(np.float32)).cuda() for G in to_lib_cores(start)])
+        pcs.append(A.ProblemConfig(dims=dims, ranks=ranks, J=150, prec=A._abi.FP32, alpha=alpha, variant=var,
+                                   seed=60 + p))
+        cfgs.append(ob.Config(J=150, alpha=alpha, variant=var, seed=60 + p))
+        ranks_l.append(ranks)
+    s = A.Solver(pcs, Xd, cores_d)
+    assert s.tensor_pieces() == 3
+    for t in range(3):
+        before = [[c.double().cpu().numpy() for c in cs] for cs in cores_d]
+        s.run(t, 1)
+        torch.cuda.synchronize()
+        for p, var in enumerate(variants):
+            N = 3
+            st = ob.State.new([tr.fold2(before[p][k], ranks_l[p][k], ranks_l[p][(k + 1) % N]) for k in range(N)])
+            ob.step(st, Xs[p], cfgs[p], t)
+            assert_update_close([c.double().cpu().numpy() for c in cores_d[p]], before[p],
+                                [tr.unfold2(G) for G in st.cores], before[p],
+                                1e-4 if var == ob.VARIANT_SCALED else 2e-5, 2.0 ** -24,
+                                what=f"problem {p} core")
+    s.close()
