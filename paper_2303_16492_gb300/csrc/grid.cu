@@ -124,33 +124,36 @@ struct FastDiv {
 template <typename Emit>
 __device__ __forceinline__ void chain_row(const float (&prow)[kGridRmax], const float *S, int Ra, int Rb, Emit emit) {
   // the outputs in a loop (the code stays small enough for the instruction
-  // cache), each inner product unrolled against the registers
+  // cache), each inner product unrolled against the registers as four
+  // interleaved partial sums (groups of four terms, modulo 4) added pairwise:
+  // four independent FMA chains in flight instead of one
   if ((Ra & 3) == 0) {
     const int Ra4 = Ra >> 2;
 #pragma unroll 1
     for (int r = 0; r < Rb; ++r) {
       const float4 *col = reinterpret_cast<const float4 *>(S + r * Ra);
-      float acc = 0.f;
+      float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int c4 = 0; c4 < kGridRmax / 4; ++c4)
         if (c4 < Ra4) {
           const float4 sv = col[c4];
-          acc = fmaf(prow[4 * c4], sv.x, acc);
-          acc = fmaf(prow[4 * c4 + 1], sv.y, acc);
-          acc = fmaf(prow[4 * c4 + 2], sv.z, acc);
-          acc = fmaf(prow[4 * c4 + 3], sv.w, acc);
+          float &x = a[c4 & 3];
+          x = fmaf(prow[4 * c4], sv.x, x);
+          x = fmaf(prow[4 * c4 + 1], sv.y, x);
+          x = fmaf(prow[4 * c4 + 2], sv.z, x);
+          x = fmaf(prow[4 * c4 + 3], sv.w, x);
         }
-      emit(r, acc);
+      emit(r, (a[0] + a[1]) + (a[2] + a[3]));
     }
   } else {
 #pragma unroll 1
     for (int r = 0; r < Rb; ++r) {
       const float *col = S + r * Ra;
-      float acc = 0.f;
+      float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int c = 0; c < kGridRmax; ++c)
-        if (c < Ra) acc = fmaf(prow[c], col[c], acc);
-      emit(r, acc);
+        if (c < Ra) a[(c >> 2) & 3] = fmaf(prow[c], col[c], a[(c >> 2) & 3]);
+      emit(r, (a[0] + a[1]) + (a[2] + a[3]));
     }
   }
 }
