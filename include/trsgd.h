@@ -149,9 +149,10 @@ typedef struct trsgd_handle trsgd_handle;
  *              double for TRSGD_FP64 and float otherwise.  Borrowed for the
  *              handle's lifetime and updated in place by every step.  For
  *              float cores of plain problems the library also keeps each
- *              core as BF16 operand pieces (3 x 256 bytes per 128 rows and
- *              16 columns); every step launch rebuilds them from the cores
- *              first, so the caller may change the cores between calls.
+ *              core as BF16 operand pieces (three: 6 bytes per entry, rows
+ *              padded to 128 and columns to 16); every step launch rebuilds
+ *              them from the cores first, so the caller may change the cores
+ *              between calls.
  *   stream     the stream every later call of this handle enqueues on.
  *   out        receives the handle.
  * Synchronising (it builds the mode-major copies and distribution tables).
