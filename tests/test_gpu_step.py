@@ -553,3 +553,32 @@ def test_scaled_zero_subchain_is_a_numerical_error(prec):
     assert ei.value.status == A._abi.ENUMERIC
     for c, b in zip(case.cores_d, before):
         assert torch.equal(c, b)
+
+
+def test_cores_changed_between_launches_are_used():
+    """FP32 on the tensor pieces keeps every core as BF16 operand pieces that
+    each launch rebuilds: cores overwritten by the caller between launches
+    must be the ones the next steps use.  After a 3-step launch the device
+    cores get fresh values in place; then a 2-step launch (the pieces of the
+    updated rows rewritten inside it) and single steps are compared with the
+    oracle from the new values.  I_1 = 150 rows: two row chunks of G_1."""
+    A = api()
+    case = Case(dims=[150, 20, 25], ranks=[8, 8, 8], J=64, prec=1, alpha=0.05)
+    assert case.solver.tensor_pieces() == 3
+    case.solver.run(0, 3)
+    rng = np.random.default_rng(77)
+    for G in case.cores_d:
+        G.copy_(torch.from_numpy(rng.standard_normal(tuple(G.shape)).astype(np.float32) * 0.3).cuda())
+    torch.cuda.synchronize()
+    case.resync()
+    for t in (3, 4):
+        ob.step(case.state, case.X, case.ocfg, t)
+    case.solver.run(3, 2)
+    torch.cuda.synchronize()
+    case.assert_cores(2e-5)
+    for t in (5, 6):
+        case.resync()
+        ob.step(case.state, case.X, case.ocfg, t)
+        case.solver.step(t)
+        torch.cuda.synchronize()
+        case.assert_cores(2e-5)
