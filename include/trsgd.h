@@ -251,9 +251,9 @@ trsgd_status trsgd_reconstruct(int32_t N, const int64_t *I, const int64_t *R,
  *   loss_dev float [1] receives L.
  * The adjoint of core k != n is accumulated per sample from prefix and
  * suffix slice products of the chain (product rule on the trace).  The
- * per-sample terms are added with FP32 atomics, so the last bits of the loss
- * and of the gradients depend on the order in which the samples finish (the
- * stepping entry points, in contrast, sum in a fixed order). */
+ * per-sample terms go to a stream-ordered scratch (cudaMallocAsync, freed
+ * on the stream) and are added in increasing j: the results are
+ * bit-reproducible. */
 trsgd_status trsgd_sampled_loss_grad(int32_t N, const int64_t *I, const int64_t *R,
                                      int32_t n, int64_t J, const int32_t *idx_dev,
                                      const float *XS_dev, const float *w_dev,

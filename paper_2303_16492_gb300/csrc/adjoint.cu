@@ -10,7 +10,10 @@
 //   dL/dS_s           += (B_s M_j A_s)^T,
 // A_s = S_1 ... S_{s-1} (prefix), B_s = S_{s+1} ... S_L (suffix).  Each CTA
 // handles one sample and recomputes its prefix and suffix products in shared
-// memory, so nothing of size J*N*R^2 is ever stored.
+// memory, so no prefix or suffix product is ever stored.  The per-sample
+// terms (the loss, w_j e, Z(j, :) and each slice's R x R term) go to a
+// stream-ordered scratch, and three reduction kernels add them in increasing
+// j (fixed order, no atomics): the results do not depend on the schedule.
 #include "blocks.cuh"
 #include "internal.h"
 
@@ -26,8 +29,9 @@ struct AdjArgs {
   const float *XS;
   const float *w;
   const float *cores[kMaxOrder];
-  float *grads[kMaxOrder];
-  float *loss;
+  bool grads;                        // the gradients are wanted
+  // per-sample scratch: loss [J], w_j e [J][I_n], Z [J][Q], slice terms [J][L][kAdjR^2]
+  float *lossj, *ew, *zj, *cb;
 };
 
 __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
@@ -85,15 +89,12 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
   if (tid == 0) {
     float tot = 0.f;
     for (int x = 0; x < NT / 32; ++x) tot += red[x];
-    atomicAdd(a.loss, tot);
+    a.lossj[j] = tot;
   }
-  if (a.grads[0] == nullptr) return;
-  // core n: w e_i Z(q)
-  float *gn = a.grads[n];
-  for (int e = tid; e < In * Q; e += NT) {
-    const int i = e / Q, q = e % Q;
-    atomicAdd(gn + e, wj * e_s[i] * Z[q]);
-  }
+  if (!a.grads) return;
+  // core n: the terms w e_i Z(q), as w e and Z
+  for (int i = tid; i < In; i += NT) a.ew[(size_t)j * In + i] = wj * e_s[i];
+  for (int q = tid; q < Q; q += NT) a.zj[(size_t)j * Q + q] = Z[q];
   // M[r][r'] = sum_i w e_i G_n(i)[r][r'] = sum_i w e_i G_n(2)(i, r + r' R_n)
   for (int e = tid; e < Rn * Rn1; e += NT) {
     const int r = e / Rn1, rp = e % Rn1;
@@ -115,14 +116,13 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
       T1[r * Ra + x] = acc;
     }
     __syncthreads();
-    // grad slice (x, b) += (B_s T1)[b][x], B_s = Suf[cur] (R_{k+1} x R_n)
-    const int i = a.idx[(size_t)j * N + k];
-    float *gk = a.grads[k] + (size_t)i * Ra * Rb;
+    // this sample's term of slice (x, b): (B_s T1)[b][x], B_s = Suf[cur] (R_{k+1} x R_n)
+    float *ck = a.cb + ((size_t)j * L + s) * (kAdjR * kAdjR);
     for (int e = tid; e < Ra * Rb; e += NT) {
       const int x = e % Ra, b = e / Ra;
       float acc = 0.f;
       for (int r = 0; r < Rn; ++r) acc = fmaf(Suf[cur][b * Rn + r], T1[r * Ra + x], acc);
-      atomicAdd(gk + x + b * Ra, acc);
+      ck[x + b * Ra] = acc;
     }
     // B_{s-1} = S_s B_s  (R_k x R_n)
     if (s > 0) {
@@ -138,10 +138,51 @@ __global__ void __launch_bounds__(kAdjThreads) adjoint_kernel(AdjArgs a) {
   }
 }
 
+// The loss: each thread sums a contiguous run of samples in order, then
+// thread 0 adds the runs in thread order.
+__global__ void __launch_bounds__(kAdjThreads) adjoint_loss_kernel(const float *lossj, int J, float *loss) {
+  __shared__ float part[kAdjThreads];
+  const int tid = threadIdx.x, per = (J + kAdjThreads - 1) / kAdjThreads;
+  float acc = 0.f;
+  for (int j = tid * per; j < min(J, (tid + 1) * per); ++j) acc += lossj[j];
+  part[tid] = acc;
+  __syncthreads();
+  if (tid == 0) {
+    float tot = 0.f;
+    for (int x = 0; x < kAdjThreads; ++x) tot += part[x];
+    *loss = tot;
+  }
+}
+
+// dL/dG_n(2)(i, q) = sum_j (w_j e_ij) Z(j, q), j increasing; one thread per entry.
+__global__ void adjoint_core_n_kernel(const float *ew, const float *zj, int J, int In, int Q, float *gn) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)In * Q) return;
+  const int i = (int)(e / Q), q = (int)(e % Q);
+  float acc = 0.f;
+  for (int j = 0; j < J; ++j) acc = fmaf(ew[(size_t)j * In + i], zj[(size_t)j * Q + q], acc);
+  gn[e] = acc;
+}
+
+// dL/dG_k(i) = sum over the samples j with index i on core k of their slice
+// terms, j increasing; one thread per slice entry.  s = core k's position in
+// the chain.
+__global__ void adjoint_slices_kernel(const float *cb, const int *idx, int J, int N, int L, int k, int s, int Ik,
+                                      int RR, float *gk) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)Ik * RR) return;
+  const int i = (int)(e / RR), el = (int)(e % RR);
+  float acc = 0.f;
+  for (int j = 0; j < J; ++j)
+    if (__ldg(idx + (size_t)j * N + k) == i) acc += cb[((size_t)j * L + s) * (kAdjR * kAdjR) + el];
+  gk[e] = acc;
+}
+
 cudaError_t launch_sampled_loss_grad(int N, const int *I, const int *R, int n, int J,
                                      const int *idx, const float *XS, const float *w,
                                      const float *const *cores, float *const *grads, float *loss,
                                      cudaStream_t s) {
+  if (J <= 0) return cudaSuccess;   // the caller zeroed the loss and the gradients
   AdjArgs a = {};
   a.N = N;
   a.n = n;
@@ -150,19 +191,40 @@ cudaError_t launch_sampled_loss_grad(int N, const int *I, const int *R, int n, i
     a.I[k] = I[k];
     a.R[k] = R[k];
     a.cores[k] = cores[k];
-    a.grads[k] = grads ? grads[k] : nullptr;
   }
+  a.grads = grads != nullptr;
   a.idx = idx;
   a.XS = XS;
   a.w = w;
-  a.loss = loss;
-  const size_t dyn = (size_t)I[n] * sizeof(float);
-  if (dyn > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
+  const int L = N - 1, In = I[n], Q = R[n] * R[(n + 1) % N];
+  const size_t nl = (size_t)J, new_ = grads ? (size_t)J * In : 0, nz = grads ? (size_t)J * Q : 0,
+               nc = grads ? (size_t)J * L * kAdjR * kAdjR : 0;
+  float *scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void **>(&scratch), (nl + new_ + nz + nc) * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  a.lossj = scratch;
+  a.ew = scratch + nl;
+  a.zj = a.ew + new_;
+  a.cb = a.zj + nz;
+  const size_t dyn = (size_t)In * sizeof(float);
+  if (dyn > 48 * 1024) e = cudaFuncSetAttribute(adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+  if (e == cudaSuccess) {
+    adjoint_kernel<<<J, kAdjThreads, dyn, s>>>(a);
+    adjoint_loss_kernel<<<1, kAdjThreads, 0, s>>>(a.lossj, J, loss);
+    if (grads) {
+      const long long nn = (long long)In * Q;
+      adjoint_core_n_kernel<<<(unsigned)((nn + 255) / 256), 256, 0, s>>>(a.ew, a.zj, J, In, Q, grads[n]);
+      for (int sp = 0; sp < L; ++sp) {
+        const int k = (n + 1 + sp) % N, RR = R[k] * R[(k + 1) % N];
+        const long long nk = (long long)I[k] * RR;
+        adjoint_slices_kernel<<<(unsigned)((nk + 255) / 256), 256, 0, s>>>(a.cb, idx, J, N, L, k, sp, I[k], RR,
+                                                                            grads[k]);
+      }
+    }
+    e = cudaGetLastError();
   }
-  if (J > 0) adjoint_kernel<<<J, kAdjThreads, dyn, s>>>(a);
-  return cudaGetLastError();
+  const cudaError_t f = cudaFreeAsync(scratch, s);
+  return e != cudaSuccess ? e : f;
 }
 
 }  // namespace trsgd
