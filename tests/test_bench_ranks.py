@@ -73,3 +73,21 @@ def test_reference_arm_line_on_rank_zero(monkeypatch):
     line = json.loads(buf.getvalue().strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_traffic_record_reported_only_for_its_sources(monkeypatch):
+    """roofline.traffic comes from an ncu capture tied to a digest of the step
+    kernel's sources: reported while the digest matches, null once any of
+    those files differs (a stale capture is never reported)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    key = ("c2", "step_cluster_kernel<float,float,12,3,false>")
+    rec = bench.MEASURED_TRAFFIC_PER_STEP[key]
+    monkeypatch.setattr(bench, "sources_digest", lambda files: rec["sources"])
+    assert bench.measured_traffic(*key) == rec["bytes"]
+    monkeypatch.setattr(bench, "sources_digest", lambda files: "0" * 16)
+    assert bench.measured_traffic(*key) is None
+    assert bench.measured_traffic("c3", key[1]) is None
+    # the digest covers every source file the step kernel is built from
+    for f in bench.STEP_KERNEL_SOURCES:
+        assert os.path.exists(os.path.join(ROOT, "paper_2303_16492_gb300", "csrc", f)), f
